@@ -1,0 +1,6 @@
+"""FP64 CPU oracle of the SG-splatting rasterizer -- test infrastructure only.
+
+Only the tests, the smoke check and the bench's CPU-baseline leg may import it.
+"""
+from .sg_oracle import *  # noqa: F401,F403
+from .sg_oracle import Decisions, ViewResult  # noqa: F401
