@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark: forward + backward of the SG-splatting rasterizer.
+
+One step = one forward (preprocessSG, depth sort, duplicateWithKeys, tile sort,
+ranges, blend) and one backward (blend adjoint, preprocess adjoint) of one
+1920x1080 view of a synthetic 1M-Gaussian scene with 0-4 SG lobes per Gaussian
+(mix 20/30/25/15/10 %), soft masks U(0,1), and an upstream image gradient
+N(0, 0.01). Inputs are resident in HBM; L2 is flushed between timed steps.
+
+Prints ONE JSON line. `--impl reference` times the FP64 CPU oracle instead
+(the only place besides the cpu_baseline leg where bench.py runs it).
+Multi-GPU (torchrun): independent replicas, one per rank, no collective on the
+data path (weak scaling); rank 0 prints the max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ms/view & Mpixel/s (1080p, 1M Gaussians, ≤4 SG); batched vs plain"
+UNIT = "Mpixel/s"
+L2_FLUSH_BYTES = 512 << 20
+
+# Algorithmic FP32 work per evaluated (pixel, Gaussian) pair, FMA = 2 flops
+# (derivation in the design doc): forward 23, backward 69.
+FLOPS_PER_EVAL = {"blend_fwd": 23.0, "blend_bwd": 69.0}
+# GB300 FP32 (non-tensor) peak: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
+SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["f32", "f16", "f16_bf16s"], default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-tiles", type=int, default=48,
+                    help="tiles of the frame the CPU oracle blends per sample")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2509_07021_gb300 import synth
+    scene, cams, rng = synth.config3()
+    d_img = synth.upstream_grad(np.random.default_rng(synth.SEED_BASE + 33), cams[0])
+    return scene, cams, d_img
+
+
+def workload_config(args, cams, extra=None):
+    c = cams[0]
+    cfg = {"workload": f"1M Gaussians, {c.width}x{c.height}, lobes 0-4 (mix 20/30/25/15/10%), "
+                       f"masks U(0,1), {args.storage} storage, fwd+bwd, 1 view/step",
+           "n_gaussians": 1_000_000, "width": c.width, "height": c.height, "views_per_step": 1,
+           "storage": args.storage, "l2": "flushed between timed steps (512 MiB write)",
+           "parallelism": f"replicas x{args.gpus}"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline / --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(scene, cam, d_img, n_tiles, seed=0):
+    """One bounded oracle sample of the workload: full preprocess and tile
+    sort of the frame, then forward + backward blend on n_tiles random tiles
+    (upstream gradient restricted to them). Returns (seconds, est. seconds
+    for the full frame, threads)."""
+    import oracle
+    t0 = time.perf_counter()
+    dec = oracle.decisions_fp32(scene, cam)
+    oracle.tile_lists(dec, cam)
+    t_fixed_lists = time.perf_counter() - t0
+    sel = np.zeros(cam.n_tiles, bool)
+    sel[np.random.default_rng(seed).choice(cam.n_tiles, n_tiles, replace=False)] = True
+    t1 = time.perf_counter()
+    res = oracle.render_forward(scene, cam, tile_sel=sel, need_grad=True)
+    m = np.repeat(np.repeat(sel.reshape(cam.tiles_y, cam.tiles_x), 16, 0), 16, 1)
+    m = m[:cam.height, :cam.width]
+    oracle.render_backward(res, scene, cam, d_img * m[None])
+    t_sample = time.perf_counter() - t1
+    total = t_fixed_lists + t_sample
+    # the sample repeats the preprocess/sort once more inside render_forward:
+    # count it once, scale the per-tile blend part to the whole frame
+    t_blend = max(t_sample - t_fixed_lists, 0.0)
+    est_full = t_sample - t_blend + t_blend * cam.n_tiles / n_tiles
+    return total, est_full, oracle.num_threads()
+
+
+def cpu_baseline_line(scene, cam, d_img, n_tiles):
+    total, est_full, threads = oracle_sample(scene, cam, d_img, n_tiles)
+    mpx = cam.width * cam.height / 1e6
+    return {"value": mpx / est_full, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"FP64 oracle: full-frame preprocess + tile sort, forward+backward blend on "
+                       f"{n_tiles} of {cam.n_tiles} random tiles ({total:.1f} s wall), blend time "
+                       f"scaled to the frame; {threads} OpenMP threads for the blend, numpy/torch "
+                       f"for the rest")}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    scene, cams, d_img = workload()
+    cam = cams[0]
+    n_tiles = max(4, args.cpu_tiles // 3)
+    for _ in range(args.warmup):
+        oracle_sample(scene, cam, d_img, n_tiles)
+    ests, totals = [], []
+    threads = 1
+    for i in range(args.steps):
+        total, est, threads = oracle_sample(scene, cam, d_img, n_tiles, seed=i)
+        ests.append(est)
+        totals.append(total)
+    ms = 1e3 * float(np.mean(ests))
+    value = cam.width * cam.height / 1e6 / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, cams),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step: full-frame preprocess + tile sort, fwd+bwd blend "
+                                       f"on {n_tiles} random tiles, blend scaled to the frame "
+                                       f"(mean wall {np.mean(totals):.1f} s/step)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2509_07021_gb300 import render, sgsplat
+    from paper_2509_07021_gb300.sgsplat import DeviceScene
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local)
+    sgsplat.lib()   # fails loudly if the extension is missing
+    scene, cams, d_img_np = workload()
+    cam = cams[0]
+    ds = DeviceScene.from_host(scene, device="cuda", storage=args.storage)
+    d_img = torch.from_numpy(d_img_np)[None].cuda()
+    grads = render.alloc_grads(ds)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step():
+        out = render.render_forward(ds, cams)
+        render.render_backward(ds, cams, out, d_img, grads)
+        return out
+
+    for _ in range(max(args.warmup, 1)):
+        out = step()
+    torch.cuda.synchronize()
+    n_pairs = out.sizes["n_pairs"]
+
+    # pair evaluations (counting kernels, untimed)
+    sgsplat.sg_profile_enable(sgsplat.SG_PROFILE_COUNT)
+    sgsplat.sg_profile_read(reset=True)
+    step()
+    torch.cuda.synchronize()
+    evals = sgsplat.sg_profile_read(reset=True)["pair_evals"]
+    sgsplat.sg_profile_enable(0)
+
+    # ---- timed region (device events per step, L2 flushed between steps) ----
+    sgsplat.sg_profile_enable(sgsplat.SG_PROFILE_EVENTS)
+    sgsplat.sg_profile_read(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = sgsplat.sg_kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record()
+        step()
+        ends[i].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = sgsplat.sg_kernel_launches() - launches0
+    clk = clocks.stop()
+    sgsplat.sg_profile_enable(0)
+    prof = sgsplat.sg_profile_read(reset=True)
+    t_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms_step = max_over_ranks(t_ms / args.steps, world)
+    px = cam.width * cam.height
+    value = world * px / (ms_step / 1e3) / 1e6
+
+    # ---- roofline of the dominant kernel ----
+    stages = prof["stages"]
+    fl_stages = {k: v for k, v in stages.items() if v["launches"]}
+    dom = max(fl_stages, key=lambda k: fl_stages[k]["ms"])
+    share = {k: round(v["ms"] / max(sum(x["ms"] for x in fl_stages.values()), 1e-9), 4)
+             for k, v in fl_stages.items()}
+    avg_ms = stages[dom]["ms"] / max(stages[dom]["launches"], 1)
+    if dom in FLOPS_PER_EVAL:
+        ev = evals["forward" if dom == "blend_fwd" else "backward"]
+        achieved = ev * FLOPS_PER_EVAL[dom] / (avg_ms / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz (FP32 non-tensor)",
+                "pair_evals": ev, "flops_per_eval": FLOPS_PER_EVAL[dom], "avg_ms": avg_ms}
+    else:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "traffic": None, "avg_ms": avg_ms}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = run_e2e(args, ds, cams, d_img_np, grads, world)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args, cams, {"n_pairs": n_pairs}),
+            "roofline": roof, "clocks": clk, "e2e": e2e,
+            "gpu_launches": int(launches),
+            "stages_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in fl_stages.items()},
+            "stage_share": share,
+            "pair_evals": evals}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_line(scene, cam, d_img_np, args.cpu_tiles)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, ds, cams, d_img_np, grads, world):
+    """Same metric through the public API with pinned host inputs and outputs:
+    every step copies the scene and the upstream gradient host->device and the
+    image and all gradients device->host."""
+    import torch
+    from paper_2509_07021_gb300 import render
+    from paper_2509_07021_gb300.sgsplat import DeviceScene
+
+    fields = list(DeviceScene.FLOAT_FIELDS) + ["lobe_off"]
+    host_in = {k: getattr(ds, k).cpu().pin_memory() for k in fields}
+    host_dimg = torch.from_numpy(d_img_np)[None].pin_memory()
+    dev_dimg = torch.empty_like(host_dimg, device="cuda")
+    host_img = torch.empty((1, 3, cams[0].height, cams[0].width), dtype=torch.float32).pin_memory()
+    host_grads = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in grads.items()}
+    h2d = sum(t.numel() * t.element_size() for t in host_in.values()) + host_dimg.numel() * 4
+    d2h = host_img.numel() * 4 + sum(t.numel() * 4 for t in host_grads.values())
+
+    def step():
+        for k in fields:
+            getattr(ds, k).copy_(host_in[k], non_blocking=True)
+        dev_dimg.copy_(host_dimg, non_blocking=True)
+        out = render.render_forward(ds, cams)
+        render.render_backward(ds, cams, out, dev_dimg, grads)
+        host_img.copy_(out.img, non_blocking=True)
+        for k, v in grads.items():
+            host_grads[k].copy_(v, non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    t = (time.perf_counter() - t0) / args.steps
+    t = max_over_ranks(t, world)
+    px = cams[0].width * cams[0].height
+    return {"value": world * px / t / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t}
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

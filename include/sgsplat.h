@@ -1,0 +1,258 @@
+/*
+ * sgsplat.h -- C ABI of the GB300 (sm_103a) SG-splatting rasterizer.
+ *
+ * The library renders 3D Gaussians whose view-dependent colour is a diffuse
+ * base plus a variable number of arbitrarily oriented Spherical-Gaussian
+ * lobes (MEGS^2, Sec. 3.2, Eq. 1-2):
+ *
+ *     c(v) = c0 + sum_k m_k * a_k * exp(s_k * (mu_k . v - 1)),   rgb = max(c, 0)
+ *
+ * and composites them front to back over 16x16 pixel tiles (Sec. 3.1):
+ *
+ *     C = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j) + T_final * bg,
+ *     alpha_i = min(0.99, m_g o_i exp(-1/2 d^T Sigma2D^-1 d)).
+ *
+ * Forward and backward (the exact adjoint, gradients for every float input
+ * including the soft-pruning masks m_g and m_l of Sec. 3.3).
+ *
+ * Conventions (all entry points)
+ *  - Every pointer marked "device" is a CUDA device pointer on the current
+ *    device; every pointer marked "host" is ordinary host memory read during
+ *    the call only. The library allocates NO device memory: inputs, outputs,
+ *    gradients and the workspaces are owned by the caller.
+ *  - Work is issued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and is stream ordered. sg_render_forward synchronises the stream
+ *    once (a 4-byte read of the pair count); every other call is asynchronous.
+ *  - Float arrays are planar structure of arrays: a "[3][N]" array holds N x
+ *    values, then N y values, then N z values. Base addresses must be 16-byte
+ *    aligned.
+ *  - Quaternions are (w, x, y, z), not necessarily normalised. Scales and
+ *    opacities are the activated values (scale > 0, opacity in [0, 1]).
+ *  - Cameras are pinhole, OpenCV axes (x right, y down, z forward); pixel
+ *    (i, j) is sampled at its centre.
+ *  - Return value: SG_OK or an sg_status error code; sg_last_error() gives a
+ *    message (thread local). No call aborts or throws across the ABI. A CUDA
+ *    launch failure is reported as SG_ERR_CUDA; the stream's earlier work is
+ *    not undone.
+ *  - NaN or infinite geometry culls the Gaussian; NaN colour inputs propagate
+ *    into the image.
+ */
+#ifndef SGSPLAT_H
+#define SGSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SG_ABI_VERSION 1
+#define SG_TILE 16          /* tile edge in pixels */
+#define SG_MAX_VIEWS 128    /* views per call */
+#define SG_MAX_SCENES 32    /* scenes per batched call */
+
+typedef enum sg_status {
+    SG_OK = 0,
+    SG_ERR_INVALID_ARG = 1, /* null/misaligned pointer, bad size or dtype */
+    SG_ERR_WORKSPACE = 2,   /* workspace smaller than sg_sizes says */
+    SG_ERR_CAPACITY = 3,    /* more (tile, Gaussian) pairs than the workspace holds */
+    SG_ERR_TIMEOUT = 4,     /* a bounded device wait expired */
+    SG_ERR_CUDA = 5         /* a CUDA runtime call failed */
+} sg_status;
+
+/* Storage type of a parameter family. Arithmetic is always binary32. */
+typedef enum sg_dtype { SG_F32 = 0, SG_F16 = 1, SG_BF16 = 2 } sg_dtype;
+
+/*
+ * One scene: N Gaussians with L lobes in CSR form (Gaussian g owns lobes
+ * lobe_off[g] .. lobe_off[g+1]-1). Device pointers.
+ *   means  [3][N]  centre mu (Sec. 3.1)            dtype_geom
+ *   scales [3][N]  per-axis std (Sigma = R S S^T R^T)  dtype_geom
+ *   quats  [4][N]  rotation (w, x, y, z)           dtype_geom
+ *   opac   [N]     opacity o                       dtype_geom
+ *   gmask  [N]     per-Gaussian soft mask m_g      binary32
+ *   c0     [3][N]  diffuse colour (Eq. 2)          binary32
+ *   lobe_off [N+1] int32, lobe_off[0] = 0, non-decreasing, lobe_off[N] = L
+ *   axis   [3][L]  lobe axis mu (Eq. 1), normalised by the kernel   dtype_lobe
+ *   sharp  [L]     lobe sharpness s (Eq. 1), used as given          dtype_sharp
+ *   amp    [3][L]  lobe RGB amplitude a (Eq. 1)                      dtype_lobe
+ *   lmask  [L]     per-lobe soft mask m_l                            binary32
+ * Only SG_F32 (all families), SG_F16 (geom, lobe, sharp) and SG_BF16 (sharp)
+ * are accepted.
+ */
+typedef struct sg_scene {
+    int64_t n;
+    int64_t n_lobes;
+    int32_t dtype_geom;
+    int32_t dtype_lobe;
+    int32_t dtype_sharp;
+    int32_t reserved;
+    const void *means;
+    const void *scales;
+    const void *quats;
+    const void *opac;
+    const float *gmask;
+    const float *c0;
+    const int32_t *lobe_off;
+    const void *axis;
+    const void *sharp;
+    const void *amp;
+    const float *lmask;
+} sg_scene;
+
+/*
+ * Pinhole camera (host struct, copied at each call).
+ *   viewmat: row-major 3x4 world->camera [R | t], R a rotation.
+ *   near_plane: Gaussians with camera depth <= near_plane are culled (0.2).
+ *   bg: background colour added as T_final * bg.
+ */
+typedef struct sg_camera {
+    int32_t width;
+    int32_t height;
+    float fx, fy, cx, cy;
+    float viewmat[12];
+    float near_plane;
+    float bg[3];
+} sg_camera;
+
+/* Gradients for one scene (device pointers, binary32, same layout as the
+ * sg_scene arrays). Every array is OVERWRITTEN; contributions of all views of
+ * the scene are summed. A NULL pointer skips that family. */
+typedef struct sg_grads {
+    float *means;
+    float *scales;
+    float *quats;
+    float *opac;
+    float *gmask;
+    float *c0;
+    float *axis;
+    float *sharp;
+    float *amp;
+    float *lmask;
+} sg_grads;
+
+/* Sizes reported by the query and by the forward call. */
+typedef struct sg_sizes {
+    uint64_t n_entries;        /* sum over views of the view's scene's N */
+    uint64_t n_tiles;          /* tiles over all views */
+    uint64_t n_pixels;         /* pixels over all views */
+    uint64_t n_pairs;          /* (tile, Gaussian) pairs of the last forward */
+    uint64_t pair_capacity;    /* pairs the queried workspace holds */
+    uint64_t ws_fixed_bytes;   /* forward workspace part independent of pairs */
+    uint64_t ws_per_pair_bytes;/* forward workspace bytes per pair of capacity */
+    uint64_t ws_bytes;         /* forward workspace for pair_capacity */
+    uint64_t bwd_ws_bytes;     /* backward scratch */
+} sg_sizes;
+
+/*
+ * Byte offsets, inside the forward workspace, of the buffers a finished
+ * sg_render_forward leaves there (M = sg_sizes.n_entries; entry
+ * e = ent_off(view) + Gaussian id, views in call order). Read-only views for
+ * inspection, e.g. visibility and screen radius per Gaussian.
+ *   rec           [M] 48-byte records, binary32:
+ *                     x, y, conic A, conic B | conic C, o', r, g | b, radius, depth, 0
+ *                 (x, y: projected centre in pixel-index coordinates; conic
+ *                 (A, B, C) = inverse of the dilated 2D covariance; o' = m_g o;
+ *                 rgb = max(c(v), 0); radius = ceil(3 sqrt(lambda_max)); depth =
+ *                 camera-space z). Valid where tiles_touched > 0.
+ *   tiles_touched [M] uint32, 0 = culled
+ *   rect          [M] 2 x uint32: x0 | x1 << 16, y0 | y1 << 16 (tiles, half open)
+ *   depth_order   [M] uint32 entries sorted by (depth bits, entry)
+ *   ranges        [n_tiles] 2 x uint32 [start, end) into the pair arrays
+ *   pair_tile     [n_pairs] uint32 global tile id (view tile offset + ty * tiles_x + tx)
+ *   pair_entry    [n_pairs] uint32 entry of each pair, sorted by (tile, depth bits, entry)
+ */
+typedef struct sg_ws_layout {
+    uint64_t rec;
+    uint64_t tiles_touched;
+    uint64_t rect;
+    uint64_t depth_order;
+    uint64_t ranges;
+    uint64_t pair_tile;
+    uint64_t pair_entry;
+    uint64_t total_bytes;
+} sg_ws_layout;
+
+/* Layout of a forward workspace of ws_bytes for this scene and these cameras
+ * (host only; the same arguments as the forward call). */
+int sg_workspace_layout(const sg_scene *scene, const sg_camera *cams, int n_views, size_t ws_bytes,
+                        sg_ws_layout *out);
+
+/*
+ * Stage profiling (off by default; process wide, not thread safe against
+ * concurrent renders). With SG_PROFILE_EVENTS set, every stage of the
+ * following forward/backward calls is bracketed by CUDA events recorded on
+ * the call's stream; with SG_PROFILE_COUNT set, the blend kernels also count
+ * (pixel, Gaussian) pair evaluations (a slower counting variant: use it in
+ * a pass of its own). sg_profile_read waits for the recorded events, adds
+ * their times (ms) and launch counts per stage into ms[i] / launches[i]
+ * (arrays of SG_PROFILE_STAGES), the forward and backward pair evaluations
+ * into pair_evals[0..1] (any pointer may be NULL), and clears them if
+ * reset != 0.
+ */
+#define SG_PROFILE_EVENTS 1
+#define SG_PROFILE_COUNT 2
+#define SG_PROFILE_STAGES 12
+int sg_profile_enable(int flags);
+int sg_profile_read(double *ms, int64_t *launches, int64_t *pair_evals, int reset);
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t sg_kernel_launches(void);
+/* Name of stage i ("preprocess", "depth_sort", ..., "preprocess_bwd"); NULL if out of range. */
+const char *sg_profile_stage_name(int i);
+
+/* Version of this ABI (SG_ABI_VERSION). */
+int sg_version(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *sg_last_error(void);
+
+/*
+ * Workspace sizes for rendering `scene` from `n_views` cameras with room for
+ * `pair_capacity` (tile, Gaussian) pairs. Host-only, no device work.
+ * scene: host struct (pointers are not dereferenced); cams: host [n_views].
+ */
+int sg_workspace_query(const sg_scene *scene, const sg_camera *cams, int n_views,
+                       uint64_t pair_capacity, sg_sizes *out);
+
+/*
+ * Forward render of one scene from n_views cameras (Sec. 3.1 compositing with
+ * the SG colour of Eq. 2). Runs preprocessSG, the depth-key radix sort,
+ * duplicateWithKeys, the tile-key radix sort, tile ranges and the tile blend.
+ *
+ * ws: device workspace of ws_bytes, 256-byte aligned. It must hold at least
+ *   sg_sizes.ws_fixed_bytes; the pairs the call needs are counted on the
+ *   device and read back once (the call synchronises `stream` here). If they
+ *   exceed the capacity, the call returns SG_ERR_CAPACITY with out->n_pairs
+ *   and out->ws_bytes set to what is needed and leaves the outputs
+ *   unspecified; call again with a larger workspace. After success the
+ *   workspace holds what sg_render_backward reads: keep it unmodified.
+ * img: device [n_views] x [3][H][W] binary32, views packed one after another.
+ * T_final: device [n_views] x [H][W] binary32, transmittance after the walk.
+ * last: device [n_views] x [H][W] int32, 1 + position (inside the pixel's
+ *   tile list) of the last blended Gaussian, 0 if none.
+ * out: host, may be NULL.
+ */
+int sg_render_forward(const sg_scene *scene, const sg_camera *cams, int n_views, void *ws,
+                      size_t ws_bytes, float *img, float *T_final, int32_t *last,
+                      sg_sizes *out, void *stream);
+
+/*
+ * Backward of sg_render_forward for L = sum(d_img * img): the exact adjoint of
+ * the compositing (zero through skips, the early stop and clamped branches).
+ * ws: the workspace of the matching forward call (read only).
+ * T_final, last: the forward's outputs (device, read only).
+ * d_img: device, same layout as img.
+ * bwd_ws: device scratch of at least sg_sizes.bwd_ws_bytes, 256-byte aligned.
+ * grads: host struct of device pointers (overwritten, see sg_grads).
+ */
+int sg_render_backward(const sg_scene *scene, const sg_camera *cams, int n_views,
+                       const void *ws, size_t ws_bytes, const float *T_final,
+                       const int32_t *last, const float *d_img, void *bwd_ws,
+                       size_t bwd_ws_bytes, const sg_grads *grads, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGSPLAT_H */

@@ -150,7 +150,8 @@ void orc_blend_forward(int W, int H, const int64_t *ranges, const int64_t *ids,
 
 /*
  * Adjoint of orc_blend_forward for the loss L = sum(dimg * img). Accumulates
- * dL/d(xy, conic, o', rgb) per Gaussian (arrays are added to, not cleared).
+ * dL/d(xy, conic, o', rgb) per Gaussian (arrays are added to, not cleared);
+ * tiles run in parallel, so the FP64 summation order varies from run to run.
  * Exact derivative of the walk as written: zero through the skips, the stop,
  * and on the clamped branch of the 0.99 alpha clamp.
  */
@@ -169,6 +170,7 @@ void orc_blend_backward(int W, int H, const int64_t *ranges, const int64_t *ids,
         const int64_t len = ranges[2 * t + 1] - ranges[2 * t];
         if (len > max_len) max_len = len;
     }
+#pragma omp parallel for schedule(dynamic, 4)
     for (int t = 0; t < tx_n * ty_n; ++t) {
         if (tile_sel && !tile_sel[t]) continue;
         const int tx = t % tx_n, ty = t / tx_n;
@@ -195,24 +197,52 @@ void orc_blend_backward(int W, int H, const int64_t *ranges, const int64_t *ids,
                     double dalpha = 0.0;
                     for (int ch = 0; ch < 3; ++ch) {
                         const double ci = rgb[3 * id + ch];
-                        drgb[3 * id + ch] += al * Ti * gc[ch];
+                        {
+                        const double v_ = al * Ti * gc[ch];
+#pragma omp atomic
+                        drgb[3 * id + ch] += v_;
+                    }
                         dalpha += gc[ch] * (ci * Ti - (S[ch] + Tf * bg[ch]) / (1.0 - al));
                         S[ch] += ci * al * Ti;
                     }
                     if (rc[i]) continue; /* alpha = 0.99 constant on this branch */
                     const double G = rG[i];
-                    dop[id] += dalpha * G;
+                    {
+                        const double v_ = dalpha * G;
+#pragma omp atomic
+                        dop[id] += v_;
+                    }
                     const double dpower = dalpha * op[id] * G;
                     const double dx = (double)px - xy[2 * id + 0];
                     const double dy = (double)py - xy[2 * id + 1];
                     const double A = conic[3 * id + 0], B = conic[3 * id + 1],
                                  C = conic[3 * id + 2];
-                    dconic[3 * id + 0] += dpower * (-0.5 * dx * dx);
-                    dconic[3 * id + 1] += dpower * (-dx * dy);
-                    dconic[3 * id + 2] += dpower * (-0.5 * dy * dy);
+                    {
+                        const double v_ = dpower * (-0.5 * dx * dx);
+#pragma omp atomic
+                        dconic[3 * id + 0] += v_;
+                    }
+                    {
+                        const double v_ = dpower * (-dx * dy);
+#pragma omp atomic
+                        dconic[3 * id + 1] += v_;
+                    }
+                    {
+                        const double v_ = dpower * (-0.5 * dy * dy);
+#pragma omp atomic
+                        dconic[3 * id + 2] += v_;
+                    }
                     /* d power / d dx = -(A dx + B dy); d dx / d x_centre = -1 */
-                    dxy[2 * id + 0] += dpower * (A * dx + B * dy);
-                    dxy[2 * id + 1] += dpower * (C * dy + B * dx);
+                    {
+                        const double v_ = dpower * (A * dx + B * dy);
+#pragma omp atomic
+                        dxy[2 * id + 0] += v_;
+                    }
+                    {
+                        const double v_ = dpower * (C * dy + B * dx);
+#pragma omp atomic
+                        dxy[2 * id + 1] += v_;
+                    }
                 }
             }
         free(rk);

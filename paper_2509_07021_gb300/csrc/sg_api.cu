@@ -1,0 +1,544 @@
+// C ABI of the SG-splatting rasterizer: argument checks, workspace layout and
+// the launch sequence of the forward and backward passes.
+#include "sg_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+using namespace sgk;
+
+namespace {
+std::atomic<int64_t> &launch_counter();
+}
+
+void sgk::count_launches(int n) { launch_counter() += n; }
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    return fail(SG_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define SG_CUDA(call, where)                                 \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);  \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// stage profiler: CUDA events recorded on the caller's stream
+// ---------------------------------------------------------------------------
+enum Stage {
+    ST_SETUP = 0, ST_PRE, ST_DEPTH_SORT, ST_OFFSETS, ST_READ_PAIRS, ST_DUPLICATE, ST_TILE_SORT,
+    ST_RANGES, ST_BLEND_FWD, ST_BWD_CLEAR, ST_BLEND_BWD, ST_PRE_BWD, ST_N
+};
+static_assert(ST_N == SG_PROFILE_STAGES, "stage count");
+const char *const kStageNames[ST_N] = {"setup", "preprocess", "depth_sort", "pair_offsets",
+                                       "read_pairs", "duplicate", "tile_sort", "tile_ranges",
+                                       "blend_fwd", "bwd_clear", "blend_bwd", "preprocess_bwd"};
+
+struct Profiler {
+    std::mutex mu;
+    int flags = 0;
+    std::vector<cudaEvent_t> pool;
+    struct Pending { int stage; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    double ms[ST_N] = {};
+    int64_t launches[ST_N] = {};
+    int64_t evals[2] = {};
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+Profiler &prof() { static Profiler p; return p; }
+
+std::atomic<int64_t> &launch_counter() {
+    static std::atomic<int64_t> c{0};
+    return c;
+}
+
+// Brackets one stage with events when profiling is on.
+struct StageTimer {
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    StageTimer(int st, cudaStream_t stream) : stage(st), s(stream) {
+        Profiler &p = prof();
+        if (!(p.flags & SG_PROFILE_EVENTS)) return;
+        std::lock_guard<std::mutex> g(p.mu);
+        a = p.get();
+        if (a) cudaEventRecord(a, s);
+    }
+    ~StageTimer() {
+        if (!a) return;
+        Profiler &p = prof();
+        std::lock_guard<std::mutex> g(p.mu);
+        cudaEvent_t b = p.get();
+        if (!b) return;
+        cudaEventRecord(b, s);
+        p.pending.push_back({stage, a, b});
+    }
+};
+
+constexpr size_t ALIGN = 256;
+size_t al(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool dtype_ok(int dg, int dl, int ds) {
+    return (dg == SG_F32 && dl == SG_F32 && ds == SG_F32) ||
+           (dg == SG_F16 && dl == SG_F16 && (ds == SG_F16 || ds == SG_BF16));
+}
+
+int tile_bits_for(uint64_t n_tiles) {
+    if (n_tiles <= 1) return 0;
+    int b = 0;
+    while ((1ull << b) < n_tiles) ++b;
+    return b;
+}
+
+// Fills the batch table from host structs. Pointers of the scenes are
+// validated only when check_ptrs is set (the query does not need them).
+int build_batch(const sg_scene *scenes, int n_scenes, const sg_camera *cams, const int32_t *view_scene,
+                int n_views, bool check_ptrs, Batch &b) {
+    if (!scenes || !cams) return fail(SG_ERR_INVALID_ARG, "scene and cameras must not be NULL");
+    if (n_views < 1 || n_views > SG_MAX_VIEWS)
+        return fail(SG_ERR_INVALID_ARG, "n_views = %d outside [1, %d]", n_views, SG_MAX_VIEWS);
+    if (n_scenes < 1 || n_scenes > SG_MAX_SCENES)
+        return fail(SG_ERR_INVALID_ARG, "n_scenes = %d outside [1, %d]", n_scenes, SG_MAX_SCENES);
+    std::memset(&b, 0, sizeof(Batch));
+    b.n_views = n_views;
+    b.n_scenes = n_scenes;
+    uint64_t bwd_blk = 0;
+    for (int s = 0; s < n_scenes; ++s) {
+        const sg_scene &sc = scenes[s];
+        if (sc.n < 0 || sc.n > (int64_t)INT32_MAX - PRE_THREADS)
+            return fail(SG_ERR_INVALID_ARG, "scene %d: n = %lld out of range", s, (long long)sc.n);
+        if (sc.n_lobes < 0 || sc.n_lobes > (int64_t)INT32_MAX)
+            return fail(SG_ERR_INVALID_ARG, "scene %d: n_lobes = %lld out of range", s, (long long)sc.n_lobes);
+        if (!dtype_ok(sc.dtype_geom, sc.dtype_lobe, sc.dtype_sharp))
+            return fail(SG_ERR_INVALID_ARG, "scene %d: unsupported dtype combination (%d, %d, %d)", s,
+                        sc.dtype_geom, sc.dtype_lobe, sc.dtype_sharp);
+        if (s > 0 && (sc.dtype_geom != scenes[0].dtype_geom || sc.dtype_lobe != scenes[0].dtype_lobe ||
+                      sc.dtype_sharp != scenes[0].dtype_sharp))
+            return fail(SG_ERR_INVALID_ARG, "scene %d: all scenes of a call must share storage types", s);
+        if (check_ptrs && sc.n > 0) {
+            const void *req[] = {sc.means, sc.scales, sc.quats, sc.opac, sc.gmask, sc.c0, sc.lobe_off};
+            for (const void *p : req)
+                if (!p || !aligned(p, 16))
+                    return fail(SG_ERR_INVALID_ARG, "scene %d: a Gaussian array is NULL or not 16-byte aligned", s);
+        }
+        if (check_ptrs && sc.n_lobes > 0) {
+            const void *req[] = {sc.axis, sc.sharp, sc.amp, sc.lmask};
+            for (const void *p : req)
+                if (!p || !aligned(p, 16))
+                    return fail(SG_ERR_INVALID_ARG, "scene %d: a lobe array is NULL or not 16-byte aligned", s);
+        }
+        SceneDesc &d = b.scene[s];
+        d.means = sc.means; d.scales = sc.scales; d.quats = sc.quats; d.opac = sc.opac;
+        d.gmask = sc.gmask; d.c0 = sc.c0; d.lobe_off = sc.lobe_off;
+        d.axis = sc.axis; d.sharp = sc.sharp; d.amp = sc.amp; d.lmask = sc.lmask;
+        d.n = sc.n; d.n_lobes = sc.n_lobes;
+        d.dtype_geom = sc.dtype_geom; d.dtype_lobe = sc.dtype_lobe; d.dtype_sharp = sc.dtype_sharp;
+        d.blk_off = (uint32_t)bwd_blk;
+        bwd_blk += div_up((uint64_t)sc.n, PRE_THREADS);
+    }
+    uint64_t tiles = 0, pix = 0, ent = 0, blk = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const sg_camera &c = cams[v];
+        const int s = view_scene ? view_scene[v] : 0;
+        if (s < 0 || s >= n_scenes) return fail(SG_ERR_INVALID_ARG, "view %d: scene index %d", v, s);
+        if (c.width < 1 || c.height < 1 || c.width > 16 * 65535 || c.height > 16 * 65535)
+            return fail(SG_ERR_INVALID_ARG, "view %d: bad image size %dx%d", v, c.width, c.height);
+        if (!(c.fx > 0.f) || !(c.fy > 0.f) || !std::isfinite(c.fx) || !std::isfinite(c.fy) ||
+            !std::isfinite(c.cx) || !std::isfinite(c.cy) || !(c.near_plane >= 0.f))
+            return fail(SG_ERR_INVALID_ARG, "view %d: bad intrinsics", v);
+        for (int i = 0; i < 12; ++i)
+            if (!std::isfinite(c.viewmat[i])) return fail(SG_ERR_INVALID_ARG, "view %d: non-finite viewmat", v);
+        ViewDesc &d = b.view[v];
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        std::memcpy(d.V, c.viewmat, sizeof(d.V));
+        // camera centre -R^T t (FP64 on the host)
+        for (int i = 0; i < 3; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc -= (double)c.viewmat[4 * k + i] * (double)c.viewmat[4 * k + 3];
+            d.campos[i] = (float)acc;
+        }
+        d.near_plane = c.near_plane;
+        d.bg[0] = c.bg[0]; d.bg[1] = c.bg[1]; d.bg[2] = c.bg[2];
+        d.W = c.width; d.H = c.height;
+        d.tiles_x = (c.width + TILE - 1) / TILE;
+        d.tiles_y = (c.height + TILE - 1) / TILE;
+        d.scene = s;
+        d.n = (int32_t)scenes[s].n;
+        d.tile_off = (uint32_t)tiles;
+        d.blk_off = (uint32_t)blk;
+        d.pix_off = pix;
+        d.ent_off = ent;
+        tiles += (uint64_t)d.tiles_x * d.tiles_y;
+        pix += (uint64_t)c.width * c.height;
+        ent += (uint64_t)scenes[s].n;
+        blk += div_up((uint64_t)scenes[s].n, PRE_THREADS);
+    }
+    if (tiles >= (1ull << 31)) return fail(SG_ERR_INVALID_ARG, "too many tiles (%llu)", (unsigned long long)tiles);
+    if (ent >= (1ull << 32) - 1)
+        return fail(SG_ERR_INVALID_ARG, "too many (view, Gaussian) entries (%llu)", (unsigned long long)ent);
+    if (blk >= (1ull << 31) || bwd_blk >= (1ull << 31)) return fail(SG_ERR_INVALID_ARG, "too many blocks");
+    b.n_tiles = (uint32_t)tiles;
+    b.n_entries = ent;
+    b.pre_blocks = (uint32_t)blk;
+    b.bwd_blocks = (uint32_t)bwd_blk;
+    return SG_OK;
+}
+
+uint64_t n_pixels_of(const Batch &b) {
+    uint64_t p = 0;
+    for (int v = 0; v < b.n_views; ++v) p += (uint64_t)b.view[v].W * b.view[v].H;
+    return p;
+}
+
+WsLayout make_layout(const Batch &b, uint64_t cap) {
+    WsLayout L{};
+    const uint64_t M = b.n_entries, T = b.n_tiles;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
+    L.batch = take(sizeof(Batch));
+    L.counters = take(CNT_N * sizeof(uint64_t));
+    L.rec = take(M * sizeof(Rec));
+    L.tiles_touched = take(M * 4);
+    L.rect = take(M * 8);
+    L.dkey0 = take(M * 4);
+    L.dval0 = take(M * 4);
+    L.dkey1 = take(M * 4);
+    L.dval1 = take(M * 4);
+    L.offsets = take(M * 4);
+    L.ranges = take(T * 8);
+    L.fixed_end = o;
+    // pair-capacity dependent tail; the backward only reads pval_final
+    L.pval_final = take(cap * 4);
+    L.pkey_final = take(cap * 4);
+    L.pval_tmp = take(cap * 4);
+    L.pkey_tmp = take(cap * 4);
+    const uint64_t items = M > cap ? M : cap;
+    L.hist_blocks = (uint32_t)div_up(items, RS_TILE);
+    L.hist = take((size_t)RS_RADIX * L.hist_blocks * 4);
+    const uint64_t sums = div_up(items, SCAN_TILE) + div_up((uint64_t)RS_RADIX * L.hist_blocks, SCAN_TILE) + 1;
+    L.scan_sums = take(sums * 8);
+    L.total = o;
+    L.M = M;
+    L.n_tiles = T;
+    L.cap = cap;
+    L.tile_bits = tile_bits_for(T);
+    L.tile_passes = radix_passes(L.tile_bits);
+    return L;
+}
+
+uint64_t capacity_for(const Batch &b, size_t ws_bytes) {
+    if (make_layout(b, 0).total > ws_bytes) return UINT64_MAX;   // not even the fixed part
+    uint64_t lo = 0, hi = (1ull << 32) - 1;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo + 1) / 2;
+        if (make_layout(b, mid).total <= ws_bytes) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+size_t bwd_bytes(const Batch &b) {
+    return al(sizeof(Batch)) + al(CNT_N * sizeof(uint64_t)) + al(9 * b.n_entries * sizeof(float));
+}
+
+void fill_sizes(const Batch &b, const WsLayout &L, uint64_t n_pairs, sg_sizes *out) {
+    if (!out) return;
+    out->n_entries = b.n_entries;
+    out->n_tiles = b.n_tiles;
+    out->n_pixels = n_pixels_of(b);
+    out->n_pairs = n_pairs;
+    out->pair_capacity = L.cap;
+    out->ws_fixed_bytes = make_layout(b, 0).total;
+    out->ws_per_pair_bytes = 17;
+    out->ws_bytes = L.total;
+    out->bwd_ws_bytes = bwd_bytes(b);
+}
+
+int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, const int32_t *view_scene,
+                 int n_views, void *ws, size_t ws_bytes, float *img, float *T_final, int32_t *last,
+                 sg_sizes *out, cudaStream_t stream) {
+    std::unique_ptr<Batch> hb(new Batch);
+    int st = build_batch(scenes, n_scenes, cams, view_scene, n_views, true, *hb);
+    if (st != SG_OK) return st;
+    const Batch &b = *hb;
+    if (!img || !T_final || !last) return fail(SG_ERR_INVALID_ARG, "output pointers must not be NULL");
+    if (!aligned(img, 16) || !aligned(T_final, 16) || !aligned(last, 16))
+        return fail(SG_ERR_INVALID_ARG, "outputs must be 16-byte aligned");
+    if (!ws || !aligned(ws, ALIGN)) return fail(SG_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+    const uint64_t cap = capacity_for(b, ws_bytes);
+    if (cap == UINT64_MAX) {
+        WsLayout L0 = make_layout(b, 0);
+        fill_sizes(b, L0, 0, out);
+        return fail(SG_ERR_WORKSPACE, "workspace of %zu bytes is below the fixed part (%zu bytes)", ws_bytes,
+                    L0.total);
+    }
+    const WsLayout L = make_layout(b, cap);
+    char *w = static_cast<char *>(ws);
+    Batch *db = reinterpret_cast<Batch *>(w + L.batch);
+    uint64_t *counters = reinterpret_cast<uint64_t *>(w + L.counters);
+    Rec *rec = reinterpret_cast<Rec *>(w + L.rec);
+    uint32_t *tt = reinterpret_cast<uint32_t *>(w + L.tiles_touched);
+    uint2 *rect = reinterpret_cast<uint2 *>(w + L.rect);
+    uint32_t *dkey0 = reinterpret_cast<uint32_t *>(w + L.dkey0);
+    uint32_t *dval0 = reinterpret_cast<uint32_t *>(w + L.dval0);
+    uint32_t *dkey1 = reinterpret_cast<uint32_t *>(w + L.dkey1);
+    uint32_t *dval1 = reinterpret_cast<uint32_t *>(w + L.dval1);
+    uint32_t *offs = reinterpret_cast<uint32_t *>(w + L.offsets);
+    uint2 *ranges = reinterpret_cast<uint2 *>(w + L.ranges);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(w + L.hist);
+    uint64_t *sums = reinterpret_cast<uint64_t *>(w + L.scan_sums);
+    const uint64_t M = L.M;
+
+    const bool counting = (prof().flags & SG_PROFILE_COUNT) != 0;
+    {
+        StageTimer t(ST_SETUP, stream);
+        SG_CUDA(launch_setup(b, db, counters, stream), "setup");
+    }
+    {
+        StageTimer t(ST_PRE, stream);
+        SG_CUDA(launch_preprocess(b, db, rec, tt, rect, dkey0, dval0, stream), "preprocessSG");
+    }
+    {
+        // depth digits, once per entry (result back in dkey0/dval0 after 4 passes)
+        StageTimer t(ST_DEPTH_SORT, stream);
+        SG_CUDA(launch_radix_sort(dkey0, dval0, dkey1, dval1, counters + CNT_ENTRIES, M, 32, hist, sums,
+                                  stream),
+                "depth sort");
+    }
+    {
+        StageTimer t(ST_OFFSETS, stream);
+        SG_CUDA(launch_scan(tt, dval0, offs, M, sums, counters + CNT_PAIRS, stream), "pair offsets");
+    }
+    uint64_t K = 0;
+    {
+        StageTimer t(ST_READ_PAIRS, stream);
+        SG_CUDA(cudaMemcpyAsync(&K, counters + CNT_PAIRS, sizeof(K), cudaMemcpyDeviceToHost, stream),
+                "read pairs");
+    }
+    SG_CUDA(cudaStreamSynchronize(stream), "read pairs");
+    if (K > cap || K >= (1ull << 32) - 1) {
+        const WsLayout need = make_layout(b, K);
+        fill_sizes(b, need, K, out);
+        return fail(SG_ERR_CAPACITY, "%llu pairs exceed the workspace capacity %llu (need %zu bytes)",
+                    (unsigned long long)K, (unsigned long long)cap, need.total);
+    }
+    // duplicate into the buffer from which an even/odd number of tile passes ends in *_final
+    uint32_t *pk_final = reinterpret_cast<uint32_t *>(w + L.pkey_final);
+    uint32_t *pv_final = reinterpret_cast<uint32_t *>(w + L.pval_final);
+    uint32_t *pk_tmp = reinterpret_cast<uint32_t *>(w + L.pkey_tmp);
+    uint32_t *pv_tmp = reinterpret_cast<uint32_t *>(w + L.pval_tmp);
+    const bool even = (L.tile_passes % 2) == 0;
+    uint32_t *k0 = even ? pk_final : pk_tmp, *v0 = even ? pv_final : pv_tmp;
+    uint32_t *k1 = even ? pk_tmp : pk_final, *v1 = even ? pv_tmp : pv_final;
+    {
+        StageTimer t(ST_DUPLICATE, stream);
+        SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, offs, counters, cap, k0, v0, n_views, stream),
+                "duplicateWithKeys");
+    }
+    {
+        StageTimer t(ST_TILE_SORT, stream);
+        SG_CUDA(launch_radix_sort(k0, v0, k1, v1, counters + CNT_PAIRS, K, L.tile_bits, hist, sums, stream),
+                "tile sort");
+    }
+    {
+        StageTimer t(ST_RANGES, stream);
+        SG_CUDA(launch_ranges(pk_final, counters, K, ranges, L.n_tiles, stream), "tile ranges");
+    }
+    unsigned long long *evals = counting ? reinterpret_cast<unsigned long long *>(counters + 3) : nullptr;
+    if (counting) SG_CUDA(cudaMemsetAsync(evals, 0, 8, stream), "clear counter");
+    {
+        StageTimer t(ST_BLEND_FWD, stream);
+        SG_CUDA(launch_blend_forward(db, b.n_tiles, ranges, pv_final, rec, img, T_final, last, n_views, evals,
+                                     stream),
+                "blend forward");
+    }
+    if (counting) {
+        uint64_t ne = 0;
+        SG_CUDA(cudaMemcpyAsync(&ne, evals, 8, cudaMemcpyDeviceToHost, stream), "read counter");
+        SG_CUDA(cudaStreamSynchronize(stream), "read counter");
+        std::lock_guard<std::mutex> g(prof().mu);
+        prof().evals[0] += (int64_t)ne;
+    }
+    fill_sizes(b, L, K, out);
+    return SG_OK;
+}
+
+int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, const int32_t *view_scene,
+                  int n_views, const void *ws, size_t ws_bytes, const float *T_final, const int32_t *last,
+                  const float *d_img, void *bwd_ws, size_t bwd_ws_bytes, const sg_grads *grads,
+                  cudaStream_t stream) {
+    std::unique_ptr<Batch> hb(new Batch);
+    int st = build_batch(scenes, n_scenes, cams, view_scene, n_views, true, *hb);
+    if (st != SG_OK) return st;
+    Batch &b = *hb;
+    if (!grads) return fail(SG_ERR_INVALID_ARG, "grads must not be NULL");
+    for (int s = 0; s < n_scenes; ++s) b.scene[s].grads = grads[s];
+    if (!T_final || !last || !d_img) return fail(SG_ERR_INVALID_ARG, "T_final, last and d_img must not be NULL");
+    if (!ws || !aligned(ws, ALIGN)) return fail(SG_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+    if (!bwd_ws || !aligned(bwd_ws, ALIGN))
+        return fail(SG_ERR_INVALID_ARG, "backward scratch NULL or not 256-byte aligned");
+    if (bwd_ws_bytes < bwd_bytes(b))
+        return fail(SG_ERR_WORKSPACE, "backward scratch of %zu bytes, %zu needed", bwd_ws_bytes, bwd_bytes(b));
+    const uint64_t cap = capacity_for(b, ws_bytes);
+    if (cap == UINT64_MAX) return fail(SG_ERR_WORKSPACE, "workspace smaller than its fixed part");
+    const WsLayout L = make_layout(b, cap);
+    const char *w = static_cast<const char *>(ws);
+    const Rec *rec = reinterpret_cast<const Rec *>(w + L.rec);
+    const uint32_t *tt = reinterpret_cast<const uint32_t *>(w + L.tiles_touched);
+    const uint2 *ranges = reinterpret_cast<const uint2 *>(w + L.ranges);
+    const uint32_t *pv_final = reinterpret_cast<const uint32_t *>(w + L.pval_final);
+    char *bw = static_cast<char *>(bwd_ws);
+    Batch *db = reinterpret_cast<Batch *>(bw);
+    uint64_t *counters = reinterpret_cast<uint64_t *>(bw + al(sizeof(Batch)));
+    float *dg = reinterpret_cast<float *>(bw + al(sizeof(Batch)) + al(CNT_N * sizeof(uint64_t)));
+    const uint64_t M = L.M;
+
+    const bool counting = (prof().flags & SG_PROFILE_COUNT) != 0;
+    unsigned long long *evals = counting ? reinterpret_cast<unsigned long long *>(counters + 3) : nullptr;
+    {
+        StageTimer t(ST_SETUP, stream);
+        SG_CUDA(launch_setup(b, db, counters, stream), "setup");
+    }
+    {
+        StageTimer t(ST_BWD_CLEAR, stream);
+        if (M > 0) SG_CUDA(cudaMemsetAsync(dg, 0, 9 * M * sizeof(float), stream), "clear 2D gradients");
+    }
+    {
+        StageTimer t(ST_BLEND_BWD, stream);
+        SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M,
+                                      n_views, evals, stream),
+                "blend backward");
+    }
+    {
+        StageTimer t(ST_PRE_BWD, stream);
+        SG_CUDA(launch_preprocess_backward(b, db, tt, dg, M, stream), "preprocess backward");
+    }
+    if (counting) {
+        uint64_t ne = 0;
+        SG_CUDA(cudaMemcpyAsync(&ne, evals, 8, cudaMemcpyDeviceToHost, stream), "read counter");
+        SG_CUDA(cudaStreamSynchronize(stream), "read counter");
+        std::lock_guard<std::mutex> g(prof().mu);
+        prof().evals[1] += (int64_t)ne;
+    }
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sg_profile_enable(int flags) {
+    Profiler &p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.flags = flags & (SG_PROFILE_EVENTS | SG_PROFILE_COUNT);
+    return SG_OK;
+}
+
+int sg_profile_read(double *ms, int64_t *launches, int64_t *pair_evals, int reset) {
+    Profiler &p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    int rc = SG_OK;
+    for (auto &q : p.pending) {
+        cudaError_t e = cudaEventSynchronize(q.b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, q.a, q.b);
+        if (e != cudaSuccess) rc = cuda_fail(e, "profile read");
+        p.ms[q.stage] += t;
+        p.launches[q.stage] += 1;
+        p.pool.push_back(q.a);
+        p.pool.push_back(q.b);
+    }
+    p.pending.clear();
+    for (int i = 0; i < ST_N; ++i) {
+        if (ms) ms[i] = p.ms[i];
+        if (launches) launches[i] = p.launches[i];
+    }
+    if (pair_evals) { pair_evals[0] = p.evals[0]; pair_evals[1] = p.evals[1]; }
+    if (reset) {
+        for (int i = 0; i < ST_N; ++i) { p.ms[i] = 0.0; p.launches[i] = 0; }
+        p.evals[0] = p.evals[1] = 0;
+    }
+    return rc;
+}
+
+int64_t sg_kernel_launches(void) { return launch_counter().load(); }
+
+const char *sg_profile_stage_name(int i) { return (i >= 0 && i < ST_N) ? kStageNames[i] : nullptr; }
+
+int sg_version(void) { return SG_ABI_VERSION; }
+
+const char *sg_last_error(void) { return g_err; }
+
+int sg_workspace_query(const sg_scene *scene, const sg_camera *cams, int n_views, uint64_t pair_capacity,
+                       sg_sizes *out) {
+    if (!out) return fail(SG_ERR_INVALID_ARG, "out must not be NULL");
+    std::unique_ptr<Batch> hb(new Batch);
+    int st = build_batch(scene, 1, cams, nullptr, n_views, false, *hb);
+    if (st != SG_OK) return st;
+    if (pair_capacity >= (1ull << 32) - 1) return fail(SG_ERR_INVALID_ARG, "pair capacity too large");
+    const WsLayout L = make_layout(*hb, pair_capacity);
+    fill_sizes(*hb, L, 0, out);
+    return SG_OK;
+}
+
+int sg_workspace_layout(const sg_scene *scene, const sg_camera *cams, int n_views, size_t ws_bytes,
+                        sg_ws_layout *out) {
+    if (!out) return fail(SG_ERR_INVALID_ARG, "out must not be NULL");
+    std::unique_ptr<Batch> hb(new Batch);
+    int st = build_batch(scene, 1, cams, nullptr, n_views, false, *hb);
+    if (st != SG_OK) return st;
+    const uint64_t cap = capacity_for(*hb, ws_bytes);
+    if (cap == UINT64_MAX) return fail(SG_ERR_WORKSPACE, "workspace smaller than its fixed part");
+    const WsLayout L = make_layout(*hb, cap);
+    out->rec = L.rec;
+    out->tiles_touched = L.tiles_touched;
+    out->rect = L.rect;
+    out->depth_order = L.dval0;
+    out->ranges = L.ranges;
+    out->pair_tile = L.pkey_final;
+    out->pair_entry = L.pval_final;
+    out->total_bytes = L.total;
+    return SG_OK;
+}
+
+int sg_render_forward(const sg_scene *scene, const sg_camera *cams, int n_views, void *ws, size_t ws_bytes,
+                      float *img, float *T_final, int32_t *last, sg_sizes *out, void *stream) {
+    g_err[0] = '\0';
+    return forward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, img, T_final, last, out,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int sg_render_backward(const sg_scene *scene, const sg_camera *cams, int n_views, const void *ws,
+                       size_t ws_bytes, const float *T_final, const int32_t *last, const float *d_img,
+                       void *bwd_ws, size_t bwd_ws_bytes, const sg_grads *grads, void *stream) {
+    g_err[0] = '\0';
+    return backward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, T_final, last, d_img, bwd_ws,
+                         bwd_ws_bytes, grads, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal declarations shared by the kernel translation units of the
+// SG-splatting rasterizer (sm_103a). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/sgsplat.h"
+
+namespace sgk {
+
+constexpr int TILE = SG_TILE;             // 16x16 pixel tiles
+constexpr int BLEND_THREADS = TILE * TILE;
+constexpr int PRE_THREADS = 256;
+
+// Per-view camera and packing offsets. Built on the host, copied into the
+// workspace by k_setup so that kernels take a single pointer.
+struct ViewDesc {
+    float fx, fy, cx, cy;
+    float V[12];          // world->camera [R|t], row-major
+    float campos[3];      // camera centre in world space (-R^T t)
+    float near_plane;
+    float bg[3];
+    int32_t W, H, tiles_x, tiles_y;
+    int32_t scene;        // index into Batch::scene
+    int32_t n;            // Gaussians of that scene
+    uint32_t tile_off;    // first global tile id of the view
+    uint32_t blk_off;     // first preprocess block of the view
+    uint32_t pad0;
+    uint64_t pix_off;     // first pixel of the view in T_final / last (img: x3)
+    uint64_t ent_off;     // first (view, Gaussian) entry of the view
+};
+
+struct SceneDesc {
+    const void *means, *scales, *quats, *opac;
+    const float *gmask, *c0;
+    const int32_t *lobe_off;
+    const void *axis, *sharp, *amp;
+    const float *lmask;
+    sg_grads grads;
+    int64_t n, n_lobes;
+    int32_t dtype_geom, dtype_lobe, dtype_sharp;
+    uint32_t blk_off;     // first preprocess-backward block of the scene
+};
+
+struct Batch {
+    int32_t n_views, n_scenes;
+    uint32_t n_tiles;
+    uint32_t pre_blocks;
+    uint32_t bwd_blocks;
+    uint32_t pad0;
+    uint64_t n_entries;
+    ViewDesc view[SG_MAX_VIEWS];
+    SceneDesc scene[SG_MAX_SCENES];
+};
+
+// One projected Gaussian as the blend reads it: 48 bytes, two 32-byte sectors.
+struct __align__(16) Rec {
+    float4 a;   // x, y, conic A, conic B
+    float4 b;   // conic C, o' = m_g * o, r, g
+    float4 c;   // b, unused x3
+};
+
+// Device counters kept in the workspace.
+enum : int { CNT_ENTRIES = 0, CNT_PAIRS = 1, CNT_STATUS = 2, CNT_N = 4 };
+
+// Radix sort / scan geometry.
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;   // 4096 keys per block
+constexpr int RS_RADIX = 256;
+constexpr int SCAN_TILE = 4096;
+
+// Byte offsets of every workspace buffer (host computed, identical for the
+// forward and the backward of one call).
+struct WsLayout {
+    size_t batch, counters, rec, tiles_touched, rect, dkey0, dval0, dkey1, dval1,
+        offsets, ranges, scan_sums, hist, fixed_end;
+    size_t pval_final, pkey_final, pval_tmp, pkey_tmp, total;
+    uint64_t M, n_tiles, cap;
+    uint32_t hist_blocks;     // radix blocks of the larger sort
+    int tile_bits, tile_passes;
+};
+
+__host__ __device__ inline uint64_t div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// Process-wide count of kernels this library has launched (sg_kernel_launches).
+void count_launches(int n);
+
+// ---- launchers (host side, defined in the .cu files) ----
+cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStream_t s);
+cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32_t *tiles_touched,
+                              uint2 *rect, uint32_t *dkey, uint32_t *dval, cudaStream_t s);
+cudaError_t launch_preprocess_backward(const Batch &hb, const Batch *db,
+                                       const uint32_t *tiles_touched, const float *dg,
+                                       uint64_t M, cudaStream_t s);
+
+// Exclusive scan of `in` (or of tiles_touched[idx[i]] when idx != null) into
+// `out`, total written to *total. n items (host known).
+cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t *out,
+                        uint64_t n, uint64_t *block_sums, uint64_t *total, cudaStream_t s);
+
+// Stable LSD radix sort of (key, val) u32 pairs on bits [0, bits); item count read
+// from *n_dev, at most max_n. Ping-pongs between (k0,v0) and (k1,v1); the
+// sorted result ends in (k0,v0) when the pass count is even, else in (k1,v1).
+cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
+                              const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
+                              uint64_t *scan_sums, cudaStream_t s);
+int radix_passes(int bits);
+
+cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,
+                             const uint32_t *tiles_touched, const uint2 *rect,
+                             const uint32_t *offsets, const uint64_t *counters, uint64_t cap,
+                             uint32_t *pkey, uint32_t *pval, int n_views, cudaStream_t s);
+cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64_t cap,
+                          uint2 *ranges, uint64_t n_tiles, cudaStream_t s);
+
+cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
+                                 const uint32_t *pval, const Rec *rec, float *img,
+                                 float *T_final, int32_t *last, int n_views,
+                                 unsigned long long *evals, cudaStream_t s);
+cudaError_t launch_blend_backward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
+                                  const uint32_t *pval, const Rec *rec, const float *T_final,
+                                  const int32_t *last, const float *d_img, float *dg,
+                                  uint64_t M, int n_views, unsigned long long *evals,
+                                  cudaStream_t s);
+
+}  // namespace sgk

@@ -1,0 +1,549 @@
+// preprocessSG (forward) and its adjoint.
+//
+// Forward, one thread per (view, Gaussian): EWA projection of the 3D Gaussian
+// (Sec. 3.1) with a 0.3 px low-pass dilation, conic, 3-sigma radius, tile
+// rectangle, depth key, and the view-dependent SG colour of Eq. 2 with the
+// soft-pruning masks. Every quantity that decides an integer (cull, radius,
+// tile rectangle, depth key) is computed with a fixed binary32 recipe:
+// one IEEE round-to-nearest operation per step in a written order, no fused
+// multiply-add, so it is reproducible off the GPU.
+//
+// Backward, one thread per Gaussian of a scene, looping over the views of
+// that scene: chains dL/d(centre, conic, o', rgb) of each view back to every
+// scene input and writes the sums (no atomics).
+#include "sg_internal.cuh"
+
+namespace sgk {
+
+// ---------------------------------------------------------------------------
+// parameter loads (storage type -> binary32)
+// ---------------------------------------------------------------------------
+template <int DT>
+__device__ __forceinline__ float ldp(const void *p, int64_t i);
+template <>
+__device__ __forceinline__ float ldp<SG_F32>(const void *p, int64_t i) {
+    return __ldg(static_cast<const float *>(p) + i);
+}
+template <>
+__device__ __forceinline__ float ldp<SG_F16>(const void *p, int64_t i) {
+    return __half2float(static_cast<const __half *>(p)[i]);
+}
+template <>
+__device__ __forceinline__ float ldp<SG_BF16>(const void *p, int64_t i) {
+    return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]);
+}
+
+// exactly rounded binary32 steps (never contracted into FMA)
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
+
+__device__ __forceinline__ int clamp_tile(float f, int n) {
+    // floor'ed tile coordinate -> [0, n]; NaN -> 0
+    if (f >= (float)n) return n;
+    if (f > 0.f) return (int)f;
+    return 0;
+}
+
+struct Geo {
+    // camera-space centre
+    float tx, ty, tz;
+    // normalised quaternion and rotation
+    float qw, qx, qy, qz, invq;
+    float R[3][3];
+    float M[3][3];      // R * diag(s)
+    float S[3][3];      // Sigma_3D
+    float ux, uy;       // t_x / t_z, t_y / t_z
+    float ccx, ccy;     // guard-band clamped x, y
+    float j00, j02, j11, j12;
+    float A[2][3];      // J * W
+    float ca, cb, cc;   // Sigma_2D entries after dilation
+    float det;
+    float conA, conB, conC;
+    float x, y;         // projected centre (pixel index coordinates)
+    float rf;           // radius (float)
+    int x0, y0, x1, y1; // tile rectangle, half open
+    float op;           // o' = m_g * o
+    bool visible;
+};
+
+// The binary32 decision recipe. Fills every field of g.
+__device__ __forceinline__ void project_recipe(const ViewDesc &vw, float px, float py, float pz,
+                                               float s0, float s1, float s2, float q0, float q1,
+                                               float q2, float q3, float opac, float gmask,
+                                               Geo &g) {
+    const float *V = vw.V;
+    g.tx = fa(fa(fa(fm(V[0], px), fm(V[1], py)), fm(V[2], pz)), V[3]);
+    g.ty = fa(fa(fa(fm(V[4], px), fm(V[5], py)), fm(V[6], pz)), V[7]);
+    g.tz = fa(fa(fa(fm(V[8], px), fm(V[9], py)), fm(V[10], pz)), V[11]);
+    const bool near_ok = g.tz > vw.near_plane;
+
+    const float n2 = fa(fa(fa(fm(q0, q0), fm(q1, q1)), fm(q2, q2)), fm(q3, q3));
+    g.invq = fdv(1.f, fsq(n2));
+    const float w = fm(q0, g.invq), x = fm(q1, g.invq), y = fm(q2, g.invq), z = fm(q3, g.invq);
+    g.qw = w; g.qx = x; g.qy = y; g.qz = z;
+    g.R[0][0] = fs(1.f, fm(2.f, fa(fm(y, y), fm(z, z))));
+    g.R[0][1] = fm(2.f, fs(fm(x, y), fm(w, z)));
+    g.R[0][2] = fm(2.f, fa(fm(x, z), fm(w, y)));
+    g.R[1][0] = fm(2.f, fa(fm(x, y), fm(w, z)));
+    g.R[1][1] = fs(1.f, fm(2.f, fa(fm(x, x), fm(z, z))));
+    g.R[1][2] = fm(2.f, fs(fm(y, z), fm(w, x)));
+    g.R[2][0] = fm(2.f, fs(fm(x, z), fm(w, y)));
+    g.R[2][1] = fm(2.f, fa(fm(y, z), fm(w, x)));
+    g.R[2][2] = fs(1.f, fm(2.f, fa(fm(x, x), fm(y, y))));
+    const float s[3] = {s0, s1, s2};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) g.M[i][j] = fm(g.R[i][j], s[j]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            g.S[i][j] = fa(fa(fm(g.M[i][0], g.M[j][0]), fm(g.M[i][1], g.M[j][1])),
+                           fm(g.M[i][2], g.M[j][2]));
+            g.S[j][i] = g.S[i][j];
+        }
+
+    const float fx = vw.fx, fy = vw.fy;
+    const float tanx = fdv(fm(0.5f, (float)vw.W), fx);
+    const float tany = fdv(fm(0.5f, (float)vw.H), fy);
+    const float limx = fm(1.3f, tanx), limy = fm(1.3f, tany);
+    g.ux = fdv(g.tx, g.tz);
+    g.uy = fdv(g.ty, g.tz);
+    g.ccx = fm(fminf(limx, fmaxf(-limx, g.ux)), g.tz);
+    g.ccy = fm(fminf(limy, fmaxf(-limy, g.uy)), g.tz);
+    const float tz2 = fm(g.tz, g.tz);
+    g.j00 = fdv(fx, g.tz);
+    g.j11 = fdv(fy, g.tz);
+    g.j02 = -fdv(fm(fx, g.ccx), tz2);
+    g.j12 = -fdv(fm(fy, g.ccy), tz2);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        g.A[0][j] = fa(fm(g.j00, V[0 + j]), fm(g.j02, V[8 + j]));
+        g.A[1][j] = fa(fm(g.j11, V[4 + j]), fm(g.j12, V[8 + j]));
+    }
+    float B[2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            B[i][j] = fa(fa(fm(g.A[i][0], g.S[0][j]), fm(g.A[i][1], g.S[1][j])),
+                         fm(g.A[i][2], g.S[2][j]));
+    g.ca = fa(fa(fa(fm(B[0][0], g.A[0][0]), fm(B[0][1], g.A[0][1])), fm(B[0][2], g.A[0][2])), 0.3f);
+    g.cb = fa(fa(fm(B[0][0], g.A[1][0]), fm(B[0][1], g.A[1][1])), fm(B[0][2], g.A[1][2]));
+    g.cc = fa(fa(fa(fm(B[1][0], g.A[1][0]), fm(B[1][1], g.A[1][1])), fm(B[1][2], g.A[1][2])), 0.3f);
+    g.det = fs(fm(g.ca, g.cc), fm(g.cb, g.cb));
+    const bool det_ok = g.det > 0.f;
+    g.conA = fdv(g.cc, g.det);
+    g.conB = -fdv(g.cb, g.det);
+    g.conC = fdv(g.ca, g.det);
+    const float mid = fm(0.5f, fa(g.ca, g.cc));
+    const float lam1 = fa(mid, fsq(fmaxf(0.1f, fs(fm(mid, mid), g.det))));
+    g.rf = ceilf(fm(3.f, fsq(lam1)));
+    g.x = fs(fa(fm(fx, g.ux), vw.cx), 0.5f);
+    g.y = fs(fa(fm(fy, g.uy), vw.cy), 0.5f);
+    g.x0 = clamp_tile(floorf(fdv(fs(g.x, g.rf), 16.f)), vw.tiles_x);
+    g.x1 = clamp_tile(floorf(fdv(fa(fa(g.x, g.rf), 15.f), 16.f)), vw.tiles_x);
+    g.y0 = clamp_tile(floorf(fdv(fs(g.y, g.rf), 16.f)), vw.tiles_y);
+    g.y1 = clamp_tile(floorf(fdv(fa(fa(g.y, g.rf), 15.f), 16.f)), vw.tiles_y);
+    const bool area_ok = (g.x1 > g.x0) && (g.y1 > g.y0);
+    g.op = fm(gmask, opac);
+    const bool op_ok = g.op >= (1.0f / 255.0f);
+    const bool finite = isfinite(g.x) && isfinite(g.y) && isfinite(g.rf) && isfinite(g.conA) &&
+                        isfinite(g.conB) && isfinite(g.conC);
+    g.visible = near_ok && det_ok && area_ok && op_ok && finite;
+}
+
+template <int DG>
+__device__ __forceinline__ void load_geo(const SceneDesc &sc, int64_t g, float &px, float &py,
+                                         float &pz, float &s0, float &s1, float &s2, float &q0,
+                                         float &q1, float &q2, float &q3, float &o) {
+    const int64_t n = sc.n;
+    px = ldp<DG>(sc.means, g);
+    py = ldp<DG>(sc.means, n + g);
+    pz = ldp<DG>(sc.means, 2 * n + g);
+    s0 = ldp<DG>(sc.scales, g);
+    s1 = ldp<DG>(sc.scales, n + g);
+    s2 = ldp<DG>(sc.scales, 2 * n + g);
+    q0 = ldp<DG>(sc.quats, g);
+    q1 = ldp<DG>(sc.quats, n + g);
+    q2 = ldp<DG>(sc.quats, 2 * n + g);
+    q3 = ldp<DG>(sc.quats, 3 * n + g);
+    o = ldp<DG>(sc.opac, g);
+}
+
+__device__ __forceinline__ int find_block_view(const Batch &b, uint32_t blk) {
+    int lo = 0, hi = b.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.view[mid].blk_off <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_block_scene(const Batch &b, uint32_t blk) {
+    int lo = 0, hi = b.n_scenes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.scene[mid].blk_off <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// setup: copy the batch table into the workspace, seed the counters
+// ---------------------------------------------------------------------------
+__global__ void k_setup(const Batch b, Batch *dst, uint64_t *counters) {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&b);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    constexpr int words = sizeof(Batch) / 4;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = src[i];
+    if (threadIdx.x == 0) {
+        counters[CNT_ENTRIES] = b.n_entries;
+        counters[CNT_PAIRS] = 0;
+        counters[CNT_STATUS] = 0;
+        counters[3] = 0;
+    }
+}
+
+cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStream_t s) {
+    static_assert(sizeof(Batch) % 4 == 0, "batch size");
+    static_assert(sizeof(Batch) < 32000, "batch must fit the kernel parameter space");
+    k_setup<<<1, 256, 0, s>>>(b, dst, counters);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K1 preprocessSG
+// ---------------------------------------------------------------------------
+template <int DG, int DL, int DS>
+__global__ void __launch_bounds__(PRE_THREADS)
+k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__restrict__ tiles_touched,
+             uint2 *__restrict__ rect, uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
+    const Batch &b = *bp;
+    const int v = find_block_view(b, blockIdx.x);
+    const ViewDesc &vw = b.view[v];
+    const SceneDesc &sc = b.scene[vw.scene];
+    const int64_t g = (int64_t)(blockIdx.x - vw.blk_off) * PRE_THREADS + threadIdx.x;
+    if (g >= vw.n) return;
+    const uint64_t e = vw.ent_off + (uint64_t)g;
+
+    float px, py, pz, s0, s1, s2, q0, q1, q2, q3, o;
+    load_geo<DG>(sc, g, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o);
+    const float gm = __ldg(sc.gmask + g);
+    Geo G;
+    project_recipe(vw, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o, gm, G);
+    if (!G.visible) {
+        tiles_touched[e] = 0u;
+        rect[e] = make_uint2(0u, 0u);
+        dkey[e] = 0xFFFFFFFFu;
+        dval[e] = (uint32_t)e;
+        return;
+    }
+
+    // SG colour (Eq. 2): view direction from the camera centre to the Gaussian
+    float dx = px - vw.campos[0], dy = py - vw.campos[1], dz = pz - vw.campos[2];
+    const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv; dy *= inv; dz *= inv;
+    const int64_t n = sc.n, L = sc.n_lobes;
+    float cr = __ldg(sc.c0 + g), cg = __ldg(sc.c0 + n + g), cbl = __ldg(sc.c0 + 2 * n + g);
+    // CSR bounds clamped to [0, L] so a malformed lobe_off cannot read out of range
+    const int hi = min(__ldg(sc.lobe_off + g + 1), (int)L);
+    const int lo = max(0, min(__ldg(sc.lobe_off + g), hi));
+    for (int k = lo; k < hi; ++k) {
+        const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
+                    az = ldp<DL>(sc.axis, 2 * L + k);
+        const float ia = 1.0f / sqrtf(ax * ax + ay * ay + az * az);
+        const float dot = (ax * dx + ay * dy + az * dz) * ia;
+        const float sh = ldp<DS>(sc.sharp, k);
+        const float wgt = __ldg(sc.lmask + k) * expf(sh * (dot - 1.0f));
+        cr += wgt * ldp<DL>(sc.amp, k);
+        cg += wgt * ldp<DL>(sc.amp, L + k);
+        cbl += wgt * ldp<DL>(sc.amp, 2 * L + k);
+    }
+    Rec r;
+    r.a = make_float4(G.x, G.y, G.conA, G.conB);
+    r.b = make_float4(G.conC, G.op, fmaxf(cr, 0.f), fmaxf(cg, 0.f));
+    r.c = make_float4(fmaxf(cbl, 0.f), G.rf, G.tz, 0.f);
+    rec[e] = r;
+    tiles_touched[e] = (uint32_t)((G.x1 - G.x0) * (G.y1 - G.y0));
+    rect[e] = make_uint2((uint32_t)G.x0 | ((uint32_t)G.x1 << 16), (uint32_t)G.y0 | ((uint32_t)G.y1 << 16));
+    dkey[e] = __float_as_uint(G.tz);
+    dval[e] = (uint32_t)e;
+}
+
+template <int DG, int DL, int DS>
+static cudaError_t launch_pre_t(const Batch &hb, const Batch *db, Rec *rec, uint32_t *tt, uint2 *rect,
+                                uint32_t *dkey, uint32_t *dval, cudaStream_t s) {
+    if (hb.pre_blocks == 0) return cudaSuccess;
+    k_preprocess<DG, DL, DS><<<hb.pre_blocks, PRE_THREADS, 0, s>>>(db, rec, tt, rect, dkey, dval);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32_t *tiles_touched,
+                              uint2 *rect, uint32_t *dkey, uint32_t *dval, cudaStream_t s) {
+    // all scenes of one call share storage types (checked by the API layer)
+    const SceneDesc &sc = hb.scene[0];
+    const int key = sc.dtype_geom * 9 + sc.dtype_lobe * 3 + sc.dtype_sharp;
+    switch (key) {
+        case SG_F32 * 9 + SG_F32 * 3 + SG_F32:
+            return launch_pre_t<SG_F32, SG_F32, SG_F32>(hb, db, rec, tiles_touched, rect, dkey, dval, s);
+        case SG_F16 * 9 + SG_F16 * 3 + SG_F16:
+            return launch_pre_t<SG_F16, SG_F16, SG_F16>(hb, db, rec, tiles_touched, rect, dkey, dval, s);
+        case SG_F16 * 9 + SG_F16 * 3 + SG_BF16:
+            return launch_pre_t<SG_F16, SG_F16, SG_BF16>(hb, db, rec, tiles_touched, rect, dkey, dval, s);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K8 preprocess backward
+// ---------------------------------------------------------------------------
+// dg layout: planar [9][M]: dx, dy, dA, dB, dC, do', dr, dg, db per entry.
+template <int DG, int DL, int DS>
+__global__ void __launch_bounds__(PRE_THREADS)
+k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tiles_touched,
+                 const float *__restrict__ dg, uint64_t M) {
+    const Batch &b = *bp;
+    const int si = find_block_scene(b, blockIdx.x);
+    const SceneDesc &sc = b.scene[si];
+    const int64_t g = (int64_t)(blockIdx.x - sc.blk_off) * PRE_THREADS + threadIdx.x;
+    if (g >= sc.n) return;
+    const int64_t n = sc.n, L = sc.n_lobes;
+
+    float px, py, pz, s0, s1, s2, q0, q1, q2, q3, o;
+    load_geo<DG>(sc, g, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o);
+    const float gm = __ldg(sc.gmask + g);
+    const float c00 = __ldg(sc.c0 + g), c01 = __ldg(sc.c0 + n + g), c02 = __ldg(sc.c0 + 2 * n + g);
+    const int hi = min(__ldg(sc.lobe_off + g + 1), (int)L);
+    const int lo = max(0, min(__ldg(sc.lobe_off + g), hi));
+
+    float d_mean[3] = {0.f, 0.f, 0.f}, d_scale[3] = {0.f, 0.f, 0.f}, d_q[4] = {0.f, 0.f, 0.f, 0.f};
+    float d_opac = 0.f, d_gmask = 0.f, d_c0[3] = {0.f, 0.f, 0.f};
+    bool first = true;   // first visible view writes lobe gradients, later views add
+
+    for (int v = 0; v < b.n_views; ++v) {
+        const ViewDesc &vw = b.view[v];
+        if (vw.scene != si) continue;
+        const uint64_t e = vw.ent_off + (uint64_t)g;
+        if (tiles_touched[e] == 0u) continue;
+        const float gx = dg[e], gy = dg[M + e], gA = dg[2 * M + e], gB = dg[3 * M + e],
+                    gC = dg[4 * M + e], gop = dg[5 * M + e];
+        const float grgb[3] = {dg[6 * M + e], dg[7 * M + e], dg[8 * M + e]};
+
+        Geo G;
+        project_recipe(vw, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o, gm, G);
+
+        // o' = m_g * o
+        d_opac += gm * gop;
+        d_gmask += o * gop;
+
+        // ---- colour (Eq. 2) ----
+        float vx = px - vw.campos[0], vy = py - vw.campos[1], vz = pz - vw.campos[2];
+        const float dn = sqrtf(vx * vx + vy * vy + vz * vz);
+        const float idn = 1.0f / dn;
+        vx *= idn; vy *= idn; vz *= idn;
+        float col[3] = {c00, c01, c02};
+        for (int k = lo; k < hi; ++k) {
+            const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
+                        az = ldp<DL>(sc.axis, 2 * L + k);
+            const float ia = 1.0f / sqrtf(ax * ax + ay * ay + az * az);
+            const float dot = (ax * vx + ay * vy + az * vz) * ia;
+            const float wgt = __ldg(sc.lmask + k) * expf(ldp<DS>(sc.sharp, k) * (dot - 1.0f));
+            col[0] += wgt * ldp<DL>(sc.amp, k);
+            col[1] += wgt * ldp<DL>(sc.amp, L + k);
+            col[2] += wgt * ldp<DL>(sc.amp, 2 * L + k);
+        }
+        float gc[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            gc[ch] = col[ch] >= 0.f ? grgb[ch] : 0.f;   // max(c, 0)
+            d_c0[ch] += gc[ch];
+        }
+        float dvx = 0.f, dvy = 0.f, dvz = 0.f;
+        for (int k = lo; k < hi; ++k) {
+            const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
+                        az = ldp<DL>(sc.axis, 2 * L + k);
+            const float na = sqrtf(ax * ax + ay * ay + az * az);
+            const float ia = 1.0f / na;
+            const float mx = ax * ia, my = ay * ia, mz = az * ia;
+            const float dot = mx * vx + my * vy + mz * vz;
+            const float sh = ldp<DS>(sc.sharp, k);
+            const float ex = expf(sh * (dot - 1.0f));
+            const float m = __ldg(sc.lmask + k);
+            const float a0 = ldp<DL>(sc.amp, k), a1 = ldp<DL>(sc.amp, L + k), a2 = ldp<DL>(sc.amp, 2 * L + k);
+            const float ga = a0 * gc[0] + a1 * gc[1] + a2 * gc[2];
+            const float de = m * ga;
+            const float dd = de * ex * sh;                 // dL/d(mu_hat . v)
+            const float gmx = dd * vx, gmy = dd * vy, gmz = dd * vz;   // dL/dmu_hat
+            const float pr = mx * gmx + my * gmy + mz * gmz;
+            dvx += dd * mx; dvy += dd * my; dvz += dd * mz;
+            float ga_out[3] = {m * ex * gc[0], m * ex * gc[1], m * ex * gc[2]};
+            float gax[3] = {(gmx - mx * pr) * ia, (gmy - my * pr) * ia, (gmz - mz * pr) * ia};
+            const float gs = de * ex * (dot - 1.0f);
+            const float gml = ex * ga;
+            const sg_grads &gr = sc.grads;
+            if (first) {
+                if (gr.amp) { gr.amp[k] = ga_out[0]; gr.amp[L + k] = ga_out[1]; gr.amp[2 * L + k] = ga_out[2]; }
+                if (gr.axis) { gr.axis[k] = gax[0]; gr.axis[L + k] = gax[1]; gr.axis[2 * L + k] = gax[2]; }
+                if (gr.sharp) gr.sharp[k] = gs;
+                if (gr.lmask) gr.lmask[k] = gml;
+            } else {
+                if (gr.amp) { gr.amp[k] += ga_out[0]; gr.amp[L + k] += ga_out[1]; gr.amp[2 * L + k] += ga_out[2]; }
+                if (gr.axis) { gr.axis[k] += gax[0]; gr.axis[L + k] += gax[1]; gr.axis[2 * L + k] += gax[2]; }
+                if (gr.sharp) gr.sharp[k] += gs;
+                if (gr.lmask) gr.lmask[k] += gml;
+            }
+        }
+        first = false;
+        // v = (p - cam) / |p - cam|
+        {
+            const float pr = vx * dvx + vy * dvy + vz * dvz;
+            d_mean[0] += (dvx - vx * pr) * idn;
+            d_mean[1] += (dvy - vy * pr) * idn;
+            d_mean[2] += (dvz - vz * pr) * idn;
+        }
+
+        // ---- projected centre: x = fx t_x / t_z + cx - 0.5 ----
+        const float itz = 1.0f / G.tz;
+        float dtx = vw.fx * itz * gx;
+        float dty = vw.fy * itz * gy;
+        float dtz = -(vw.fx * G.tx * gx + vw.fy * G.ty * gy) * itz * itz;
+
+        // ---- conic (A, B, C) = (c, -b, a) / det ----
+        const float a = G.ca, bb = G.cb, c = G.cc;
+        const float id2 = 1.0f / (G.det * G.det);
+        const float da = (-c * c * gA + bb * c * gB - bb * bb * gC) * id2;
+        const float db = (2.f * bb * c * gA - (a * c + bb * bb) * gB + 2.f * a * bb * gC) * id2;
+        const float dc = (-bb * bb * gA + a * bb * gB - a * a * gC) * id2;
+
+        // ---- Sigma_2D = A Sigma A^T (A = J W) ----
+        float SA0[3], SA1[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            SA0[i] = G.S[i][0] * G.A[0][0] + G.S[i][1] * G.A[0][1] + G.S[i][2] * G.A[0][2];
+            SA1[i] = G.S[i][0] * G.A[1][0] + G.S[i][1] * G.A[1][1] + G.S[i][2] * G.A[1][2];
+        }
+        float dA0[3], dA1[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            dA0[i] = 2.f * da * SA0[i] + db * SA1[i];
+            dA1[i] = db * SA0[i] + 2.f * dc * SA1[i];
+        }
+        // symmetric gradient w.r.t. Sigma_3D, then M (Sigma = M M^T)
+        float Gs[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                Gs[i][j] = 2.f * da * G.A[0][i] * G.A[0][j] +
+                           db * (G.A[0][i] * G.A[1][j] + G.A[1][i] * G.A[0][j]) +
+                           2.f * dc * G.A[1][i] * G.A[1][j];
+        float dM[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                dM[i][k] = Gs[i][0] * G.M[0][k] + Gs[i][1] * G.M[1][k] + Gs[i][2] * G.M[2][k];
+        const float sv[3] = {s0, s1, s2};
+        float dR[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            d_scale[k] += dM[0][k] * G.R[0][k] + dM[1][k] * G.R[1][k] + dM[2][k] * G.R[2][k];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) dR[i][k] = dM[i][k] * sv[k];
+        }
+        // rotation of the unit quaternion (w, x, y, z)
+        {
+            const float w = G.qw, x = G.qx, y = G.qy, z = G.qz;
+            const float gw = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] -
+                                    y * dR[2][0] + x * dR[2][1]);
+            const float gxq = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] -
+                                     w * dR[1][2] + z * dR[2][0] + w * dR[2][1] - 2.f * x * dR[2][2]);
+            const float gyq = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] +
+                                     z * dR[1][2] - w * dR[2][0] + z * dR[2][1] - 2.f * y * dR[2][2]);
+            const float gzq = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] -
+                                     2.f * z * dR[1][1] + y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+            const float pr = w * gw + x * gxq + y * gyq + z * gzq;
+            d_q[0] += (gw - w * pr) * G.invq;
+            d_q[1] += (gxq - x * pr) * G.invq;
+            d_q[2] += (gyq - y * pr) * G.invq;
+            d_q[3] += (gzq - z * pr) * G.invq;
+        }
+        // J entries
+        const float *V = vw.V;
+        const float dJ00 = dA0[0] * V[0] + dA0[1] * V[1] + dA0[2] * V[2];
+        const float dJ02 = dA0[0] * V[8] + dA0[1] * V[9] + dA0[2] * V[10];
+        const float dJ11 = dA1[0] * V[4] + dA1[1] * V[5] + dA1[2] * V[6];
+        const float dJ12 = dA1[0] * V[8] + dA1[1] * V[9] + dA1[2] * V[10];
+        const float itz2 = itz * itz;
+        dtz += -(vw.fx * dJ00 + vw.fy * dJ11) * itz2;
+        {
+            const float limx = 1.3f * (0.5f * (float)vw.W / vw.fx);
+            const float limy = 1.3f * (0.5f * (float)vw.H / vw.fy);
+            const bool inx = G.ux >= -limx && G.ux <= limx;
+            const bool iny = G.uy >= -limy && G.uy <= limy;
+            // J02 = -fx ccx / tz^2, ccx = clamp(tx/tz) tz
+            const float dccx = -vw.fx * itz2 * dJ02;
+            const float dccy = -vw.fy * itz2 * dJ12;
+            dtz += 2.f * vw.fx * G.ccx * itz2 * itz * dJ02 + 2.f * vw.fy * G.ccy * itz2 * itz * dJ12;
+            if (inx) dtx += dccx; else dtz += dccx * fminf(limx, fmaxf(-limx, G.ux));
+            if (iny) dty += dccy; else dtz += dccy * fminf(limy, fmaxf(-limy, G.uy));
+        }
+        // t = W p + t
+        d_mean[0] += V[0] * dtx + V[4] * dty + V[8] * dtz;
+        d_mean[1] += V[1] * dtx + V[5] * dty + V[9] * dtz;
+        d_mean[2] += V[2] * dtx + V[6] * dty + V[10] * dtz;
+    }
+
+    const sg_grads &gr = sc.grads;
+    if (first) {   // not visible in any view: lobe gradients are zero
+        for (int k = lo; k < hi; ++k) {
+            if (gr.amp) { gr.amp[k] = 0.f; gr.amp[L + k] = 0.f; gr.amp[2 * L + k] = 0.f; }
+            if (gr.axis) { gr.axis[k] = 0.f; gr.axis[L + k] = 0.f; gr.axis[2 * L + k] = 0.f; }
+            if (gr.sharp) gr.sharp[k] = 0.f;
+            if (gr.lmask) gr.lmask[k] = 0.f;
+        }
+    }
+    if (gr.means) { gr.means[g] = d_mean[0]; gr.means[n + g] = d_mean[1]; gr.means[2 * n + g] = d_mean[2]; }
+    if (gr.scales) { gr.scales[g] = d_scale[0]; gr.scales[n + g] = d_scale[1]; gr.scales[2 * n + g] = d_scale[2]; }
+    if (gr.quats) {
+        gr.quats[g] = d_q[0]; gr.quats[n + g] = d_q[1]; gr.quats[2 * n + g] = d_q[2]; gr.quats[3 * n + g] = d_q[3];
+    }
+    if (gr.opac) gr.opac[g] = d_opac;
+    if (gr.gmask) gr.gmask[g] = d_gmask;
+    if (gr.c0) { gr.c0[g] = d_c0[0]; gr.c0[n + g] = d_c0[1]; gr.c0[2 * n + g] = d_c0[2]; }
+}
+
+template <int DG, int DL, int DS>
+static cudaError_t launch_bwd_t(const Batch &hb, const Batch *db, const uint32_t *tt, const float *dg,
+                                uint64_t M, cudaStream_t s) {
+    if (hb.bwd_blocks == 0) return cudaSuccess;
+    k_preprocess_bwd<DG, DL, DS><<<hb.bwd_blocks, PRE_THREADS, 0, s>>>(db, tt, dg, M);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_backward(const Batch &hb, const Batch *db, const uint32_t *tiles_touched,
+                                       const float *dg, uint64_t M, cudaStream_t s) {
+    const SceneDesc &sc = hb.scene[0];
+    const int key = sc.dtype_geom * 9 + sc.dtype_lobe * 3 + sc.dtype_sharp;
+    switch (key) {
+        case SG_F32 * 9 + SG_F32 * 3 + SG_F32:
+            return launch_bwd_t<SG_F32, SG_F32, SG_F32>(hb, db, tiles_touched, dg, M, s);
+        case SG_F16 * 9 + SG_F16 * 3 + SG_F16:
+            return launch_bwd_t<SG_F16, SG_F16, SG_F16>(hb, db, tiles_touched, dg, M, s);
+        case SG_F16 * 9 + SG_F16 * 3 + SG_BF16:
+            return launch_bwd_t<SG_F16, SG_F16, SG_BF16>(hb, db, tiles_touched, dg, M, s);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sgk

@@ -1,0 +1,311 @@
+"""ctypes binding of libsgsplat.so: the C ABI declared in include/sgsplat.h.
+
+Argument marshalling only. Every step of the rasterizer runs in the CUDA
+library; there is no CPU fallback. If the library has not been built, or no
+CUDA device is present, calls raise instead of computing anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+SG_OK, SG_ERR_INVALID_ARG, SG_ERR_WORKSPACE, SG_ERR_CAPACITY, SG_ERR_TIMEOUT, SG_ERR_CUDA = range(6)
+SG_F32, SG_F16, SG_BF16 = 0, 1, 2
+SG_MAX_VIEWS = 128
+SG_MAX_SCENES = 32
+
+STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_WORKSPACE", 3: "SG_ERR_CAPACITY",
+                4: "SG_ERR_TIMEOUT", 5: "SG_ERR_CUDA"}
+
+EXPORTS = ("sg_version", "sg_last_error", "sg_workspace_query", "sg_workspace_layout",
+           "sg_render_forward", "sg_render_backward", "sg_profile_enable", "sg_profile_read",
+           "sg_profile_stage_name", "sg_kernel_launches")
+SG_PROFILE_EVENTS, SG_PROFILE_COUNT, SG_PROFILE_STAGES = 1, 2, 12
+
+_P = ctypes.c_void_p
+
+
+class sg_scene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_lobes", ctypes.c_int64),
+                ("dtype_geom", ctypes.c_int32), ("dtype_lobe", ctypes.c_int32),
+                ("dtype_sharp", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("means", _P), ("scales", _P), ("quats", _P), ("opac", _P), ("gmask", _P),
+                ("c0", _P), ("lobe_off", _P), ("axis", _P), ("sharp", _P), ("amp", _P),
+                ("lmask", _P)]
+
+
+class sg_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float), ("viewmat", ctypes.c_float * 12),
+                ("near_plane", ctypes.c_float), ("bg", ctypes.c_float * 3)]
+
+
+class sg_grads(ctypes.Structure):
+    _fields_ = [(k, _P) for k in ("means", "scales", "quats", "opac", "gmask", "c0", "axis",
+                                  "sharp", "amp", "lmask")]
+
+
+class sg_sizes(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "n_entries", "n_tiles", "n_pixels", "n_pairs", "pair_capacity", "ws_fixed_bytes",
+        "ws_per_pair_bytes", "ws_bytes", "bwd_ws_bytes")]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class sg_ws_layout(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "rec", "tiles_touched", "rect", "depth_order", "ranges", "pair_tile", "pair_entry",
+        "total_bytes")]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class SGError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_LIB = None
+
+
+def library_path():
+    return _build.library_path()
+
+
+def lib():
+    """Loads libsgsplat.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsgsplat.so not built ({path}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(path)
+        L.sg_version.argtypes = []
+        L.sg_version.restype = ctypes.c_int
+        L.sg_last_error.argtypes = []
+        L.sg_last_error.restype = ctypes.c_char_p
+        L.sg_workspace_query.argtypes = [ctypes.POINTER(sg_scene), ctypes.POINTER(sg_camera),
+                                         ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(sg_sizes)]
+        L.sg_workspace_query.restype = ctypes.c_int
+        L.sg_workspace_layout.argtypes = [ctypes.POINTER(sg_scene), ctypes.POINTER(sg_camera),
+                                          ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(sg_ws_layout)]
+        L.sg_workspace_layout.restype = ctypes.c_int
+        L.sg_render_forward.argtypes = [ctypes.POINTER(sg_scene), ctypes.POINTER(sg_camera),
+                                        ctypes.c_int, _P, ctypes.c_size_t, _P, _P, _P,
+                                        ctypes.POINTER(sg_sizes), _P]
+        L.sg_render_forward.restype = ctypes.c_int
+        L.sg_render_backward.argtypes = [ctypes.POINTER(sg_scene), ctypes.POINTER(sg_camera),
+                                         ctypes.c_int, _P, ctypes.c_size_t, _P, _P, _P, _P,
+                                         ctypes.c_size_t, ctypes.POINTER(sg_grads), _P]
+        L.sg_render_backward.restype = ctypes.c_int
+        L.sg_profile_enable.argtypes = [ctypes.c_int]
+        L.sg_profile_enable.restype = ctypes.c_int
+        L.sg_profile_read.argtypes = [_P, _P, _P, ctypes.c_int]
+        L.sg_profile_read.restype = ctypes.c_int
+        L.sg_kernel_launches.argtypes = []
+        L.sg_kernel_launches.restype = ctypes.c_int64
+        L.sg_profile_stage_name.argtypes = [ctypes.c_int]
+        L.sg_profile_stage_name.restype = ctypes.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def _check(status):
+    if status != SG_OK:
+        raise SGError(status, lib().sg_last_error().decode())
+    return status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# Host-side descriptions
+# ---------------------------------------------------------------------------
+
+_TORCH_DT = {SG_F32: torch.float32, SG_F16: torch.float16, SG_BF16: torch.bfloat16}
+
+
+@dataclass
+class DeviceScene:
+    """Scene arrays on the GPU in the planar layout of sg_scene."""
+    means: torch.Tensor
+    scales: torch.Tensor
+    quats: torch.Tensor
+    opac: torch.Tensor
+    gmask: torch.Tensor
+    c0: torch.Tensor
+    lobe_off: torch.Tensor
+    axis: torch.Tensor
+    sharp: torch.Tensor
+    amp: torch.Tensor
+    lmask: torch.Tensor
+    dtype_geom: int = SG_F32
+    dtype_lobe: int = SG_F32
+    dtype_sharp: int = SG_F32
+
+    FLOAT_FIELDS = ("means", "scales", "quats", "opac", "gmask", "c0", "axis", "sharp", "amp",
+                    "lmask")
+
+    @property
+    def n(self):
+        return int(self.means.shape[1])
+
+    @property
+    def n_lobes(self):
+        return int(self.sharp.shape[0])
+
+    @classmethod
+    def from_host(cls, scene, device="cuda", storage="f32"):
+        """storage: 'f32' | 'f16' (geometry and lobes in binary16) | 'f16_bf16s'
+        (as f16, sharpness in bfloat16)."""
+        dg, dl, ds = {"f32": (SG_F32,) * 3, "f16": (SG_F16,) * 3,
+                      "f16_bf16s": (SG_F16, SG_F16, SG_BF16)}[storage]
+        fam = {"means": dg, "scales": dg, "quats": dg, "opac": dg, "axis": dl, "amp": dl,
+               "sharp": ds}
+        kw = {}
+        for k in cls.FLOAT_FIELDS:
+            a = torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32))
+            kw[k] = a.to(device=device, dtype=_TORCH_DT[fam.get(k, SG_F32)]).contiguous()
+        kw["lobe_off"] = torch.from_numpy(np.ascontiguousarray(scene.lobe_off, np.int32)).to(device)
+        return cls(dtype_geom=dg, dtype_lobe=dl, dtype_sharp=ds, **kw)
+
+    def struct(self):
+        s = sg_scene()
+        s.n = self.n
+        s.n_lobes = self.n_lobes
+        s.dtype_geom, s.dtype_lobe, s.dtype_sharp = self.dtype_geom, self.dtype_lobe, self.dtype_sharp
+        for k in self.FLOAT_FIELDS + ("lobe_off",):
+            t = getattr(self, k)
+            setattr(s, k, t.data_ptr() if t.numel() else None)
+        return s
+
+
+def camera_struct(cam):
+    c = sg_camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    vm = np.asarray(cam.viewmat, np.float32).reshape(12)
+    for i in range(12):
+        c.viewmat[i] = float(vm[i])
+    c.near_plane = float(cam.near)
+    bg = np.asarray(cam.bg, np.float32).reshape(3)
+    for i in range(3):
+        c.bg[i] = float(bg[i])
+    return c
+
+
+def camera_array(cams):
+    arr = (sg_camera * len(cams))()
+    for i, cam in enumerate(cams):
+        arr[i] = camera_struct(cam)
+    return arr
+
+
+def grads_struct(grads: dict):
+    g = sg_grads()
+    for k, _ in sg_grads._fields_:
+        t = grads.get(k)
+        setattr(g, k, t.data_ptr() if (t is not None and t.numel()) else None)
+    return g
+
+
+# ---------------------------------------------------------------------------
+# The C entry points, same names
+# ---------------------------------------------------------------------------
+
+def sg_version() -> int:
+    return int(lib().sg_version())
+
+
+def sg_last_error() -> str:
+    return lib().sg_last_error().decode()
+
+
+def sg_workspace_query(scene: DeviceScene, cams, pair_capacity: int) -> dict:
+    s = scene.struct()
+    c = camera_array(cams)
+    out = sg_sizes()
+    _check(lib().sg_workspace_query(ctypes.byref(s), c, len(cams), int(pair_capacity),
+                                    ctypes.byref(out)))
+    return out.as_dict()
+
+
+def sg_workspace_layout(scene: DeviceScene, cams, ws_bytes: int) -> dict:
+    s = scene.struct()
+    c = camera_array(cams)
+    out = sg_ws_layout()
+    _check(lib().sg_workspace_layout(ctypes.byref(s), c, len(cams), int(ws_bytes), ctypes.byref(out)))
+    return out.as_dict()
+
+
+def sg_render_forward(scene: DeviceScene, cams, ws: torch.Tensor, img, T_final, last,
+                      stream=None, raise_on_error=True):
+    """Returns (status, sizes dict). Raises SGError on failure unless
+    raise_on_error is False (then the status is returned)."""
+    s = scene.struct()
+    c = camera_array(cams)
+    out = sg_sizes()
+    st = lib().sg_render_forward(ctypes.byref(s), c, len(cams), _ptr(ws), ws.numel(), _ptr(img),
+                                 _ptr(T_final), _ptr(last), ctypes.byref(out),
+                                 _stream_handle(stream))
+    if raise_on_error:
+        _check(st)
+    return st, out.as_dict()
+
+
+def sg_render_backward(scene: DeviceScene, cams, ws, T_final, last, d_img, bwd_ws, grads: dict,
+                       stream=None):
+    s = scene.struct()
+    c = camera_array(cams)
+    g = grads_struct(grads)
+    _check(lib().sg_render_backward(ctypes.byref(s), c, len(cams), _ptr(ws), ws.numel(),
+                                    _ptr(T_final), _ptr(last), _ptr(d_img), _ptr(bwd_ws),
+                                    bwd_ws.numel(), ctypes.byref(g), _stream_handle(stream)))
+
+
+def sg_profile_enable(flags: int):
+    _check(lib().sg_profile_enable(int(flags)))
+
+
+def sg_profile_stage_name(i: int):
+    r = lib().sg_profile_stage_name(int(i))
+    return None if r is None else r.decode()
+
+
+def sg_profile_read(reset=True) -> dict:
+    """Per-stage GPU milliseconds and launch counts since the last reset, plus
+    pair evaluations of the counting blend kernels."""
+    ms = (ctypes.c_double * SG_PROFILE_STAGES)()
+    n = (ctypes.c_int64 * SG_PROFILE_STAGES)()
+    ev = (ctypes.c_int64 * 2)()
+    _check(lib().sg_profile_read(ctypes.cast(ms, _P), ctypes.cast(n, _P), ctypes.cast(ev, _P),
+                                 int(bool(reset))))
+    stages = {sg_profile_stage_name(i): {"ms": ms[i], "launches": int(n[i])}
+              for i in range(SG_PROFILE_STAGES)}
+    return {"stages": stages, "pair_evals": {"forward": int(ev[0]), "backward": int(ev[1])}}
+
+
+def sg_kernel_launches() -> int:
+    return int(lib().sg_kernel_launches())

@@ -1,0 +1,165 @@
+"""Helpers for the GPU-vs-oracle parity tests: run the CUDA path through the C
+ABI, read its workspace, and compare with the FP64 oracle."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2509_07021_gb300 import render, sgsplat
+from paper_2509_07021_gb300.sgsplat import DeviceScene
+
+IMG_TOL = 2e-4      # max abs per channel (images)
+GRAD_TOL = 1e-3     # relative L2 per gradient tensor
+
+
+def u32(t: torch.Tensor) -> np.ndarray:
+    return t.view(torch.int32).cpu().numpy().view(np.uint32)
+
+
+class GpuView:
+    """Per-view slices of a finished forward's workspace."""
+
+    def __init__(self, ds: DeviceScene, cams, out: render.ForwardOut):
+        ws = out.ws
+        lay = sgsplat.sg_workspace_layout(ds, cams, ws.numel())
+        M, K, T = out.sizes["n_entries"], out.sizes["n_pairs"], out.sizes["n_tiles"]
+        torch.cuda.synchronize()
+        self.rec = ws[lay["rec"]:lay["rec"] + 48 * M].view(torch.float32).reshape(M, 12).cpu().numpy()
+        self.tt = u32(ws[lay["tiles_touched"]:lay["tiles_touched"] + 4 * M])
+        rect = u32(ws[lay["rect"]:lay["rect"] + 8 * M]).reshape(M, 2)
+        self.rect = np.stack([rect[:, 0] & 0xFFFF, rect[:, 1] & 0xFFFF, rect[:, 0] >> 16,
+                              rect[:, 1] >> 16], 1).astype(np.int64)
+        self.ranges = u32(ws[lay["ranges"]:lay["ranges"] + 8 * T]).reshape(T, 2).astype(np.int64)
+        self.pair_tile = u32(ws[lay["pair_tile"]:lay["pair_tile"] + 4 * K]).astype(np.int64)
+        self.pair_entry = u32(ws[lay["pair_entry"]:lay["pair_entry"] + 4 * K]).astype(np.int64)
+        self.n = ds.n
+        self.cams = cams
+        self.K = K
+
+
+def tile_offsets(cams):
+    offs = [0]
+    for c in cams:
+        offs.append(offs[-1] + c.n_tiles)
+    return offs
+
+
+def check_decisions(gv: GpuView, scene, cams, results):
+    """Cull, radius, rectangle, depth key, binary32 centre/conic/opacity: bit exact.
+    Tile lists and ranges: bit exact."""
+    toffs = tile_offsets(cams)
+    for v, (cam, res) in enumerate(zip(cams, results)):
+        sl = slice(v * gv.n, (v + 1) * gv.n)
+        dec = res.dec
+        vis = gv.tt[sl] > 0
+        np.testing.assert_array_equal(vis, dec.visible, err_msg=f"view {v}: visibility")
+        rec = gv.rec[sl][vis]
+        np.testing.assert_array_equal(gv.rect[sl][vis], dec.rect[vis], err_msg=f"view {v}: rect")
+        np.testing.assert_array_equal(rec[:, 9].astype(np.int64), dec.radius[vis], err_msg="radius")
+        np.testing.assert_array_equal(rec[:, 10].view(np.uint32), dec.depth_bits[vis], err_msg="depth")
+        np.testing.assert_array_equal(rec[:, 0:2].view(np.uint32),
+                                      dec.xy32[vis].astype(np.float32).view(np.uint32), err_msg="xy")
+        np.testing.assert_array_equal(rec[:, [2, 3, 4]].view(np.uint32),
+                                      dec.conic32[vis].astype(np.float32).view(np.uint32), err_msg="conic")
+        opd = (scene.gmask.astype(np.float32) * scene.opac.astype(np.float32))[vis]
+        np.testing.assert_array_equal(rec[:, 5], opd)
+        tt = (dec.rect[:, 2] - dec.rect[:, 0]) * (dec.rect[:, 3] - dec.rect[:, 1])
+        np.testing.assert_array_equal(gv.tt[sl][vis], tt[vis])
+        # tile lists
+        rg = gv.ranges[toffs[v]:toffs[v + 1]]
+        lens = rg[:, 1] - rg[:, 0]
+        np.testing.assert_array_equal(lens, res.ranges[:, 1] - res.ranges[:, 0], err_msg="list lengths")
+        nonempty = lens > 0
+        starts = rg[nonempty, 0]
+        idx = np.concatenate([np.arange(s, s + l) for s, l in zip(starts, lens[nonempty])]) \
+            if nonempty.any() else np.zeros(0, np.int64)
+        np.testing.assert_array_equal(gv.pair_entry[idx] - v * gv.n, res.ids, err_msg="sorted lists")
+        np.testing.assert_array_equal(gv.pair_tile[idx] - toffs[v], (res.keys >> np.uint64(32)).astype(np.int64))
+    # pairs of all views are contiguous and ordered by global tile
+    assert gv.K == sum(len(r.ids) for r in results)
+    assert np.all(np.diff(gv.pair_tile) >= 0)
+
+
+def pixel_mask_of_tiles(cam, tile_sel):
+    m = np.repeat(np.repeat(tile_sel.reshape(cam.tiles_y, cam.tiles_x), 16, 0), 16, 1)
+    return m[:cam.height, :cam.width].astype(bool)
+
+
+def check_image(img, T, last, res, cam, mask=None, tol=IMG_TOL):
+    """img [3,H,W], T [H,W], last [H,W] from the GPU against one oracle view.
+    Unambiguous pixels: image within tol, last exact, T within tol.
+    Ambiguous pixels (a threshold within the oracle's band): counted, and the
+    image must stay within one blended contribution (0.02) of the oracle."""
+    amb = res.ambiguous
+    sel = np.ones(amb.shape, bool) if mask is None else mask
+    ok = sel & ~amb
+    err = np.abs(img - res.img)
+    assert ok.sum() > 0
+    max_err = err[:, ok].max()
+    assert max_err <= tol, f"image max abs error {max_err:.3e} > {tol}"
+    np.testing.assert_array_equal(last[ok], res.last[ok])
+    assert np.abs(T - res.T_final)[ok].max() <= tol
+    n_amb = int((sel & amb).sum())
+    if n_amb:
+        assert err[:, sel & amb].max() <= 0.02
+    assert n_amb <= max(2, 0.01 * sel.sum()), f"{n_amb} ambiguous pixels"
+    return {"max_abs_err": float(max_err), "mean_abs_err": float(err[:, ok].mean()),
+            "ambiguous": n_amb, "pixels": int(sel.sum())}
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def check_grads(g_gpu: dict, g_orc: dict, tol=GRAD_TOL, skip=()):
+    report = {}
+    for k, ref in g_orc.items():
+        if k in skip:
+            continue
+        got = g_gpu[k].detach().cpu().numpy().astype(np.float64)
+        assert got.shape == ref.shape, k
+        if np.linalg.norm(ref) == 0:
+            assert np.abs(got).max() <= 1e-6, (k, np.abs(got).max())
+            report[k] = 0.0
+            continue
+        r = rel_l2(got, ref)
+        report[k] = r
+        assert r <= tol, f"{k}: relative L2 {r:.3e} > {tol}"
+    return report
+
+
+def gpu_render(scene, cams, storage="f32"):
+    ds = DeviceScene.from_host(scene, storage=storage)
+    out = render.render_forward(ds, cams)
+    torch.cuda.synchronize()
+    return ds, out
+
+
+def unpack_views(t, cams, ch):
+    """Flat or [V,...] output -> list of per-view numpy arrays ([3,H,W] or [H,W])."""
+    a = t.detach().cpu().numpy()
+    if a.ndim > 1:
+        return [a[v] for v in range(len(cams))]
+    out, o = [], 0
+    for c in cams:
+        n = c.width * c.height * ch
+        x = a[o:o + n]
+        out.append(x.reshape(3, c.height, c.width) if ch == 3 else x.reshape(c.height, c.width))
+        o += n
+    return out
+
+
+def masked_dimg(rng, cams, results, tile_sels=None, std=0.01):
+    """Upstream gradients N(0, std), zero at the oracle's ambiguous pixels (and
+    outside the selected tiles when given)."""
+    out = []
+    for i, (cam, res) in enumerate(zip(cams, results)):
+        d = rng.normal(0.0, std, (3, cam.height, cam.width)).astype(np.float32)
+        keep = ~res.ambiguous
+        if tile_sels is not None:
+            keep &= pixel_mask_of_tiles(cam, tile_sels[i])
+        d *= keep[None]
+        out.append(d)
+    return out

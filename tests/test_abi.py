@@ -1,0 +1,140 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+include/sgsplat.h declares, sizes workspaces on the host, and rejects bad
+arguments before touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2509_07021_gb300 import sgsplat, synth
+from paper_2509_07021_gb300.sgsplat import DeviceScene
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2509_07021_gb300 import build
+    if not os.path.exists(build.library_path()):
+        build.build()
+    return sgsplat.lib()
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(sg_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert {"sg_render_forward", "sg_render_backward", "sg_workspace_query"} <= set(names)
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(sgsplat.EXPORTS) <= set(names)
+
+
+def test_version(L):
+    assert sgsplat.sg_version() == 1
+
+
+def _cpu_scene(n=100, lobes=2):
+    """A DeviceScene whose tensors live on the CPU: only its sizes are used by the
+    host-only calls below (pointers are never dereferenced there)."""
+    s = synth.make_scene(np.random.default_rng(0), n, lobes=lobes)
+    return DeviceScene.from_host(s, device="cpu")
+
+
+def test_workspace_query_sizes(L):
+    ds = _cpu_scene(1000, 3)
+    cams = [synth.make_camera(128, 96, 150.0), synth.make_camera(64, 64, 80.0)]
+    q0 = sgsplat.sg_workspace_query(ds, cams, 0)
+    q1 = sgsplat.sg_workspace_query(ds, cams, 100_000)
+    assert q0["n_entries"] == 2000
+    assert q0["n_tiles"] == 8 * 6 + 4 * 4
+    assert q0["n_pixels"] == 128 * 96 + 64 * 64
+    assert q0["ws_fixed_bytes"] == q0["ws_bytes"] == q1["ws_fixed_bytes"]
+    # 16 bytes of pair buffers per pair plus the radix histograms
+    assert 16 * 100_000 <= q1["ws_bytes"] - q1["ws_fixed_bytes"] <= 18 * 100_000 + 4096
+    assert q1["bwd_ws_bytes"] >= 9 * 4 * 2000
+    lay = sgsplat.sg_workspace_layout(ds, cams, q1["ws_bytes"])
+    assert lay["total_bytes"] == q1["ws_bytes"]
+    offs = sorted(v for k, v in lay.items() if k != "total_bytes")
+    assert all(o % 256 == 0 for o in offs)
+    assert len(set(offs)) == len(offs)
+
+
+def _status(L, fn, *args):
+    return fn(*args)
+
+
+def test_invalid_arguments_rejected_on_host(L):
+    ds = _cpu_scene(10, 1)
+    s = ds.struct()
+    cams = sgsplat.camera_array([synth.make_camera(32, 32, 40.0)])
+    out = sgsplat.sg_sizes()
+    P = ctypes.c_void_p
+    # no cameras
+    assert L.sg_workspace_query(ctypes.byref(s), None, 1, 0, ctypes.byref(out)) == sgsplat.SG_ERR_INVALID_ARG
+    # n_views out of range
+    assert L.sg_workspace_query(ctypes.byref(s), cams, 0, 0, ctypes.byref(out)) == sgsplat.SG_ERR_INVALID_ARG
+    assert L.sg_workspace_query(ctypes.byref(s), cams, 129, 0, ctypes.byref(out)) == sgsplat.SG_ERR_INVALID_ARG
+    # bad dtype
+    s2 = ds.struct()
+    s2.dtype_geom = 7
+    assert L.sg_workspace_query(ctypes.byref(s2), cams, 1, 0, ctypes.byref(out)) == sgsplat.SG_ERR_INVALID_ARG
+    assert "dtype" in sgsplat.sg_last_error()
+    # negative size
+    s3 = ds.struct()
+    s3.n = -1
+    assert L.sg_workspace_query(ctypes.byref(s3), cams, 1, 0, ctypes.byref(out)) == sgsplat.SG_ERR_INVALID_ARG
+    # zero-sized image and non-finite intrinsics
+    bad = sgsplat.camera_array([synth.make_camera(32, 32, 40.0)])
+    bad[0].width = 0
+    assert L.sg_workspace_query(ctypes.byref(s), bad, 1, 0, ctypes.byref(out)) == sgsplat.SG_ERR_INVALID_ARG
+    bad = sgsplat.camera_array([synth.make_camera(32, 32, 40.0)])
+    bad[0].fx = float("nan")
+    assert L.sg_workspace_query(ctypes.byref(s), bad, 1, 0, ctypes.byref(out)) == sgsplat.SG_ERR_INVALID_ARG
+    # forward: NULL outputs, NULL / misaligned workspace are refused before any device work
+    st = L.sg_render_forward(ctypes.byref(s), cams, 1, P(256), 1 << 20, None, None, None,
+                             ctypes.byref(out), None)
+    assert st == sgsplat.SG_ERR_INVALID_ARG
+    st = L.sg_render_forward(ctypes.byref(s), cams, 1, P(8), 1 << 20, P(256), P(256), P(256),
+                             ctypes.byref(out), None)
+    assert st == sgsplat.SG_ERR_INVALID_ARG
+    # misaligned scene array
+    s4 = ds.struct()
+    s4.means = 4
+    st = L.sg_render_forward(ctypes.byref(s4), cams, 1, P(256), 1 << 20, P(256), P(256), P(256),
+                             ctypes.byref(out), None)
+    assert st == sgsplat.SG_ERR_INVALID_ARG and "aligned" in sgsplat.sg_last_error()
+    # backward: missing gradient struct
+    st = L.sg_render_backward(ctypes.byref(s), cams, 1, P(256), 1 << 20, P(256), P(256), P(256),
+                              P(256), 1 << 20, None, None)
+    assert st == sgsplat.SG_ERR_INVALID_ARG
+
+
+def test_workspace_too_small_for_fixed_part(L):
+    ds = _cpu_scene(10, 1)
+    cams = [synth.make_camera(32, 32, 40.0)]
+    with pytest.raises(sgsplat.SGError) as e:
+        sgsplat.sg_workspace_layout(ds, cams, 64)
+    assert e.value.status == sgsplat.SG_ERR_WORKSPACE
+
+
+def test_product_path_has_no_oracle_import():
+    """The package never imports the oracle (no CPU fallback)."""
+    pkg = os.path.join(ROOT, "paper_2509_07021_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", src, flags=re.M), f
+                assert "sg_blend_oracle" not in src and "liborc" not in src, f
