@@ -70,6 +70,8 @@ def lib():
 
 
 def _p(a):
+    """Address of a numpy array for a C call. The caller must hold a reference
+    to `a` until the call returns (the address does not keep it alive)."""
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
 
@@ -387,9 +389,10 @@ def render_backward(res: ViewResult, scene, cam, dimg):
     dop = np.zeros(N)
     drgb = np.zeros((N, 3))
     bg = _c(cam.bg, np.float64)
+    dimg64 = _c(dimg, np.float64)   # keep the converted copy alive across the call
     lib().orc_blend_backward(cam.width, cam.height, _p(res.ranges), _p(res.ids), _p(res.xy),
                              _p(res.conic), _p(res.op), _p(res.rgb), _p(bg), _p(res.tile_sel),
-                             _p(_c(dimg, np.float64)), _p(dxy), _p(dcon), _p(dop), _p(drgb))
+                             _p(dimg64), _p(dxy), _p(dcon), _p(dop), _p(drgb))
     grads_out = [torch.from_numpy(a[vis_idx]) for a in (dxy, dcon, dop, drgb)]
     leaves_ = [P[k] for k in PARAM_NAMES]
     gl = torch.autograd.grad(list(outs), leaves_, grad_outputs=grads_out, allow_unused=True)
@@ -438,9 +441,13 @@ def brute_force(scene, cam, gate=True):
     img = np.zeros((3, H, W))
     T = np.ones((H, W))
     last = np.zeros((H, W), np.int64)
-    lib().orc_brute_force(N, W, H, _p(_c(dec.depth_bits, np.uint32)), _p(_c(dec.rect, np.int32)),
-                          _p(_c(dec.visible, np.uint8)), _p(xy), _p(con), _p(op), _p(rgb),
-                          _p(_c(cam.bg, np.float64)), int(gate), _p(img), _p(T), _p(last))
+    # converted copies are bound to names so they outlive the C call
+    depth_bits = _c(dec.depth_bits, np.uint32)
+    rect = _c(dec.rect, np.int32)
+    vis = _c(dec.visible, np.uint8)
+    bg = _c(cam.bg, np.float64)
+    lib().orc_brute_force(N, W, H, _p(depth_bits), _p(rect), _p(vis), _p(xy), _p(con), _p(op),
+                          _p(rgb), _p(bg), int(gate), _p(img), _p(T), _p(last))
     return img, T, last
 
 

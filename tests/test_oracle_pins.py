@@ -361,8 +361,9 @@ def test_weight_sum_and_monotone_T(orc):
         last = np.zeros((80, 96), np.int64)
         amb = np.zeros((80, 96), np.uint8)
         p = orc.sg_oracle._p
+        bg = np.zeros(3)
         orc.lib().orc_blend_forward(96, 80, p(r), p(res.ids), p(res.xy), p(res.conic),
-                                    p(res.op), p(res.rgb), p(np.zeros(3)), None, p(img), p(T),
+                                    p(res.op), p(res.rgb), p(bg), None, p(img), p(T),
                                     p(last), p(amb), None)
         if prev is not None:
             assert (T <= prev + 1e-15).all()
