@@ -251,6 +251,32 @@ int sg_render_backward(const sg_scene *scene, const sg_camera *cams, int n_views
                        const int32_t *last, const float *d_img, void *bwd_ws,
                        size_t bwd_ws_bytes, const sg_grads *grads, void *stream);
 
+/*
+ * Backward without caller scratch. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory at render
+ * time -- an engine frame loop or a serving process that reserves all of its
+ * GPU memory at start-up, or code that must not call cudaMalloc because it
+ * synchronises the device. It is sg_render_backward with the 2D-gradient
+ * scratch taken from a static device array inside the library instead of
+ * bwd_ws; the caller still passes every input and output.
+ *  - Limit: the scratch holds SG_NOALLOC_SCRATCH_BYTES (16 MiB), enough for
+ *    sg_sizes.bwd_ws_bytes up to that size (about 465,000 (view, Gaussian)
+ *    entries). Larger calls return SG_ERR_WORKSPACE and do nothing.
+ *  - Every GPU that loads the library holds the 16 MiB until the process
+ *    exits. The first call on a device looks up the array's device address
+ *    (once per device); make that first call before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (other
+ *    streams, other threads) race and give wrong gradients. The array keeps
+ *    the last call's contents; each call clears what it accumulates into.
+ *  - Allocates no device memory and calls no allocating CUDA or library
+ *    routine.
+ */
+#define SG_NOALLOC_SCRATCH_BYTES (16u << 20)
+int sg_render_backward_noalloc(const sg_scene *scene, const sg_camera *cams, int n_views,
+                               const void *ws, size_t ws_bytes, const float *T_final,
+                               const int32_t *last, const float *d_img, const sg_grads *grads,
+                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

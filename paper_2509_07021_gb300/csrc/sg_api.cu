@@ -542,3 +542,85 @@ int sg_render_backward(const sg_scene *scene, const sg_camera *cams, int n_views
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Backward with library-owned scratch, for callers that cannot allocate
+// device memory while rendering
+// ---------------------------------------------------------------------------
+namespace {
+
+// Scratch of sg_render_backward_noalloc: batch table, counters and the
+// [9][M] per-entry 2D-gradient accumulators. Every device that loads the
+// library holds it until the process exits.
+__device__ __align__(256) unsigned char g_noalloc_scratch[SG_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device. In host code the
+// array's name stands for the symbol, not for device memory, so the address is
+// looked up once per device (with that device current) and cached.
+int noalloc_scratch(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "no-alloc backward: cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices)
+        return fail(SG_ERR_INVALID_ARG, "no-alloc backward: device %d out of range", dev);
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "no-alloc backward: cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" int sg_render_backward_noalloc(const sg_scene *scene, const sg_camera *cams, int n_views,
+                                          const void *ws, size_t ws_bytes, const float *T_final,
+                                          const int32_t *last, const float *d_img, const sg_grads *grads,
+                                          void *stream_) {
+    g_err[0] = '\0';
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    Batch b;   // host table on the stack: no heap allocation either
+    int st = build_batch(scene, 1, cams, nullptr, n_views, true, b);
+    if (st != SG_OK) return st;
+    if (!grads) return fail(SG_ERR_INVALID_ARG, "grads must not be NULL");
+    b.scene[0].grads = grads[0];
+    if (!T_final || !last || !d_img) return fail(SG_ERR_INVALID_ARG, "T_final, last and d_img must not be NULL");
+    if (!ws || !aligned(ws, ALIGN)) return fail(SG_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+    const size_t need = bwd_bytes(b);
+    if (need > (size_t)SG_NOALLOC_SCRATCH_BYTES)
+        return fail(SG_ERR_WORKSPACE,
+                    "no-alloc backward needs %zu bytes of scratch for %llu entries; the static scratch holds "
+                    "%zu bytes; use sg_render_backward with caller scratch",
+                    need, (unsigned long long)b.n_entries, (size_t)SG_NOALLOC_SCRATCH_BYTES);
+    const uint64_t cap = capacity_for(b, ws_bytes);
+    if (cap == UINT64_MAX) return fail(SG_ERR_WORKSPACE, "workspace smaller than its fixed part");
+    void *scratch = nullptr;
+    st = noalloc_scratch(&scratch);
+    if (st != SG_OK) return st;
+    const WsLayout L = make_layout(b, cap);
+    const char *w = static_cast<const char *>(ws);
+    const Rec *rec = reinterpret_cast<const Rec *>(w + L.rec);
+    const uint32_t *tt = reinterpret_cast<const uint32_t *>(w + L.tiles_touched);
+    const uint2 *ranges = reinterpret_cast<const uint2 *>(w + L.ranges);
+    const uint32_t *pv_final = reinterpret_cast<const uint32_t *>(w + L.pval_final);
+    char *bw = static_cast<char *>(scratch);
+    Batch *db = reinterpret_cast<Batch *>(bw);
+    uint64_t *counters = reinterpret_cast<uint64_t *>(bw + al(sizeof(Batch)));
+    float *dg = reinterpret_cast<float *>(bw + al(sizeof(Batch)) + al(CNT_N * sizeof(uint64_t)));
+    const uint64_t M = L.M;
+    // the setup kernel rewrites the table and counters; the accumulators are cleared
+    SG_CUDA(launch_setup(b, db, counters, stream), "setup");
+    if (M > 0) SG_CUDA(cudaMemsetAsync(dg, 0, 9 * M * sizeof(float), stream), "clear 2D gradients");
+    SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M, n_views,
+                                  nullptr, stream),
+            "blend backward");
+    SG_CUDA(launch_preprocess_backward(b, db, tt, dg, M, stream), "preprocess backward");
+    return SG_OK;
+}

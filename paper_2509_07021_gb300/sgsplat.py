@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_WORKSPACE", 3: "
 
 EXPORTS = ("sg_version", "sg_last_error", "sg_workspace_query", "sg_workspace_layout",
            "sg_render_forward", "sg_render_backward", "sg_profile_enable", "sg_profile_read",
-           "sg_profile_stage_name", "sg_kernel_launches")
+           "sg_profile_stage_name", "sg_kernel_launches", "sg_render_backward_noalloc")
+SG_NOALLOC_SCRATCH_BYTES = 16 << 20
 SG_PROFILE_EVENTS, SG_PROFILE_COUNT, SG_PROFILE_STAGES = 1, 2, 12
 
 _P = ctypes.c_void_p
@@ -114,6 +115,10 @@ def lib():
         L.sg_profile_enable.restype = ctypes.c_int
         L.sg_profile_read.argtypes = [_P, _P, _P, ctypes.c_int]
         L.sg_profile_read.restype = ctypes.c_int
+        L.sg_render_backward_noalloc.argtypes = [ctypes.POINTER(sg_scene), ctypes.POINTER(sg_camera),
+                                                 ctypes.c_int, _P, ctypes.c_size_t, _P, _P, _P,
+                                                 ctypes.POINTER(sg_grads), _P]
+        L.sg_render_backward_noalloc.restype = ctypes.c_int
         L.sg_kernel_launches.argtypes = []
         L.sg_kernel_launches.restype = ctypes.c_int64
         L.sg_profile_stage_name.argtypes = [ctypes.c_int]
@@ -309,3 +314,18 @@ def sg_profile_read(reset=True) -> dict:
 
 def sg_kernel_launches() -> int:
     return int(lib().sg_kernel_launches())
+
+
+def sg_render_backward_noalloc(scene: DeviceScene, cams, ws, T_final, last, d_img, grads: dict,
+                               stream=None, raise_on_error=True):
+    """Backward whose scratch is the library's static device array (for callers
+    that cannot allocate device memory while rendering). Returns the status."""
+    s = scene.struct()
+    c = camera_array(cams)
+    g = grads_struct(grads)
+    st = lib().sg_render_backward_noalloc(ctypes.byref(s), c, len(cams), _ptr(ws), ws.numel(),
+                                          _ptr(T_final), _ptr(last), _ptr(d_img), ctypes.byref(g),
+                                          _stream_handle(stream))
+    if raise_on_error:
+        _check(st)
+    return st
