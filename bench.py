@@ -44,11 +44,13 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f16", "f16_bf16s"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default blend shapes")
     ap.add_argument("--cpu-tiles", type=int, default=48,
                     help="tiles of the frame the CPU oracle blends per sample")
     return ap.parse_args()
@@ -113,9 +115,13 @@ def max_over_ranks(x, world):
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (20 ms) with timestamps; summarises those that fall in
+    the timed window (widened by `pad` seconds when the window is shorter than
+    a few samples)."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_index):
         self.idx = gpu_index
@@ -128,14 +134,17 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)   # let the sampler start before the timed region
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0, t1, pad=0.25):
+        import datetime
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.05)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -144,18 +153,25 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+            if len(parts) < 8:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[4:8]))
+            except ValueError:
+                continue
         os.unlink(self.path)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        window = "timed region"
+        if len(inside) < 3:
+            inside = [r for r in rows if t0 - pad <= r[0] <= t1 + pad]
+            window = f"timed region +-{pad}s"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        reasons = sorted({self.NAMES[i] for r in inside for i in range(4) if r[3][i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside), "reasons": reasons,
+                "samples": len(inside), "window": window}
 
 
 # ---------------------------------------------------------------------------
@@ -250,6 +266,10 @@ def run_ours(args, world, rank, local):
         render.render_backward(ds, cams, out, d_img, grads)
         return out
 
+    tuned = None
+    if not args.no_autotune:
+        from paper_2509_07021_gb300 import autotune
+        tuned = autotune.tune(ds, cams, d_img, use_cache=False)
     for _ in range(max(args.warmup, 1)):
         out = step()
     torch.cuda.synchronize()
@@ -273,15 +293,17 @@ def run_ours(args, world, rank, local):
     launches0 = sgsplat.sg_kernel_launches()
     barrier(world)
     torch.cuda.synchronize()
+    wall0 = time.time()
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         starts[i].record()
         step()
         ends[i].record()
     torch.cuda.synchronize()
+    wall1 = time.time()
     barrier(world)
     launches = sgsplat.sg_kernel_launches() - launches0
-    clk = clocks.stop()
+    clk = clocks.stop(wall0, wall1)
     sgsplat.sg_profile_enable(0)
     prof = sgsplat.sg_profile_read(reset=True)
     t_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
@@ -319,7 +341,9 @@ def run_ours(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(args, cams, {"n_pairs": n_pairs}),
+            "config": workload_config(args, cams, {"n_pairs": n_pairs,
+                                                   "tuning": sgsplat.sg_get_tuning(),
+                                                   "autotune_ms": tuned and tuned.get("ms")}),
             "roofline": roof, "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches),
             "stages_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in fl_stages.items()},

@@ -196,6 +196,21 @@ int sg_workspace_layout(const sg_scene *scene, const sg_camera *cams, int n_view
 #define SG_PROFILE_STAGES 12
 int sg_profile_enable(int flags);
 int sg_profile_read(double *ms, int64_t *launches, int64_t *pair_evals, int reset);
+/*
+ * Kernel shapes (process wide, not synchronised with renders in flight):
+ * pixels each blend thread owns, 1, 2, 4 or 8 (the block has 256 / P threads
+ * per 16x16 tile). Larger P amortises the per-Gaussian shared-memory loads
+ * and, in the backward, the warp reduction and atomics; smaller P gives more
+ * threads to hide latency. sg_set_tuning(NULL) restores the defaults.
+ */
+typedef struct sg_tuning {
+    int32_t fwd_pixels_per_thread;
+    int32_t bwd_pixels_per_thread;
+    int32_t reserved[6];
+} sg_tuning;
+int sg_set_tuning(const sg_tuning *t);
+int sg_get_tuning(sg_tuning *t);
+
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t sg_kernel_launches(void);
 /* Name of stage i ("preprocess", "depth_sort", ..., "preprocess_bwd"); NULL if out of range. */

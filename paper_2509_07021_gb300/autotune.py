@@ -1,0 +1,88 @@
+"""Autotuner for the blend kernels' shape (pixels per thread).
+
+Times each candidate on the caller's own scene and cameras with the library's
+stage events, picks the fastest forward and backward shape independently, and
+caches the choice per (GPU, image sizes, entries) in a JSON file
+($SGSPLAT_TUNE_CACHE, default ~/.cache/sgsplat/tune.json).
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import render, sgsplat
+
+CANDIDATES = (1, 2, 4, 8)
+
+
+def _cache_path():
+    return os.environ.get("SGSPLAT_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "sgsplat", "tune.json"))
+
+
+def _key(ds, cams):
+    name = torch.cuda.get_device_name()
+    sizes = ",".join(f"{c.width}x{c.height}" for c in cams)
+    # entries rounded to 2 significant digits: nearby scene sizes share a choice
+    m = ds.n * len(cams)
+    mag = 10 ** max(0, len(str(m)) - 2)
+    return f"{name}|{sizes}|{(m // mag) * mag}|{ds.dtype_geom}{ds.dtype_lobe}{ds.dtype_sharp}"
+
+
+def _load():
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store(data):
+    path = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def tune(ds, cams, d_img, reps=3, use_cache=True, candidates=CANDIDATES):
+    """Picks and sets the fastest pixels-per-thread for the forward and the
+    backward blend on this workload. Returns the choice and the timings (ms)."""
+    key = _key(ds, cams)
+    cache = _load() if use_cache else {}
+    if use_cache and key in cache:
+        c = cache[key]
+        sgsplat.sg_set_tuning(c["fwd_pixels_per_thread"], c["bwd_pixels_per_thread"])
+        return dict(c, cached=True)
+    grads = render.alloc_grads(ds)
+    timings = {}
+    prev = sgsplat.sg_get_tuning()
+    for p in candidates:
+        sgsplat.sg_set_tuning(p, p)
+        out = render.render_forward(ds, cams)          # warm-up for this shape
+        render.render_backward(ds, cams, out, d_img, grads)
+        torch.cuda.synchronize()
+        sgsplat.sg_profile_enable(sgsplat.SG_PROFILE_EVENTS)
+        sgsplat.sg_profile_read(reset=True)
+        for _ in range(reps):
+            out = render.render_forward(ds, cams)
+            render.render_backward(ds, cams, out, d_img, grads)
+        torch.cuda.synchronize()
+        st = sgsplat.sg_profile_read(reset=True)["stages"]
+        sgsplat.sg_profile_enable(0)
+        timings[p] = {"blend_fwd": st["blend_fwd"]["ms"] / reps, "blend_bwd": st["blend_bwd"]["ms"] / reps}
+    best_f = min(timings, key=lambda p: timings[p]["blend_fwd"])
+    best_b = min(timings, key=lambda p: timings[p]["blend_bwd"])
+    sgsplat.sg_set_tuning(best_f, best_b)
+    res = {"fwd_pixels_per_thread": best_f, "bwd_pixels_per_thread": best_b,
+           "ms": {str(k): v for k, v in timings.items()}, "previous": prev}
+    if use_cache:
+        cache[key] = res
+        _store(cache)
+    return dict(res, cached=False)

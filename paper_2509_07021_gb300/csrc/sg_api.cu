@@ -99,6 +99,15 @@ struct StageTimer {
     }
 };
 
+// Process-wide kernel shape choices (sg_set_tuning); defaults from measurement.
+constexpr sg_tuning kDefaultTuning = {2, 4, {0, 0, 0, 0, 0, 0}};
+sg_tuning &tuning() {
+    static sg_tuning t = kDefaultTuning;
+    return t;
+}
+
+bool ppt_ok(int p) { return p == 1 || p == 2 || p == 4 || p == 8; }
+
 constexpr size_t ALIGN = 256;
 size_t al(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -373,7 +382,8 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     if (counting) SG_CUDA(cudaMemsetAsync(evals, 0, 8, stream), "clear counter");
     {
         StageTimer t(ST_BLEND_FWD, stream);
-        SG_CUDA(launch_blend_forward(db, b.n_tiles, ranges, pv_final, rec, img, T_final, last, n_views, evals,
+        SG_CUDA(launch_blend_forward(db, b.n_tiles, ranges, pv_final, rec, img, T_final, last,
+                                     tuning().fwd_pixels_per_thread, evals,
                                      stream),
                 "blend forward");
     }
@@ -431,7 +441,7 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
     {
         StageTimer t(ST_BLEND_BWD, stream);
         SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M,
-                                      n_views, evals, stream),
+                                      tuning().bwd_pixels_per_thread, evals, stream),
                 "blend backward");
     }
     {
@@ -487,6 +497,24 @@ int sg_profile_read(double *ms, int64_t *launches, int64_t *pair_evals, int rese
 }
 
 int64_t sg_kernel_launches(void) { return launch_counter().load(); }
+
+int sg_set_tuning(const sg_tuning *t) {
+    if (!t) {
+        tuning() = kDefaultTuning;
+        return SG_OK;
+    }
+    if (!ppt_ok(t->fwd_pixels_per_thread) || !ppt_ok(t->bwd_pixels_per_thread))
+        return fail(SG_ERR_INVALID_ARG, "pixels per thread must be 1, 2, 4 or 8 (got %d, %d)",
+                    t->fwd_pixels_per_thread, t->bwd_pixels_per_thread);
+    tuning() = *t;
+    return SG_OK;
+}
+
+int sg_get_tuning(sg_tuning *t) {
+    if (!t) return fail(SG_ERR_INVALID_ARG, "t must not be NULL");
+    *t = tuning();
+    return SG_OK;
+}
 
 const char *sg_profile_stage_name(int i) { return (i >= 0 && i < ST_N) ? kStageNames[i] : nullptr; }
 
@@ -618,8 +646,8 @@ extern "C" int sg_render_backward_noalloc(const sg_scene *scene, const sg_camera
     // the setup kernel rewrites the table and counters; the accumulators are cleared
     SG_CUDA(launch_setup(b, db, counters, stream), "setup");
     if (M > 0) SG_CUDA(cudaMemsetAsync(dg, 0, 9 * M * sizeof(float), stream), "clear 2D gradients");
-    SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M, n_views,
-                                  nullptr, stream),
+    SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M,
+                                  tuning().bwd_pixels_per_thread, nullptr, stream),
             "blend backward");
     SG_CUDA(launch_preprocess_backward(b, db, tt, dg, M, stream), "preprocess backward");
     return SG_OK;

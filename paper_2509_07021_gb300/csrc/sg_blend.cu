@@ -6,10 +6,10 @@
 // alpha < 1/255 skips, and the walk stops (without blending) at the first
 // pair that would take T below 1e-4.
 //
-// One 256-thread block per 16x16 tile, one pixel per thread. Batches of 256
-// projected Gaussians are staged in shared memory; a block leaves its list
-// as soon as every pixel is done (a block-wide vote), and a warp whose
-// pixels are all done skips the batch.
+// One block per 16x16 tile, P pixels per thread (P in {1, 2, 4, 8}, picked at
+// run time). Batches of 256 projected Gaussians are staged in shared memory; a
+// block leaves its list as soon as every pixel is done (a block-wide vote), and
+// threads whose pixels are all done skip the batch.
 //
 // The per-pair arithmetic that decides skips is written with explicitly
 // rounded operations so the backward recomputes exactly the forward's
@@ -31,110 +31,181 @@ __device__ __forceinline__ int find_tile_view(const Batch &b, uint32_t t) {
     return lo;
 }
 
-struct PairEval {
-    float dx, dy, power, G, ag, alpha;
+// Shared-memory image of one projected Gaussian, prepared once per tile batch:
+//   q = (x, y, qa, qb), r = (qc, o', red, green), s = blue
+// with (qa, qb, qc) = -log2(e) * (A/2, B, C/2), so that
+//   power * log2(e) = qa dx^2 + qb dx dy + qc dy^2   and   exp(power) = 2^(that).
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr int BATCH = 256;   // Gaussians staged per shared-memory batch
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct Staged {
+    float4 q[BATCH];
+    float4 r[BATCH];
+    float s[BATCH];
+    uint32_t id[BATCH];
 };
 
-// power = -1/2 (A dx^2 + C dy^2) - B dx dy with d = pixel - centre
-__device__ __forceinline__ void eval_pair(float fpx, float fpy, const float4 &a, const float4 &b,
+__device__ __forceinline__ void stage(Staged &sm, int slot, const Rec &rc, uint32_t e) {
+    sm.q[slot] = make_float4(rc.a.x, rc.a.y, -0.5f * LOG2E * rc.a.z, -LOG2E * rc.a.w);
+    sm.r[slot] = make_float4(-0.5f * LOG2E * rc.b.x, rc.b.y, rc.b.z, rc.b.w);
+    sm.s[slot] = rc.c.x;
+    sm.id[slot] = e;
+}
+
+struct PairEval {
+    float dx, dy, t, u, p2, G, ag, alpha;
+};
+
+// Every kernel that decides a skip evaluates a pair with this exact sequence of
+// explicitly rounded operations, so the forward and the backward agree.
+__device__ __forceinline__ void eval_pair(float fpx, float fpy, const float4 &q, const float4 &r,
                                           PairEval &p) {
-    p.dx = __fsub_rn(fpx, a.x);
-    p.dy = __fsub_rn(fpy, a.y);
-    const float cdy = __fmul_rn(__fmul_rn(b.x, p.dy), p.dy);
-    const float q = __fmaf_rn(__fmul_rn(a.z, p.dx), p.dx, cdy);
-    const float bxy = __fmul_rn(__fmul_rn(a.w, p.dx), p.dy);
-    p.power = __fmaf_rn(-0.5f, q, -bxy);
-    p.G = __expf(p.power);
-    p.ag = __fmul_rn(b.y, p.G);
+    p.dx = __fsub_rn(fpx, q.x);
+    p.dy = __fsub_rn(fpy, q.y);
+    p.t = __fmaf_rn(q.w, p.dy, __fmul_rn(q.z, p.dx));      // qa dx + qb dy
+    p.u = __fmul_rn(r.x, p.dy);                             // qc dy
+    p.p2 = __fmaf_rn(p.u, p.dy, __fmul_rn(p.t, p.dx));      // power * log2(e)
+    p.G = ex2_approx(p.p2);
+    p.ag = __fmul_rn(r.y, p.G);
     p.alpha = fminf(ALPHA_MAX, p.ag);
 }
 
-// ---------------------------------------------------------------------------
-// K6 blend forward
-// ---------------------------------------------------------------------------
-// Sums a per-thread count over the block into *evals (counting builds only).
+__device__ __forceinline__ bool tile_of_block(const Batch &b, uint32_t tile, int &tx, int &ty,
+                                              const ViewDesc *&vw) {
+    vw = &b.view[find_tile_view(b, tile)];
+    const uint32_t lt = tile - vw->tile_off;
+    tx = (int)(lt % (uint32_t)vw->tiles_x);
+    ty = (int)(lt / (uint32_t)vw->tiles_x);
+    return true;
+}
+
+// Sums a per-thread count over the warp into *evals (counting variants only).
 __device__ __forceinline__ void add_evals(uint32_t ne, unsigned long long *evals) {
     const uint32_t w = __reduce_add_sync(0xffffffffu, ne);
     if ((threadIdx.x & 31) == 0 && w) atomicAdd(evals, (unsigned long long)w);
 }
 
-template <bool COUNT>
-__global__ void __launch_bounds__(BLEND_THREADS)
+// ---------------------------------------------------------------------------
+// K6 blend forward: one block per tile, P pixels per thread
+// ---------------------------------------------------------------------------
+// Thread t owns pixels t, t + NT, ..., t + (P-1) NT of the tile (NT = 256 / P
+// threads), so each warp store covers consecutive addresses.
+template <int P, bool COUNT>
+__global__ void __launch_bounds__(BLEND_THREADS / P)
 k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const uint32_t *__restrict__ pval, const Rec *__restrict__ rec,
             float *__restrict__ img, float *__restrict__ T_final, int32_t *__restrict__ last,
             unsigned long long *__restrict__ evals) {
-    __shared__ float4 sa[BLEND_THREADS];
-    __shared__ float4 sb[BLEND_THREADS];
-    __shared__ float sc[BLEND_THREADS];
+    constexpr int NT = BLEND_THREADS / P;
+    __shared__ Staged sm;
     const Batch &b = *bp;
-    const uint32_t tile = blockIdx.x;
-    const ViewDesc &vw = b.view[find_tile_view(b, tile)];
-    const uint32_t lt = tile - vw.tile_off;
-    const int tx = (int)(lt % (uint32_t)vw.tiles_x), ty = (int)(lt / (uint32_t)vw.tiles_x);
-    const int px = tx * TILE + (threadIdx.x & (TILE - 1));
-    const int py = ty * TILE + (threadIdx.x / TILE);
-    const bool inside = px < vw.W && py < vw.H;
-    const uint2 rg = ranges[tile];
+    int tx, ty;
+    const ViewDesc *vw;
+    tile_of_block(b, blockIdx.x, tx, ty, vw);
+    const uint2 rg = ranges[blockIdx.x];
     const int n = (int)(rg.y - rg.x);
-    const float fpx = (float)px, fpy = (float)py;
 
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    int lastc = 0;
+    float fpx[P], fpy[P], T[P], c0[P], c1[P], c2[P];
+    int lastc[P];
+    bool done[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int i = (int)threadIdx.x + j * NT;
+        const int px = tx * TILE + (i & (TILE - 1)), py = ty * TILE + i / TILE;
+        fpx[j] = (float)px;
+        fpy[j] = (float)py;
+        T[j] = 1.f;
+        c0[j] = c1[j] = c2[j] = 0.f;
+        lastc[j] = 0;
+        done[j] = !(px < vw->W && py < vw->H);
+    }
     uint32_t ne = 0;
-    bool done = !inside;
-    for (int base = 0; base < n; base += BLEND_THREADS) {
-        if (__syncthreads_count(done) == BLEND_THREADS) break;
-        const int j = base + (int)threadIdx.x;
-        if (j < n) {
-            const Rec r = rec[pval[rg.x + j]];
-            sa[threadIdx.x] = r.a;
-            sb[threadIdx.x] = r.b;
-            sc[threadIdx.x] = r.c.x;
+    for (int base = 0; base < n; base += BATCH) {
+        bool all = true;
+#pragma unroll
+        for (int j = 0; j < P; ++j) all = all && done[j];
+        if (__syncthreads_count(all) == NT) break;
+        const int cnt = min(BATCH, n - base);
+        for (int k = threadIdx.x; k < cnt; k += NT) {
+            const uint32_t e = pval[rg.x + base + k];
+            stage(sm, k, rec[e], e);
         }
         __syncthreads();
-        const int cnt = min(BLEND_THREADS, n - base);
-        if (!done) {
-            for (int k = 0; k < cnt; ++k) {
-                const float4 a = sa[k], bb = sb[k];
+        if (all) continue;
+        for (int k = 0; k < cnt; ++k) {
+            const float4 q = sm.q[k], r = sm.r[k];
+            const float bl = sm.s[k];
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                if (done[j]) continue;
                 PairEval p;
-                eval_pair(fpx, fpy, a, bb, p);
+                eval_pair(fpx[j], fpy[j], q, r, p);
                 if (COUNT) ++ne;
-                if (p.power > 0.f) continue;
-                if (p.alpha < ALPHA_MIN) continue;
-                const float tt = __fmul_rn(T, __fsub_rn(1.f, p.alpha));
-                if (tt < T_STOP) { done = true; break; }
-                const float w = p.alpha * T;
-                c0 += bb.z * w;
-                c1 += bb.w * w;
-                c2 += sc[k] * w;
-                T = tt;
-                lastc = base + k + 1;
+                if (p.p2 > 0.f || p.alpha < ALPHA_MIN) continue;
+                const float tt = __fmul_rn(T[j], __fsub_rn(1.f, p.alpha));
+                if (tt < T_STOP) { done[j] = true; continue; }
+                const float w = p.alpha * T[j];
+                c0[j] = fmaf(r.z, w, c0[j]);
+                c1[j] = fmaf(r.w, w, c1[j]);
+                c2[j] = fmaf(bl, w, c2[j]);
+                T[j] = tt;
+                lastc[j] = base + k + 1;
             }
         }
     }
     if (COUNT) add_evals(ne, evals);
-    if (inside) {
-        const uint64_t HW = (uint64_t)vw.W * (uint64_t)vw.H;
-        const uint64_t pix = (uint64_t)py * (uint64_t)vw.W + (uint64_t)px;
-        float *im = img + 3 * vw.pix_off;
-        im[pix] = c0 + T * vw.bg[0];
-        im[HW + pix] = c1 + T * vw.bg[1];
-        im[2 * HW + pix] = c2 + T * vw.bg[2];
-        T_final[vw.pix_off + pix] = T;
-        last[vw.pix_off + pix] = lastc;
+    const uint64_t HW = (uint64_t)vw->W * (uint64_t)vw->H;
+    float *im = img + 3 * vw->pix_off;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int px = (int)fpx[j], py = (int)fpy[j];
+        if (px < vw->W && py < vw->H) {
+            const uint64_t pix = (uint64_t)py * (uint64_t)vw->W + (uint64_t)px;
+            im[pix] = c0[j] + T[j] * vw->bg[0];
+            im[HW + pix] = c1[j] + T[j] * vw->bg[1];
+            im[2 * HW + pix] = c2[j] + T[j] * vw->bg[2];
+            T_final[vw->pix_off + pix] = T[j];
+            last[vw->pix_off + pix] = lastc[j];
+        }
     }
+}
+
+template <int P>
+static void fwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval,
+                  const Rec *rec, float *img, float *T_final, int32_t *last, unsigned long long *evals,
+                  cudaStream_t s) {
+    if (evals)
+        k_blend_fwd<P, true><<<n_tiles, BLEND_THREADS / P, 0, s>>>(db, ranges, pval, rec, img, T_final,
+                                                                  last, evals);
+    else
+        k_blend_fwd<P, false><<<n_tiles, BLEND_THREADS / P, 0, s>>>(db, ranges, pval, rec, img, T_final,
+                                                                   last, nullptr);
 }
 
 cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
                                  const uint32_t *pval, const Rec *rec, float *img, float *T_final,
-                                 int32_t *last, int n_views, unsigned long long *evals, cudaStream_t s) {
-    (void)n_views;
+                                 int32_t *last, int pixels_per_thread, unsigned long long *evals,
+                                 cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
-    if (evals)
-        k_blend_fwd<true><<<n_tiles, BLEND_THREADS, 0, s>>>(db, ranges, pval, rec, img, T_final, last, evals);
-    else
-        k_blend_fwd<false><<<n_tiles, BLEND_THREADS, 0, s>>>(db, ranges, pval, rec, img, T_final, last, nullptr);
+    switch (pixels_per_thread) {
+        case 1: fwd_p<1>(db, n_tiles, ranges, pval, rec, img, T_final, last, evals, s); break;
+        case 2: fwd_p<2>(db, n_tiles, ranges, pval, rec, img, T_final, last, evals, s); break;
+        case 4: fwd_p<4>(db, n_tiles, ranges, pval, rec, img, T_final, last, evals, s); break;
+        case 8: fwd_p<8>(db, n_tiles, ranges, pval, rec, img, T_final, last, evals, s); break;
+        default: return cudaErrorInvalidValue;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -142,11 +213,10 @@ cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 
 // ---------------------------------------------------------------------------
 // K7 blend backward
 // ---------------------------------------------------------------------------
-// Sums 9 per-lane values over the warp and adds them to dg[k*M + e].
-// Recursive halving: 4 + 2 + 1 shuffles leave each group of four lanes with
-// one of the first eight sums, two more finish it; the ninth value takes a
-// plain butterfly. 14 shuffles instead of 45, and eight lanes issue their
-// atomics together.
+// Sums 9 per-lane values over the warp and adds them to dg[k*M + e] (value k
+// scaled by sc[k]). Recursive halving: 4 + 2 + 1 shuffles leave each group of
+// four lanes with one of the first eight sums, two more finish it; the ninth
+// value takes a plain butterfly. Eight lanes issue their atomics together.
 __device__ __forceinline__ void warp_sum9_atomic(const float v[9], float *dg, uint64_t M, uint32_t e) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -178,123 +248,150 @@ __device__ __forceinline__ void warp_sum9_atomic(const float v[9], float *dg, ui
     if (lane == 1) atomicAdd(dg + 8 * M + e, d);
 }
 
-template <bool COUNT>
-__global__ void __launch_bounds__(BLEND_THREADS)
+// Per pixel the walk runs back from the pixel's last blended pair, recovering
+// the transmittance before each pair as T_i = T_{i+1} / (1 - alpha_i) and
+// keeping Sg = sum over later pairs of (c . g) alpha T, so that
+//   dL/dalpha_i = T_i (c_i . g) - (Sg + T_final (bg . g)) / (1 - alpha_i).
+// Per-thread sums over its P pixels are reduced over the warp before the
+// atomics. Accumulated per pair (in dg order):
+//   0,1: dL/dx, dL/dy   2..4: dL/dA, dL/dB, dL/dC   5: dL/do'   6..8: dL/drgb
+template <int P, bool COUNT>
+__global__ void __launch_bounds__(BLEND_THREADS / P)
 k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const uint32_t *__restrict__ pval, const Rec *__restrict__ rec,
             const float *__restrict__ T_final, const int32_t *__restrict__ last,
             const float *__restrict__ d_img, float *__restrict__ dg, uint64_t M,
             unsigned long long *__restrict__ evals) {
-    __shared__ float4 sa[BLEND_THREADS];
-    __shared__ float4 sb[BLEND_THREADS];
-    __shared__ float sc[BLEND_THREADS];
-    __shared__ uint32_t sid[BLEND_THREADS];
-    __shared__ int smax[BLEND_THREADS / 32];
+    constexpr int NT = BLEND_THREADS / P;
+    __shared__ Staged sm;
+    __shared__ int smax[(NT + 31) / 32];
     const Batch &b = *bp;
-    const uint32_t tile = blockIdx.x;
-    const ViewDesc &vw = b.view[find_tile_view(b, tile)];
-    const uint32_t lt = tile - vw.tile_off;
-    const int tx = (int)(lt % (uint32_t)vw.tiles_x), ty = (int)(lt / (uint32_t)vw.tiles_x);
-    const int px = tx * TILE + (threadIdx.x & (TILE - 1));
-    const int py = ty * TILE + (threadIdx.x / TILE);
-    const bool inside = px < vw.W && py < vw.H;
-    const uint2 rg = ranges[tile];
-    const float fpx = (float)px, fpy = (float)py;
+    int tx, ty;
+    const ViewDesc *vw;
+    tile_of_block(b, blockIdx.x, tx, ty, vw);
+    const uint2 rg = ranges[blockIdx.x];
+    const uint64_t HW = (uint64_t)vw->W * (uint64_t)vw->H;
+    const float *gi = d_img + 3 * vw->pix_off;
 
-    const uint64_t HW = (uint64_t)vw.W * (uint64_t)vw.H;
-    const uint64_t pix = (uint64_t)py * (uint64_t)vw.W + (uint64_t)px;
-    int my_last = 0;
-    float T = 1.f, Tf = 1.f, gp[3] = {0.f, 0.f, 0.f};
-    if (inside) {
-        my_last = last[vw.pix_off + pix];
-        Tf = T_final[vw.pix_off + pix];
-        T = Tf;
-        const float *gi = d_img + 3 * vw.pix_off;
-        gp[0] = gi[pix];
-        gp[1] = gi[HW + pix];
-        gp[2] = gi[2 * HW + pix];
+    float fpx[P], fpy[P], T[P], Tfbg[P], g0[P], g1[P], g2[P], Sg[P];
+    int mylast[P];
+    int tmax = 0;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int i = (int)threadIdx.x + j * NT;
+        const int px = tx * TILE + (i & (TILE - 1)), py = ty * TILE + i / TILE;
+        fpx[j] = (float)px;
+        fpy[j] = (float)py;
+        T[j] = 1.f; Tfbg[j] = 0.f; g0[j] = g1[j] = g2[j] = 0.f; Sg[j] = 0.f; mylast[j] = 0;
+        if (px < vw->W && py < vw->H) {
+            const uint64_t pix = (uint64_t)py * (uint64_t)vw->W + (uint64_t)px;
+            mylast[j] = last[vw->pix_off + pix];
+            const float tf = T_final[vw->pix_off + pix];
+            T[j] = tf;
+            g0[j] = gi[pix];
+            g1[j] = gi[HW + pix];
+            g2[j] = gi[2 * HW + pix];
+            Tfbg[j] = tf * (g0[j] * vw->bg[0] + g1[j] * vw->bg[1] + g2[j] * vw->bg[2]);
+        }
+        tmax = max(tmax, mylast[j]);
     }
-    const float bgdot = Tf * (gp[0] * vw.bg[0] + gp[1] * vw.bg[1] + gp[2] * vw.bg[2]);
-    float S0 = 0.f, S1 = 0.f, S2 = 0.f;   // sum over later pairs of c alpha T
-    uint32_t ne = 0;
-
-    const int wmax = __reduce_max_sync(0xffffffffu, my_last);
+    const int wmax = __reduce_max_sync(0xffffffffu, tmax);
     if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = wmax;
     __syncthreads();
     int maxlast = 0;
 #pragma unroll
-    for (int i = 0; i < BLEND_THREADS / 32; ++i) maxlast = max(maxlast, smax[i]);
+    for (int i = 0; i < (NT + 31) / 32; ++i) maxlast = max(maxlast, smax[i]);
+    uint32_t ne = 0;
 
-    for (int end = maxlast; end > 0; end -= BLEND_THREADS) {
-        const int start = max(0, end - BLEND_THREADS);
+    for (int end = maxlast; end > 0; end -= BATCH) {
+        const int start = max(0, end - BATCH);
         const int cnt = end - start;
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t e = pval[rg.x + start + threadIdx.x];
-            const Rec r = rec[e];
-            sa[threadIdx.x] = r.a;
-            sb[threadIdx.x] = r.b;
-            sc[threadIdx.x] = r.c.x;
-            sid[threadIdx.x] = e;
+        for (int k = threadIdx.x; k < cnt; k += NT) {
+            const uint32_t e = pval[rg.x + start + k];
+            stage(sm, k, rec[e], e);
         }
         __syncthreads();
         // warps whose pixels all end before this batch have nothing to add
-        if (__all_sync(0xffffffffu, my_last <= start)) continue;
+        if (__all_sync(0xffffffffu, tmax <= start)) continue;
         for (int k = cnt - 1; k >= 0; --k) {
             const int pos = start + k;
+            const float4 q = sm.q[k], r = sm.r[k];
+            const float bl = sm.s[k];
             float v[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) v[i] = 0.f;
-            bool contrib = false;
-            if (pos < my_last) {
-                const float4 a = sa[k], bb = sb[k];
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                if (pos >= mylast[j]) continue;
                 PairEval p;
-                eval_pair(fpx, fpy, a, bb, p);
+                eval_pair(fpx[j], fpy[j], q, r, p);
                 if (COUNT) ++ne;
-                if (!(p.power > 0.f) && !(p.alpha < ALPHA_MIN)) {
-                    contrib = true;
-                    const float oma = __fsub_rn(1.f, p.alpha);
-                    const float Ti = T / oma;
-                    const float w = p.alpha * Ti;
-                    const float cr = bb.z, cg = bb.w, cb = sc[k];
-                    v[6] = w * gp[0];
-                    v[7] = w * gp[1];
-                    v[8] = w * gp[2];
-                    const float dalpha = Ti * (cr * gp[0] + cg * gp[1] + cb * gp[2]) -
-                                         (S0 * gp[0] + S1 * gp[1] + S2 * gp[2] + bgdot) / oma;
-                    S0 += cr * w;
-                    S1 += cg * w;
-                    S2 += cb * w;
-                    T = Ti;
-                    if (!(p.ag > ALPHA_MAX)) {
-                        const float dpower = dalpha * bb.y * p.G;
-                        v[5] = dalpha * p.G;
-                        v[2] = -0.5f * p.dx * p.dx * dpower;
-                        v[3] = -p.dx * p.dy * dpower;
-                        v[4] = -0.5f * p.dy * p.dy * dpower;
-                        v[0] = dpower * (a.z * p.dx + a.w * p.dy);
-                        v[1] = dpower * (bb.x * p.dy + a.w * p.dx);
-                    }
+                if (p.p2 > 0.f || p.alpha < ALPHA_MIN) continue;
+                any = true;
+                const float oma = __fsub_rn(1.f, p.alpha);
+                const float ro = rcp_approx(oma);
+                const float Ti = T[j] * ro;
+                const float w = p.alpha * Ti;
+                const float cg = fmaf(r.z, g0[j], fmaf(r.w, g1[j], bl * g2[j]));
+                const float dal = Ti * cg - (Sg[j] + Tfbg[j]) * ro;
+                Sg[j] = fmaf(cg, w, Sg[j]);
+                T[j] = Ti;
+                v[6] = fmaf(w, g0[j], v[6]);
+                v[7] = fmaf(w, g1[j], v[7]);
+                v[8] = fmaf(w, g2[j], v[8]);
+                if (!(p.ag > ALPHA_MAX)) {
+                    const float dG = dal * p.G;          // dL/do' share of this pixel
+                    const float h = dG * r.y;            // dL/dpower
+                    v[5] += dG;
+                    // with L = log2 e: qa dx + qb dy = t, so A dx + B dy = -(t + qa dx) / L
+                    v[0] = fmaf(h, fmaf(q.z, p.dx, p.t), v[0]);
+                    v[1] = fmaf(h, fmaf(2.f, p.u, q.w * p.dx), v[1]);
+                    const float hx = h * p.dx;
+                    v[2] = fmaf(hx, p.dx, v[2]);
+                    v[3] = fmaf(hx, p.dy, v[3]);
+                    v[4] = fmaf(h * p.dy, p.dy, v[4]);
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) warp_sum9_atomic(v, dg, M, sid[k]);
+            if (__any_sync(0xffffffffu, any)) {
+                // constant factors of the accumulated forms
+                v[0] *= -1.f / LOG2E;
+                v[1] *= -1.f / LOG2E;
+                v[2] *= -0.5f;
+                v[3] *= -1.f;
+                v[4] *= -0.5f;
+                warp_sum9_atomic(v, dg, M, sm.id[k]);
+            }
         }
     }
     if (COUNT) add_evals(ne, evals);
 }
 
+template <int P>
+static void bwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval,
+                  const Rec *rec, const float *T_final, const int32_t *last, const float *d_img, float *dg,
+                  uint64_t M, unsigned long long *evals, cudaStream_t s) {
+    if (evals)
+        k_blend_bwd<P, true><<<n_tiles, BLEND_THREADS / P, 0, s>>>(db, ranges, pval, rec, T_final, last,
+                                                                  d_img, dg, M, evals);
+    else
+        k_blend_bwd<P, false><<<n_tiles, BLEND_THREADS / P, 0, s>>>(db, ranges, pval, rec, T_final, last,
+                                                                   d_img, dg, M, nullptr);
+}
+
 cudaError_t launch_blend_backward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
                                   const uint32_t *pval, const Rec *rec, const float *T_final,
                                   const int32_t *last, const float *d_img, float *dg, uint64_t M,
-                                  int n_views, unsigned long long *evals, cudaStream_t s) {
-    (void)n_views;
+                                  int pixels_per_thread, unsigned long long *evals, cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
-    if (evals)
-        k_blend_bwd<true><<<n_tiles, BLEND_THREADS, 0, s>>>(db, ranges, pval, rec, T_final, last, d_img,
-                                                             dg, M, evals);
-    else
-        k_blend_bwd<false><<<n_tiles, BLEND_THREADS, 0, s>>>(db, ranges, pval, rec, T_final, last, d_img,
-                                                              dg, M, nullptr);
+    switch (pixels_per_thread) {
+        case 1: bwd_p<1>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, evals, s); break;
+        case 2: bwd_p<2>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, evals, s); break;
+        case 4: bwd_p<4>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, evals, s); break;
+        case 8: bwd_p<8>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, evals, s); break;
+        default: return cudaErrorInvalidValue;
+    }
     count_launches(1);
     return cudaGetLastError();
 }

@@ -120,12 +120,12 @@ cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64
 
 cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
                                  const uint32_t *pval, const Rec *rec, float *img,
-                                 float *T_final, int32_t *last, int n_views,
+                                 float *T_final, int32_t *last, int pixels_per_thread,
                                  unsigned long long *evals, cudaStream_t s);
 cudaError_t launch_blend_backward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
                                   const uint32_t *pval, const Rec *rec, const float *T_final,
                                   const int32_t *last, const float *d_img, float *dg,
-                                  uint64_t M, int n_views, unsigned long long *evals,
+                                  uint64_t M, int pixels_per_thread, unsigned long long *evals,
                                   cudaStream_t s);
 
 }  // namespace sgk

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_WORKSPACE", 3: "
 
 EXPORTS = ("sg_version", "sg_last_error", "sg_workspace_query", "sg_workspace_layout",
            "sg_render_forward", "sg_render_backward", "sg_profile_enable", "sg_profile_read",
-           "sg_profile_stage_name", "sg_kernel_launches", "sg_render_backward_noalloc")
+           "sg_profile_stage_name", "sg_kernel_launches", "sg_render_backward_noalloc",
+           "sg_set_tuning", "sg_get_tuning")
 SG_NOALLOC_SCRATCH_BYTES = 16 << 20
 SG_PROFILE_EVENTS, SG_PROFILE_COUNT, SG_PROFILE_STAGES = 1, 2, 12
 
@@ -69,6 +70,11 @@ class sg_ws_layout(ctypes.Structure):
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class sg_tuning(ctypes.Structure):
+    _fields_ = [("fwd_pixels_per_thread", ctypes.c_int32), ("bwd_pixels_per_thread", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class SGError(RuntimeError):
@@ -119,6 +125,10 @@ def lib():
                                                  ctypes.c_int, _P, ctypes.c_size_t, _P, _P, _P,
                                                  ctypes.POINTER(sg_grads), _P]
         L.sg_render_backward_noalloc.restype = ctypes.c_int
+        L.sg_set_tuning.argtypes = [ctypes.POINTER(sg_tuning)]
+        L.sg_set_tuning.restype = ctypes.c_int
+        L.sg_get_tuning.argtypes = [ctypes.POINTER(sg_tuning)]
+        L.sg_get_tuning.restype = ctypes.c_int
         L.sg_kernel_launches.argtypes = []
         L.sg_kernel_launches.restype = ctypes.c_int64
         L.sg_profile_stage_name.argtypes = [ctypes.c_int]
@@ -329,3 +339,22 @@ def sg_render_backward_noalloc(scene: DeviceScene, cams, ws, T_final, last, d_im
     if raise_on_error:
         _check(st)
     return st
+
+
+def sg_set_tuning(fwd_pixels_per_thread=None, bwd_pixels_per_thread=None):
+    """Sets the blend kernels' pixels per thread; no arguments restores the defaults."""
+    if fwd_pixels_per_thread is None and bwd_pixels_per_thread is None:
+        _check(lib().sg_set_tuning(None))
+        return
+    cur = sg_get_tuning()
+    t = sg_tuning()
+    t.fwd_pixels_per_thread = int(fwd_pixels_per_thread or cur["fwd_pixels_per_thread"])
+    t.bwd_pixels_per_thread = int(bwd_pixels_per_thread or cur["bwd_pixels_per_thread"])
+    _check(lib().sg_set_tuning(ctypes.byref(t)))
+
+
+def sg_get_tuning() -> dict:
+    t = sg_tuning()
+    _check(lib().sg_get_tuning(ctypes.byref(t)))
+    return {"fwd_pixels_per_thread": int(t.fwd_pixels_per_thread),
+            "bwd_pixels_per_thread": int(t.bwd_pixels_per_thread)}

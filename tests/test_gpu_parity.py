@@ -167,6 +167,28 @@ def test_single_pixel_and_screen_covering_gaussian():
     run_parity(scene, [synth.make_camera(37, 29, 30.0)], seed=9)
 
 
+@pytest.mark.parametrize("ppt", [(1, 1), (2, 2), (4, 4), (8, 8), (2, 8), (8, 1)])
+def test_every_blend_shape(ppt):
+    """Every pixels-per-thread variant of both blend kernels against the oracle."""
+    rng = np.random.default_rng(600)
+    scene = synth.make_scene(rng, 5000, lobes=synth.LOBE_MIX, means="cube", cube_side=1.4,
+                             masks="uniform")
+    cam = synth.make_camera(70, 50, 70.0, bg=(0.3, 0.1, 0.2))
+    old = sgsplat.sg_get_tuning()
+    sgsplat.sg_set_tuning(*ppt)
+    try:
+        run_parity(scene, [cam], seed=12)
+    finally:
+        sgsplat.sg_set_tuning(old["fwd_pixels_per_thread"], old["bwd_pixels_per_thread"])
+
+
+def test_tuning_rejects_bad_shapes():
+    with pytest.raises(sgsplat.SGError):
+        sgsplat.sg_set_tuning(3, 4)
+    sgsplat.sg_set_tuning()
+    assert sgsplat.sg_get_tuning() == {"fwd_pixels_per_thread": 2, "bwd_pixels_per_thread": 4}
+
+
 def test_capacity_error_and_retry():
     scene, cams = synth.config0()
     ds = DeviceScene.from_host(scene)
