@@ -186,7 +186,7 @@ def test_tuning_rejects_bad_shapes():
     with pytest.raises(sgsplat.SGError):
         sgsplat.sg_set_tuning(3, 4)
     sgsplat.sg_set_tuning()
-    assert sgsplat.sg_get_tuning() == {"fwd_pixels_per_thread": 2, "bwd_pixels_per_thread": 4}
+    assert sgsplat.sg_get_tuning() == {"fwd_pixels_per_thread": 1, "bwd_pixels_per_thread": 4}
 
 
 def test_capacity_error_and_retry():
