@@ -55,13 +55,61 @@ struct Staged {
     float4 r[BATCH];
     float s[BATCH];
     uint32_t id[BATCH];
+    uint32_t mask[BATCH];   // sub-blocks of the tile the Gaussian can reach
 };
 
-__device__ __forceinline__ void stage(Staged &sm, int slot, const Rec &rc, uint32_t e) {
+// A 16x16 tile is 8 sub-blocks of 8x4 pixels: sub-block s covers columns
+// 8 (s & 1) .. +7 and rows 4 (s >> 1) .. +3 of the tile. Warp w's pixel slot j
+// is sub-block w * P + j, lane l its pixel (l & 7, l >> 3).
+constexpr int SUB_W = 8, SUB_H = 4;
+
+// Bit s set unless no pixel of sub-block s can reach alpha >= 1/255. The
+// region o' exp(-d^T Sigma^-1 d / 2) >= 1/255 is the ellipse
+// d^T Sigma^-1 d <= 2 ln(255 o'), whose bounding box has half extents
+// sqrt(2 ln(255 o') Sigma_xx) and sqrt(2 ln(255 o') Sigma_yy) with
+// Sigma = conic^-1. The box is padded (0.1 % + 0.05 px) so that pixels left
+// out are ones the alpha test would skip anyway: skipping them changes no
+// result.
+__device__ __forceinline__ uint32_t reach_mask(const Rec &rc, float x0, float y0) {
+    const float A = rc.a.z, B = rc.a.w, C = rc.b.x, op = rc.b.y;
+    const float detc = A * C - B * B;
+    const float k2 = 2.f * __logf(255.f * op);
+    if (!(detc > 0.f) || !(k2 >= 0.f)) return 0xFFu;
+    const float ex = sqrtf(k2 * C / detc) * 1.001f + 0.05f;
+    const float ey = sqrtf(k2 * A / detc) * 1.001f + 0.05f;
+    if (!isfinite(ex) || !isfinite(ey)) return 0xFFu;
+    const float xlo = rc.a.x - ex - x0, xhi = rc.a.x + ex - x0;
+    const float ylo = rc.a.y - ey - y0, yhi = rc.a.y + ey - y0;
+    uint32_t cols = 0u, rows = 0u;
+#pragma unroll
+    for (int sx = 0; sx < TILE / SUB_W; ++sx)
+        if (xhi >= (float)(sx * SUB_W) && xlo <= (float)(sx * SUB_W + SUB_W - 1)) cols |= 1u << sx;
+#pragma unroll
+    for (int sy = 0; sy < TILE / SUB_H; ++sy)
+        if (yhi >= (float)(sy * SUB_H) && ylo <= (float)(sy * SUB_H + SUB_H - 1)) rows |= 1u << sy;
+    uint32_t m = 0u;
+#pragma unroll
+    for (int sy = 0; sy < TILE / SUB_H; ++sy)
+        if (rows & (1u << sy)) m |= cols << (sy * (TILE / SUB_W));
+    return m;
+}
+
+template <bool CULL>
+__device__ __forceinline__ void stage(Staged &sm, int slot, const Rec &rc, uint32_t e, float x0, float y0) {
     sm.q[slot] = make_float4(rc.a.x, rc.a.y, -0.5f * LOG2E * rc.a.z, -LOG2E * rc.a.w);
     sm.r[slot] = make_float4(-0.5f * LOG2E * rc.b.x, rc.b.y, rc.b.z, rc.b.w);
     sm.s[slot] = rc.c.x;
     sm.id[slot] = e;
+    sm.mask[slot] = CULL ? reach_mask(rc, x0, y0) : 0xFFu;
+}
+
+// Pixel (column, row inside the tile) of slot j of this thread.
+template <int P>
+__device__ __forceinline__ void slot_pixel(int j, int &cx, int &cy) {
+    const int sub = (int)(threadIdx.x >> 5) * P + j;
+    const int lane = threadIdx.x & 31;
+    cx = SUB_W * (sub & 1) + (lane & (SUB_W - 1));
+    cy = SUB_H * (sub >> 1) + (lane / SUB_W);
 }
 
 struct PairEval {
@@ -100,8 +148,9 @@ __device__ __forceinline__ void add_evals(uint32_t ne, unsigned long long *evals
 // ---------------------------------------------------------------------------
 // K6 blend forward: one block per tile, P pixels per thread
 // ---------------------------------------------------------------------------
-// Thread t owns pixels t, t + NT, ..., t + (P-1) NT of the tile (NT = 256 / P
-// threads), so each warp store covers consecutive addresses.
+// Warp w owns sub-blocks w P .. w P + P - 1 of the tile, one 8x4 sub-block per
+// pixel slot, so that a Gaussian whose reach misses a sub-block is skipped by
+// the whole warp at once (NT = 256 / P threads per tile).
 template <int P, bool COUNT>
 __global__ void __launch_bounds__(BLEND_THREADS / P)
 k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
@@ -122,8 +171,9 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
     bool done[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-        const int i = (int)threadIdx.x + j * NT;
-        const int px = tx * TILE + (i & (TILE - 1)), py = ty * TILE + i / TILE;
+        int cx, cy;
+        slot_pixel<P>(j, cx, cy);
+        const int px = tx * TILE + cx, py = ty * TILE + cy;
         fpx[j] = (float)px;
         fpy[j] = (float)py;
         T[j] = 1.f;
@@ -131,6 +181,8 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
         lastc[j] = 0;
         done[j] = !(px < vw->W && py < vw->H);
     }
+    const int sub0 = (int)(threadIdx.x >> 5) * P;
+    const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
     uint32_t ne = 0;
     for (int base = 0; base < n; base += BATCH) {
         bool all = true;
@@ -140,15 +192,18 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
         const int cnt = min(BATCH, n - base);
         for (int k = threadIdx.x; k < cnt; k += NT) {
             const uint32_t e = pval[rg.x + base + k];
-            stage(sm, k, rec[e], e);
+            stage<!COUNT>(sm, k, rec[e], e, x0, y0);
         }
         __syncthreads();
         if (all) continue;
         for (int k = 0; k < cnt; ++k) {
+            const uint32_t msk = sm.mask[k] >> sub0;
+            if ((msk & ((1u << P) - 1u)) == 0u) continue;   // warp-uniform
             const float4 q = sm.q[k], r = sm.r[k];
             const float bl = sm.s[k];
 #pragma unroll
             for (int j = 0; j < P; ++j) {
+                if (!((msk >> j) & 1u)) continue;            // warp-uniform
                 if (done[j]) continue;
                 PairEval p;
                 eval_pair(fpx[j], fpy[j], q, r, p);
@@ -278,8 +333,9 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
     int tmax = 0;
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-        const int i = (int)threadIdx.x + j * NT;
-        const int px = tx * TILE + (i & (TILE - 1)), py = ty * TILE + i / TILE;
+        int cx, cy;
+        slot_pixel<P>(j, cx, cy);
+        const int px = tx * TILE + cx, py = ty * TILE + cy;
         fpx[j] = (float)px;
         fpy[j] = (float)py;
         T[j] = 1.f; Tfbg[j] = 0.f; g0[j] = g1[j] = g2[j] = 0.f; Sg[j] = 0.f; mylast[j] = 0;
@@ -302,6 +358,8 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
 #pragma unroll
     for (int i = 0; i < (NT + 31) / 32; ++i) maxlast = max(maxlast, smax[i]);
     uint32_t ne = 0;
+    const int sub0 = (int)(threadIdx.x >> 5) * P;
+    const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
 
     for (int end = maxlast; end > 0; end -= BATCH) {
         const int start = max(0, end - BATCH);
@@ -309,13 +367,15 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += NT) {
             const uint32_t e = pval[rg.x + start + k];
-            stage(sm, k, rec[e], e);
+            stage<!COUNT>(sm, k, rec[e], e, x0, y0);
         }
         __syncthreads();
         // warps whose pixels all end before this batch have nothing to add
         if (__all_sync(0xffffffffu, tmax <= start)) continue;
         for (int k = cnt - 1; k >= 0; --k) {
             const int pos = start + k;
+            const uint32_t msk = sm.mask[k] >> sub0;
+            if ((msk & ((1u << P) - 1u)) == 0u) continue;   // warp-uniform
             const float4 q = sm.q[k], r = sm.r[k];
             const float bl = sm.s[k];
             float v[9];
@@ -324,6 +384,7 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             bool any = false;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
+                if (!((msk >> j) & 1u)) continue;            // warp-uniform
                 if (pos >= mylast[j]) continue;
                 PairEval p;
                 eval_pair(fpx[j], fpy[j], q, r, p);
