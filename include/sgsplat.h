@@ -201,12 +201,17 @@ int sg_profile_read(double *ms, int64_t *launches, int64_t *pair_evals, int rese
  * pixels each blend thread owns, 1, 2, 4 or 8 (the block has 256 / P threads
  * per 16x16 tile). Larger P amortises the per-Gaussian shared-memory loads
  * and, in the backward, the warp reduction and atomics; smaller P gives more
- * threads to hide latency. sg_set_tuning(NULL) restores the defaults.
+ * threads to hide latency. *_persistent selects the persistent blend: one
+ * launch of resident blocks that take (view, tile) items from a work counter,
+ * tiles ordered by descending list length, instead of one block per tile.
+ * sg_set_tuning(NULL) restores the defaults.
  */
 typedef struct sg_tuning {
     int32_t fwd_pixels_per_thread;
     int32_t bwd_pixels_per_thread;
-    int32_t reserved[6];
+    int32_t fwd_persistent;   /* 1: resident blocks pull tiles, longest lists first */
+    int32_t bwd_persistent;
+    int32_t reserved[4];
 } sg_tuning;
 int sg_set_tuning(const sg_tuning *t);
 int sg_get_tuning(sg_tuning *t);
@@ -265,6 +270,33 @@ int sg_render_backward(const sg_scene *scene, const sg_camera *cams, int n_views
                        const void *ws, size_t ws_bytes, const float *T_final,
                        const int32_t *last, const float *d_img, void *bwd_ws,
                        size_t bwd_ws_bytes, const sg_grads *grads, void *stream);
+
+/*
+ * Batched form: n_scenes scenes (uneven sizes allowed, same storage types)
+ * rendered from n_views cameras in one call; view v shows scene
+ * view_scene[v] (host array). Views are packed as in sg_render_forward.
+ * The batched calls never synchronise the stream and launch fixed grids, so a
+ * forward + backward can be captured in a CUDA graph and replayed. The pair
+ * capacity comes from ws_bytes (sg_batched_workspace_query sizes it): when a
+ * forward needs more pairs, it skips binning and blending, records the need
+ * and sets its status to SG_ERR_CAPACITY in the workspace, where
+ * sg_forward_status reads them (that call synchronises). Gradients: one
+ * sg_grads per scene, each overwritten with the sum over that scene's views.
+ */
+int sg_batched_workspace_query(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
+                               const int32_t *view_scene, int n_views, uint64_t pair_capacity,
+                               sg_sizes *out);
+int sg_render_batched_forward(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
+                              const int32_t *view_scene, int n_views, void *ws, size_t ws_bytes,
+                              float *img, float *T_final, int32_t *last, void *stream);
+int sg_render_batched_backward(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
+                               const int32_t *view_scene, int n_views, const void *ws,
+                               size_t ws_bytes, const float *T_final, const int32_t *last,
+                               const float *d_img, void *bwd_ws, size_t bwd_ws_bytes,
+                               const sg_grads *grads, void *stream);
+/* Pairs the last forward on this workspace needed and its status (SG_OK or
+ * SG_ERR_CAPACITY). Synchronises `stream`. */
+int sg_forward_status(const void *ws, uint64_t *n_pairs, int32_t *status, void *stream);
 
 /*
  * Backward without caller scratch. The paper has no counterpart: this entry

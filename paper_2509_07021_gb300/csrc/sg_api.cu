@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -100,7 +101,7 @@ struct StageTimer {
 };
 
 // Process-wide kernel shape choices (sg_set_tuning); defaults from measurement.
-constexpr sg_tuning kDefaultTuning = {1, 4, {0, 0, 0, 0, 0, 0}};
+constexpr sg_tuning kDefaultTuning = {1, 4, 0, 0, {0, 0, 0, 0}};
 sg_tuning &tuning() {
     static sg_tuning t = kDefaultTuning;
     return t;
@@ -241,13 +242,17 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     L.dval1 = take(M * 4);
     L.offsets = take(M * 4);
     L.ranges = take(T * 8);
+    L.tok0 = take(T * 4);
+    L.tov0 = take(T * 4);
+    L.tok1 = take(T * 4);
+    L.tov1 = take(T * 4);
     L.fixed_end = o;
     // pair-capacity dependent tail; the backward only reads pval_final
     L.pval_final = take(cap * 4);
     L.pkey_final = take(cap * 4);
     L.pval_tmp = take(cap * 4);
     L.pkey_tmp = take(cap * 4);
-    const uint64_t items = M > cap ? M : cap;
+    const uint64_t items = std::max<uint64_t>(std::max<uint64_t>(M, cap), T);
     L.hist_blocks = (uint32_t)div_up(items, RS_TILE);
     L.hist = take((size_t)RS_RADIX * L.hist_blocks * 4);
     const uint64_t sums = div_up(items, SCAN_TILE) + div_up((uint64_t)RS_RADIX * L.hist_blocks, SCAN_TILE) + 1;
@@ -271,8 +276,45 @@ uint64_t capacity_for(const Batch &b, size_t ws_bytes) {
     return lo;
 }
 
-size_t bwd_bytes(const Batch &b) {
-    return al(sizeof(Batch)) + al(CNT_N * sizeof(uint64_t)) + al(9 * b.n_entries * sizeof(float));
+// Backward scratch: batch table, counters, [9][M] 2D gradients, then the
+// persistent blend's tile order (4 x T) and its radix histograms.
+struct BwdLayout {
+    size_t batch, counters, dg, tok0, tov0, tok1, tov1, hist, sums, total;
+};
+
+BwdLayout bwd_layout(const Batch &b) {
+    BwdLayout L{};
+    const uint64_t T = b.n_tiles;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
+    L.batch = take(sizeof(Batch));
+    L.counters = take(CNT_N * sizeof(uint64_t));
+    L.dg = take(9 * b.n_entries * sizeof(float));
+    L.tok0 = take(T * 4);
+    L.tov0 = take(T * 4);
+    L.tok1 = take(T * 4);
+    L.tov1 = take(T * 4);
+    const uint64_t hb = div_up(T, RS_TILE);
+    L.hist = take((size_t)RS_RADIX * hb * 4);
+    L.sums = take((div_up(T, SCAN_TILE) + div_up((uint64_t)RS_RADIX * hb, SCAN_TILE) + 1) * 8);
+    L.total = o;
+    return L;
+}
+
+size_t bwd_bytes(const Batch &b) { return bwd_layout(b).total; }
+
+// Blend shape of this call: pixels per thread from the tuning, and for the
+// persistent form the resident grid, the work counter and the tile order.
+int blend_shape(bool backward, const uint32_t *order, uint32_t *queue, BlendShape &sh) {
+    const sg_tuning &t = tuning();
+    sh.pixels_per_thread = backward ? t.bwd_pixels_per_thread : t.fwd_pixels_per_thread;
+    sh.persistent = (backward ? t.bwd_persistent : t.fwd_persistent) != 0;
+    sh.tile_order = sh.persistent ? order : nullptr;
+    sh.queue = queue;
+    sh.grid = sh.persistent ? blend_persistent_grid(backward, sh.pixels_per_thread) : 0;
+    if (sh.persistent && sh.grid <= 0)
+        return fail(SG_ERR_CUDA, "persistent blend: occupancy query failed");
+    return SG_OK;
 }
 
 void fill_sizes(const Batch &b, const WsLayout &L, uint64_t n_pairs, sg_sizes *out) {
@@ -288,9 +330,12 @@ void fill_sizes(const Batch &b, const WsLayout &L, uint64_t n_pairs, sg_sizes *o
     out->bwd_ws_bytes = bwd_bytes(b);
 }
 
+// sync = true: the plain form (one read of the pair count, SG_ERR_CAPACITY
+// returned to the caller). sync = false: the batched form (fixed grids sized by
+// the capacity, overflow recorded on the device, graph capturable).
 int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, const int32_t *view_scene,
                  int n_views, void *ws, size_t ws_bytes, float *img, float *T_final, int32_t *last,
-                 sg_sizes *out, cudaStream_t stream) {
+                 sg_sizes *out, cudaStream_t stream, bool sync) {
     std::unique_ptr<Batch> hb(new Batch);
     int st = build_batch(scenes, n_scenes, cams, view_scene, n_views, true, *hb);
     if (st != SG_OK) return st;
@@ -343,18 +388,22 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         StageTimer t(ST_OFFSETS, stream);
         SG_CUDA(launch_scan(tt, dval0, offs, M, sums, counters + CNT_PAIRS, stream), "pair offsets");
     }
-    uint64_t K = 0;
-    {
-        StageTimer t(ST_READ_PAIRS, stream);
-        SG_CUDA(cudaMemcpyAsync(&K, counters + CNT_PAIRS, sizeof(K), cudaMemcpyDeviceToHost, stream),
-                "read pairs");
-    }
-    SG_CUDA(cudaStreamSynchronize(stream), "read pairs");
-    if (K > cap || K >= (1ull << 32) - 1) {
-        const WsLayout need = make_layout(b, K);
-        fill_sizes(b, need, K, out);
-        return fail(SG_ERR_CAPACITY, "%llu pairs exceed the workspace capacity %llu (need %zu bytes)",
-                    (unsigned long long)K, (unsigned long long)cap, need.total);
+    uint64_t K = cap;   // batched form: grids sized by the capacity, counts read on the device
+    if (sync) {
+        {
+            StageTimer t(ST_READ_PAIRS, stream);
+            SG_CUDA(cudaMemcpyAsync(&K, counters + CNT_PAIRS, sizeof(K), cudaMemcpyDeviceToHost, stream),
+                    "read pairs");
+        }
+        SG_CUDA(cudaStreamSynchronize(stream), "read pairs");
+        if (K > cap || K >= (1ull << 32) - 1) {
+            const WsLayout need = make_layout(b, K);
+            fill_sizes(b, need, K, out);
+            return fail(SG_ERR_CAPACITY, "%llu pairs exceed the workspace capacity %llu (need %zu bytes)",
+                        (unsigned long long)K, (unsigned long long)cap, need.total);
+        }
+    } else {
+        SG_CUDA(launch_capacity_status(counters, cap, stream), "capacity status");
     }
     // duplicate into the buffer from which an even/odd number of tile passes ends in *_final
     uint32_t *pk_final = reinterpret_cast<uint32_t *>(w + L.pkey_final);
@@ -378,12 +427,23 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         StageTimer t(ST_RANGES, stream);
         SG_CUDA(launch_ranges(pk_final, counters, K, ranges, L.n_tiles, stream), "tile ranges");
     }
-    unsigned long long *evals = counting ? reinterpret_cast<unsigned long long *>(counters + 3) : nullptr;
+    unsigned long long *evals =
+        counting ? reinterpret_cast<unsigned long long *>(counters + CNT_EVALS) : nullptr;
     if (counting) SG_CUDA(cudaMemsetAsync(evals, 0, 8, stream), "clear counter");
+    BlendShape shape{};
+    st = blend_shape(false, reinterpret_cast<uint32_t *>(w + L.tov0),
+                     reinterpret_cast<uint32_t *>(counters + CNT_QUEUE), shape);
+    if (st != SG_OK) return st;
+    if (shape.persistent) {
+        StageTimer t(ST_RANGES, stream);
+        SG_CUDA(launch_tile_order(ranges, b.n_tiles, counters + CNT_TILES, reinterpret_cast<uint32_t *>(w + L.tok0),
+                                  reinterpret_cast<uint32_t *>(w + L.tov0), reinterpret_cast<uint32_t *>(w + L.tok1),
+                                  reinterpret_cast<uint32_t *>(w + L.tov1), hist, sums, stream),
+                "tile order");
+    }
     {
         StageTimer t(ST_BLEND_FWD, stream);
-        SG_CUDA(launch_blend_forward(db, b.n_tiles, ranges, pv_final, rec, img, T_final, last,
-                                     tuning().fwd_pixels_per_thread, evals,
+        SG_CUDA(launch_blend_forward(db, b.n_tiles, ranges, pv_final, rec, img, T_final, last, shape, evals,
                                      stream),
                 "blend forward");
     }
@@ -423,13 +483,19 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
     const uint2 *ranges = reinterpret_cast<const uint2 *>(w + L.ranges);
     const uint32_t *pv_final = reinterpret_cast<const uint32_t *>(w + L.pval_final);
     char *bw = static_cast<char *>(bwd_ws);
-    Batch *db = reinterpret_cast<Batch *>(bw);
-    uint64_t *counters = reinterpret_cast<uint64_t *>(bw + al(sizeof(Batch)));
-    float *dg = reinterpret_cast<float *>(bw + al(sizeof(Batch)) + al(CNT_N * sizeof(uint64_t)));
+    const BwdLayout BL = bwd_layout(b);
+    Batch *db = reinterpret_cast<Batch *>(bw + BL.batch);
+    uint64_t *counters = reinterpret_cast<uint64_t *>(bw + BL.counters);
+    float *dg = reinterpret_cast<float *>(bw + BL.dg);
     const uint64_t M = L.M;
 
     const bool counting = (prof().flags & SG_PROFILE_COUNT) != 0;
-    unsigned long long *evals = counting ? reinterpret_cast<unsigned long long *>(counters + 3) : nullptr;
+    unsigned long long *evals =
+        counting ? reinterpret_cast<unsigned long long *>(counters + CNT_EVALS) : nullptr;
+    BlendShape shape{};
+    st = blend_shape(true, reinterpret_cast<uint32_t *>(bw + BL.tov0),
+                     reinterpret_cast<uint32_t *>(counters + CNT_QUEUE), shape);
+    if (st != SG_OK) return st;
     {
         StageTimer t(ST_SETUP, stream);
         SG_CUDA(launch_setup(b, db, counters, stream), "setup");
@@ -438,10 +504,18 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
         StageTimer t(ST_BWD_CLEAR, stream);
         if (M > 0) SG_CUDA(cudaMemsetAsync(dg, 0, 9 * M * sizeof(float), stream), "clear 2D gradients");
     }
+    if (shape.persistent) {
+        StageTimer t(ST_BWD_CLEAR, stream);
+        SG_CUDA(launch_tile_order(ranges, b.n_tiles, counters + CNT_TILES, reinterpret_cast<uint32_t *>(bw + BL.tok0),
+                                  reinterpret_cast<uint32_t *>(bw + BL.tov0), reinterpret_cast<uint32_t *>(bw + BL.tok1),
+                                  reinterpret_cast<uint32_t *>(bw + BL.tov1), reinterpret_cast<uint32_t *>(bw + BL.hist),
+                                  reinterpret_cast<uint64_t *>(bw + BL.sums), stream),
+                "tile order");
+    }
     {
         StageTimer t(ST_BLEND_BWD, stream);
-        SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M,
-                                      tuning().bwd_pixels_per_thread, evals, stream),
+        SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M, shape,
+                                      evals, stream),
                 "blend backward");
     }
     {
@@ -558,7 +632,7 @@ int sg_render_forward(const sg_scene *scene, const sg_camera *cams, int n_views,
                       float *img, float *T_final, int32_t *last, sg_sizes *out, void *stream) {
     g_err[0] = '\0';
     return forward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, img, T_final, last, out,
-                        static_cast<cudaStream_t>(stream));
+                        static_cast<cudaStream_t>(stream), true);
 }
 
 int sg_render_backward(const sg_scene *scene, const sg_camera *cams, int n_views, const void *ws,
@@ -567,6 +641,50 @@ int sg_render_backward(const sg_scene *scene, const sg_camera *cams, int n_views
     g_err[0] = '\0';
     return backward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, T_final, last, d_img, bwd_ws,
                          bwd_ws_bytes, grads, static_cast<cudaStream_t>(stream));
+}
+
+int sg_batched_workspace_query(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
+                               const int32_t *view_scene, int n_views, uint64_t pair_capacity, sg_sizes *out) {
+    if (!out) return fail(SG_ERR_INVALID_ARG, "out must not be NULL");
+    if (!view_scene) return fail(SG_ERR_INVALID_ARG, "view_scene must not be NULL");
+    std::unique_ptr<Batch> hb(new Batch);
+    int st = build_batch(scenes, n_scenes, cams, view_scene, n_views, false, *hb);
+    if (st != SG_OK) return st;
+    if (pair_capacity >= (1ull << 32) - 1) return fail(SG_ERR_INVALID_ARG, "pair capacity too large");
+    fill_sizes(*hb, make_layout(*hb, pair_capacity), 0, out);
+    return SG_OK;
+}
+
+int sg_render_batched_forward(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
+                              const int32_t *view_scene, int n_views, void *ws, size_t ws_bytes, float *img,
+                              float *T_final, int32_t *last, void *stream) {
+    g_err[0] = '\0';
+    if (!view_scene) return fail(SG_ERR_INVALID_ARG, "view_scene must not be NULL");
+    return forward_impl(scenes, n_scenes, cams, view_scene, n_views, ws, ws_bytes, img, T_final, last, nullptr,
+                        static_cast<cudaStream_t>(stream), false);
+}
+
+int sg_render_batched_backward(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
+                               const int32_t *view_scene, int n_views, const void *ws, size_t ws_bytes,
+                               const float *T_final, const int32_t *last, const float *d_img, void *bwd_ws,
+                               size_t bwd_ws_bytes, const sg_grads *grads, void *stream) {
+    g_err[0] = '\0';
+    if (!view_scene) return fail(SG_ERR_INVALID_ARG, "view_scene must not be NULL");
+    return backward_impl(scenes, n_scenes, cams, view_scene, n_views, ws, ws_bytes, T_final, last, d_img, bwd_ws,
+                         bwd_ws_bytes, grads, static_cast<cudaStream_t>(stream));
+}
+
+int sg_forward_status(const void *ws, uint64_t *n_pairs, int32_t *status, void *stream) {
+    if (!ws || !aligned(ws, ALIGN)) return fail(SG_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+    // the counters sit right after the batch table, whatever the sizes
+    const uint64_t *counters = reinterpret_cast<const uint64_t *>(static_cast<const char *>(ws) + al(sizeof(Batch)));
+    uint64_t host[CNT_N] = {};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SG_CUDA(cudaMemcpyAsync(host, counters, sizeof(host), cudaMemcpyDeviceToHost, s), "read status");
+    SG_CUDA(cudaStreamSynchronize(s), "read status");
+    if (n_pairs) *n_pairs = host[CNT_PAIRS];
+    if (status) *status = (int32_t)host[CNT_STATUS];
+    return SG_OK;
 }
 
 }  // extern "C"
@@ -639,15 +757,18 @@ extern "C" int sg_render_backward_noalloc(const sg_scene *scene, const sg_camera
     const uint2 *ranges = reinterpret_cast<const uint2 *>(w + L.ranges);
     const uint32_t *pv_final = reinterpret_cast<const uint32_t *>(w + L.pval_final);
     char *bw = static_cast<char *>(scratch);
-    Batch *db = reinterpret_cast<Batch *>(bw);
-    uint64_t *counters = reinterpret_cast<uint64_t *>(bw + al(sizeof(Batch)));
-    float *dg = reinterpret_cast<float *>(bw + al(sizeof(Batch)) + al(CNT_N * sizeof(uint64_t)));
+    const BwdLayout BL = bwd_layout(b);
+    Batch *db = reinterpret_cast<Batch *>(bw + BL.batch);
+    uint64_t *counters = reinterpret_cast<uint64_t *>(bw + BL.counters);
+    float *dg = reinterpret_cast<float *>(bw + BL.dg);
     const uint64_t M = L.M;
+    BlendShape shape{};   // one block per tile: no tile order or work counter needed
+    shape.pixels_per_thread = tuning().bwd_pixels_per_thread;
     // the setup kernel rewrites the table and counters; the accumulators are cleared
     SG_CUDA(launch_setup(b, db, counters, stream), "setup");
     if (M > 0) SG_CUDA(cudaMemsetAsync(dg, 0, 9 * M * sizeof(float), stream), "clear 2D gradients");
-    SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M,
-                                  tuning().bwd_pixels_per_thread, nullptr, stream),
+    SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M, shape,
+                                  nullptr, stream),
             "blend backward");
     SG_CUDA(launch_preprocess_backward(b, db, tt, dg, M, stream), "preprocess backward");
     return SG_OK;

@@ -152,18 +152,17 @@ __device__ __forceinline__ void add_evals(uint32_t ne, unsigned long long *evals
 // pixel slot, so that a Gaussian whose reach misses a sub-block is skipped by
 // the whole warp at once (NT = 256 / P threads per tile).
 template <int P, bool COUNT>
-__global__ void __launch_bounds__(BLEND_THREADS / P)
-k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
-            const uint32_t *__restrict__ pval, const Rec *__restrict__ rec,
-            float *__restrict__ img, float *__restrict__ T_final, int32_t *__restrict__ last,
-            unsigned long long *__restrict__ evals) {
+__device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, Staged &sm,
+                                               const uint2 *__restrict__ ranges,
+                                               const uint32_t *__restrict__ pval,
+                                               const Rec *__restrict__ rec, float *__restrict__ img,
+                                               float *__restrict__ T_final, int32_t *__restrict__ last,
+                                               uint32_t &ne) {
     constexpr int NT = BLEND_THREADS / P;
-    __shared__ Staged sm;
-    const Batch &b = *bp;
     int tx, ty;
     const ViewDesc *vw;
-    tile_of_block(b, blockIdx.x, tx, ty, vw);
-    const uint2 rg = ranges[blockIdx.x];
+    tile_of_block(b, tile, tx, ty, vw);
+    const uint2 rg = ranges[tile];
     const int n = (int)(rg.y - rg.x);
 
     float fpx[P], fpy[P], T[P], c0[P], c1[P], c2[P];
@@ -183,7 +182,6 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
     }
     const int sub0 = (int)(threadIdx.x >> 5) * P;
     const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
-    uint32_t ne = 0;
     for (int base = 0; base < n; base += BATCH) {
         bool all = true;
 #pragma unroll
@@ -220,7 +218,6 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             }
         }
     }
-    if (COUNT) add_evals(ne, evals);
     const uint64_t HW = (uint64_t)vw->W * (uint64_t)vw->H;
     float *im = img + 3 * vw->pix_off;
 #pragma unroll
@@ -237,30 +234,72 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
     }
 }
 
-template <int P>
+// Persistent form: resident blocks pull tiles from a work counter in the
+// given order (longest lists first); otherwise one block per tile.
+template <int P, bool COUNT, bool PERSIST>
+__global__ void __launch_bounds__(BLEND_THREADS / P)
+k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
+            const uint32_t *__restrict__ pval, const Rec *__restrict__ rec,
+            float *__restrict__ img, float *__restrict__ T_final, int32_t *__restrict__ last,
+            const uint32_t *__restrict__ tile_order, uint32_t *__restrict__ queue, uint32_t n_tiles,
+            unsigned long long *__restrict__ evals) {
+    __shared__ Staged sm;
+    __shared__ uint32_t s_item;
+    const Batch &b = *bp;
+    uint32_t ne = 0;
+    if (!PERSIST) {
+        blend_fwd_tile<P, COUNT>(b, blockIdx.x, sm, ranges, pval, rec, img, T_final, last, ne);
+    } else {
+        for (;;) {
+            if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+            __syncthreads();
+            const uint32_t item = s_item;
+            __syncthreads();
+            if (item >= n_tiles) break;
+            blend_fwd_tile<P, COUNT>(b, tile_order ? tile_order[item] : item, sm, ranges, pval, rec, img,
+                                     T_final, last, ne);
+        }
+    }
+    if (COUNT) add_evals(ne, evals);
+}
+
+template <int P, bool PERSIST>
 static void fwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval,
-                  const Rec *rec, float *img, float *T_final, int32_t *last, unsigned long long *evals,
-                  cudaStream_t s) {
+                  const Rec *rec, float *img, float *T_final, int32_t *last, const BlendShape &sh,
+                  unsigned long long *evals, cudaStream_t s) {
+    const unsigned grid = PERSIST ? (unsigned)sh.grid : n_tiles;
     if (evals)
-        k_blend_fwd<P, true><<<n_tiles, BLEND_THREADS / P, 0, s>>>(db, ranges, pval, rec, img, T_final,
-                                                                  last, evals);
+        k_blend_fwd<P, true, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
+            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, evals);
     else
-        k_blend_fwd<P, false><<<n_tiles, BLEND_THREADS / P, 0, s>>>(db, ranges, pval, rec, img, T_final,
-                                                                   last, nullptr);
+        k_blend_fwd<P, false, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
+            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, nullptr);
+}
+
+template <bool PERSIST>
+static cudaError_t fwd_dispatch(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval,
+                                const Rec *rec, float *img, float *T_final, int32_t *last,
+                                const BlendShape &sh, unsigned long long *evals, cudaStream_t s) {
+    switch (sh.pixels_per_thread) {
+        case 1: fwd_p<1, PERSIST>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s); break;
+        case 2: fwd_p<2, PERSIST>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s); break;
+        case 4: fwd_p<4, PERSIST>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s); break;
+        case 8: fwd_p<8, PERSIST>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
                                  const uint32_t *pval, const Rec *rec, float *img, float *T_final,
-                                 int32_t *last, int pixels_per_thread, unsigned long long *evals,
+                                 int32_t *last, const BlendShape &sh, unsigned long long *evals,
                                  cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
-    switch (pixels_per_thread) {
-        case 1: fwd_p<1>(db, n_tiles, ranges, pval, rec, img, T_final, last, evals, s); break;
-        case 2: fwd_p<2>(db, n_tiles, ranges, pval, rec, img, T_final, last, evals, s); break;
-        case 4: fwd_p<4>(db, n_tiles, ranges, pval, rec, img, T_final, last, evals, s); break;
-        case 8: fwd_p<8>(db, n_tiles, ranges, pval, rec, img, T_final, last, evals, s); break;
-        default: return cudaErrorInvalidValue;
-    }
+    const bool persist = sh.persistent;
+    if (persist && (sh.grid <= 0 || sh.queue == nullptr)) return cudaErrorInvalidValue;
+    cudaError_t e = persist ? fwd_dispatch<true>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s)
+                            : fwd_dispatch<false>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     return cudaGetLastError();
 }
@@ -311,20 +350,19 @@ __device__ __forceinline__ void warp_sum9_atomic(const float v[9], float *dg, ui
 // atomics. Accumulated per pair (in dg order):
 //   0,1: dL/dx, dL/dy   2..4: dL/dA, dL/dB, dL/dC   5: dL/do'   6..8: dL/drgb
 template <int P, bool COUNT>
-__global__ void __launch_bounds__(BLEND_THREADS / P)
-k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
-            const uint32_t *__restrict__ pval, const Rec *__restrict__ rec,
-            const float *__restrict__ T_final, const int32_t *__restrict__ last,
-            const float *__restrict__ d_img, float *__restrict__ dg, uint64_t M,
-            unsigned long long *__restrict__ evals) {
+__device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, Staged &sm, int *smax,
+                                               const uint2 *__restrict__ ranges,
+                                               const uint32_t *__restrict__ pval,
+                                               const Rec *__restrict__ rec,
+                                               const float *__restrict__ T_final,
+                                               const int32_t *__restrict__ last,
+                                               const float *__restrict__ d_img, float *__restrict__ dg,
+                                               uint64_t M, uint32_t &ne) {
     constexpr int NT = BLEND_THREADS / P;
-    __shared__ Staged sm;
-    __shared__ int smax[(NT + 31) / 32];
-    const Batch &b = *bp;
     int tx, ty;
     const ViewDesc *vw;
-    tile_of_block(b, blockIdx.x, tx, ty, vw);
-    const uint2 rg = ranges[blockIdx.x];
+    tile_of_block(b, tile, tx, ty, vw);
+    const uint2 rg = ranges[tile];
     const uint64_t HW = (uint64_t)vw->W * (uint64_t)vw->H;
     const float *gi = d_img + 3 * vw->pix_off;
 
@@ -357,7 +395,6 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
     int maxlast = 0;
 #pragma unroll
     for (int i = 0; i < (NT + 31) / 32; ++i) maxlast = max(maxlast, smax[i]);
-    uint32_t ne = 0;
     const int sub0 = (int)(threadIdx.x >> 5) * P;
     const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
 
@@ -426,35 +463,118 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             }
         }
     }
+}
+
+template <int P, bool COUNT, bool PERSIST>
+__global__ void __launch_bounds__(BLEND_THREADS / P)
+k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
+            const uint32_t *__restrict__ pval, const Rec *__restrict__ rec,
+            const float *__restrict__ T_final, const int32_t *__restrict__ last,
+            const float *__restrict__ d_img, float *__restrict__ dg, uint64_t M,
+            const uint32_t *__restrict__ tile_order, uint32_t *__restrict__ queue, uint32_t n_tiles,
+            unsigned long long *__restrict__ evals) {
+    constexpr int NT = BLEND_THREADS / P;
+    __shared__ Staged sm;
+    __shared__ int smax[(NT + 31) / 32];
+    __shared__ uint32_t s_item;
+    const Batch &b = *bp;
+    uint32_t ne = 0;
+    if (!PERSIST) {
+        blend_bwd_tile<P, COUNT>(b, blockIdx.x, sm, smax, ranges, pval, rec, T_final, last, d_img, dg, M, ne);
+    } else {
+        for (;;) {
+            if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+            __syncthreads();
+            const uint32_t item = s_item;
+            __syncthreads();
+            if (item >= n_tiles) break;
+            blend_bwd_tile<P, COUNT>(b, tile_order ? tile_order[item] : item, sm, smax, ranges, pval, rec,
+                                     T_final, last, d_img, dg, M, ne);
+        }
+    }
     if (COUNT) add_evals(ne, evals);
 }
 
-template <int P>
+template <int P, bool PERSIST>
 static void bwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval,
                   const Rec *rec, const float *T_final, const int32_t *last, const float *d_img, float *dg,
-                  uint64_t M, unsigned long long *evals, cudaStream_t s) {
+                  uint64_t M, const BlendShape &sh, unsigned long long *evals, cudaStream_t s) {
+    const unsigned grid = PERSIST ? (unsigned)sh.grid : n_tiles;
     if (evals)
-        k_blend_bwd<P, true><<<n_tiles, BLEND_THREADS / P, 0, s>>>(db, ranges, pval, rec, T_final, last,
-                                                                  d_img, dg, M, evals);
+        k_blend_bwd<P, true, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
+            db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, evals);
     else
-        k_blend_bwd<P, false><<<n_tiles, BLEND_THREADS / P, 0, s>>>(db, ranges, pval, rec, T_final, last,
-                                                                   d_img, dg, M, nullptr);
+        k_blend_bwd<P, false, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
+            db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, nullptr);
+}
+
+template <bool PERSIST>
+static cudaError_t bwd_dispatch(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval,
+                                const Rec *rec, const float *T_final, const int32_t *last, const float *d_img,
+                                float *dg, uint64_t M, const BlendShape &sh, unsigned long long *evals,
+                                cudaStream_t s) {
+    switch (sh.pixels_per_thread) {
+        case 1: bwd_p<1, PERSIST>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, sh, evals, s); break;
+        case 2: bwd_p<2, PERSIST>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, sh, evals, s); break;
+        case 4: bwd_p<4, PERSIST>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, sh, evals, s); break;
+        case 8: bwd_p<8, PERSIST>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, sh, evals, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_blend_backward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
                                   const uint32_t *pval, const Rec *rec, const float *T_final,
                                   const int32_t *last, const float *d_img, float *dg, uint64_t M,
-                                  int pixels_per_thread, unsigned long long *evals, cudaStream_t s) {
+                                  const BlendShape &sh, unsigned long long *evals, cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
-    switch (pixels_per_thread) {
-        case 1: bwd_p<1>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, evals, s); break;
-        case 2: bwd_p<2>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, evals, s); break;
-        case 4: bwd_p<4>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, evals, s); break;
-        case 8: bwd_p<8>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, evals, s); break;
-        default: return cudaErrorInvalidValue;
-    }
+    const bool persist = sh.persistent;
+    if (persist && (sh.grid <= 0 || sh.queue == nullptr)) return cudaErrorInvalidValue;
+    cudaError_t e = persist
+        ? bwd_dispatch<true>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, sh, evals, s)
+        : bwd_dispatch<false>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, sh, evals, s);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// persistent grid: resident blocks per SM (occupancy) x SMs, per device
+// ---------------------------------------------------------------------------
+template <typename K>
+static int occupancy_grid(K kernel, int threads) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess) return 0;
+    return sms * (per > 0 ? per : 1);
+}
+
+int blend_persistent_grid(bool backward, int p) {
+    // cached per (device, direction, shape); devices beyond 16 are computed each time
+    static int cache[16][2][9] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool cacheable = dev >= 0 && dev < 16 && p >= 1 && p <= 8;
+    if (cacheable && cache[dev][backward][p]) return cache[dev][backward][p];
+    int g = 0;
+    if (!backward) {
+        switch (p) {
+            case 1: g = occupancy_grid(k_blend_fwd<1, false, true>, 256); break;
+            case 2: g = occupancy_grid(k_blend_fwd<2, false, true>, 128); break;
+            case 4: g = occupancy_grid(k_blend_fwd<4, false, true>, 64); break;
+            case 8: g = occupancy_grid(k_blend_fwd<8, false, true>, 32); break;
+        }
+    } else {
+        switch (p) {
+            case 1: g = occupancy_grid(k_blend_bwd<1, false, true>, 256); break;
+            case 2: g = occupancy_grid(k_blend_bwd<2, false, true>, 128); break;
+            case 4: g = occupancy_grid(k_blend_bwd<4, false, true>, 64); break;
+            case 8: g = occupancy_grid(k_blend_bwd<8, false, true>, 32); break;
+        }
+    }
+    if (cacheable && g > 0) cache[dev][backward][p] = g;
+    return g;
 }
 
 }  // namespace sgk

@@ -65,7 +65,15 @@ struct __align__(16) Rec {
 };
 
 // Device counters kept in the workspace.
-enum : int { CNT_ENTRIES = 0, CNT_PAIRS = 1, CNT_STATUS = 2, CNT_N = 4 };
+enum : int {
+    CNT_ENTRIES = 0,   // (view, Gaussian) entries
+    CNT_PAIRS = 1,     // (tile, Gaussian) pairs of the forward
+    CNT_STATUS = 2,    // sg_status of the last batched forward
+    CNT_EVALS = 3,     // pair evaluations (counting kernels)
+    CNT_TILES = 4,     // tiles
+    CNT_QUEUE = 5,     // persistent-blend work counter
+    CNT_N = 8
+};
 
 // Radix sort / scan geometry.
 constexpr int RS_THREADS = 256;
@@ -78,7 +86,7 @@ constexpr int SCAN_TILE = 4096;
 // forward and the backward of one call).
 struct WsLayout {
     size_t batch, counters, rec, tiles_touched, rect, dkey0, dval0, dkey1, dval1,
-        offsets, ranges, scan_sums, hist, fixed_end;
+        offsets, ranges, tok0, tov0, tok1, tov1, scan_sums, hist, fixed_end;
     size_t pval_final, pkey_final, pval_tmp, pkey_tmp, total;
     uint64_t M, n_tiles, cap;
     uint32_t hist_blocks;     // radix blocks of the larger sort
@@ -117,15 +125,32 @@ cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted
                              uint32_t *pkey, uint32_t *pval, int n_views, cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64_t cap,
                           uint2 *ranges, uint64_t n_tiles, cudaStream_t s);
+// Tiles sorted by descending list length into v0 (k0..v1: n_tiles each).
+cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, const uint64_t *n_tiles_dev,
+                              uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
+                              uint64_t *scan_sums, cudaStream_t s);
+// counters[CNT_STATUS] = SG_ERR_CAPACITY when the pairs exceed cap.
+cudaError_t launch_capacity_status(uint64_t *counters, uint64_t cap, cudaStream_t s);
+
+// Blend launch shape.
+struct BlendShape {
+    int pixels_per_thread;
+    bool persistent;              // resident blocks pull tiles from *queue
+    const uint32_t *tile_order;   // persistent: tiles in this order (null: natural order)
+    uint32_t *queue;              // persistent: zeroed work counter
+    int grid;                     // persistent: resident blocks
+};
 
 cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
                                  const uint32_t *pval, const Rec *rec, float *img,
-                                 float *T_final, int32_t *last, int pixels_per_thread,
+                                 float *T_final, int32_t *last, const BlendShape &shape,
                                  unsigned long long *evals, cudaStream_t s);
 cudaError_t launch_blend_backward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
                                   const uint32_t *pval, const Rec *rec, const float *T_final,
                                   const int32_t *last, const float *d_img, float *dg,
-                                  uint64_t M, int pixels_per_thread, unsigned long long *evals,
+                                  uint64_t M, const BlendShape &shape, unsigned long long *evals,
                                   cudaStream_t s);
+// Resident blocks per SM x SMs for the persistent blend of this shape.
+int blend_persistent_grid(bool backward, int pixels_per_thread);
 
 }  // namespace sgk

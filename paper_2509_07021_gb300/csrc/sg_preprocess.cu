@@ -197,15 +197,21 @@ __device__ __forceinline__ int find_block_scene(const Batch &b, uint32_t blk) {
 // setup: copy the batch table into the workspace, seed the counters
 // ---------------------------------------------------------------------------
 __global__ void k_setup(const Batch b, Batch *dst, uint64_t *counters) {
+    // header and the used views / scenes only
     const uint32_t *src = reinterpret_cast<const uint32_t *>(&b);
     uint32_t *d = reinterpret_cast<uint32_t *>(dst);
-    constexpr int words = sizeof(Batch) / 4;
-    for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = src[i];
+    const int head = (int)(offsetof(Batch, view) / 4);
+    const int vw0 = head, vw1 = (int)((offsetof(Batch, view) + b.n_views * sizeof(ViewDesc)) / 4);
+    const int sc0 = (int)(offsetof(Batch, scene) / 4);
+    const int sc1 = (int)((offsetof(Batch, scene) + b.n_scenes * sizeof(SceneDesc)) / 4);
+    for (int i = threadIdx.x; i < head; i += blockDim.x) d[i] = src[i];
+    for (int i = vw0 + threadIdx.x; i < vw1; i += blockDim.x) d[i] = src[i];
+    for (int i = sc0 + threadIdx.x; i < sc1; i += blockDim.x) d[i] = src[i];
+    if (threadIdx.x < CNT_N) counters[threadIdx.x] = 0;
+    __syncthreads();
     if (threadIdx.x == 0) {
         counters[CNT_ENTRIES] = b.n_entries;
-        counters[CNT_PAIRS] = 0;
-        counters[CNT_STATUS] = 0;
-        counters[3] = 0;
+        counters[CNT_TILES] = b.n_tiles;
     }
 }
 

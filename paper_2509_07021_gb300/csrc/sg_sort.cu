@@ -150,15 +150,18 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 // ---------------------------------------------------------------------------
 // stable LSD radix sort, 8-bit digits, 4096 keys per block
 // ---------------------------------------------------------------------------
+// Item counts come from the device (*n_dev) and are clamped to the capacity
+// the launch was sized for (max_n), so an overflowing count can never index
+// past the buffers.
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t *__restrict__ keys,
                                                            const uint64_t *__restrict__ n_dev,
-                                                           int shift, uint32_t mask,
+                                                           uint64_t max_n, int shift, uint32_t mask,
                                                            uint32_t *__restrict__ hist,
                                                            uint32_t nblocks) {
     __shared__ uint32_t h[RS_RADIX];
     h[threadIdx.x] = 0u;
     __syncthreads();
-    const uint64_t n = *n_dev;
+    const uint64_t n = min(*n_dev, max_n);
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
     if (base < n) {
 #pragma unroll 4
@@ -173,8 +176,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t *__res
 
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, const uint64_t *__restrict__ n_dev, int shift, uint32_t mask,
-    const uint32_t *__restrict__ hist_scan, uint32_t nblocks) {
+    uint32_t *__restrict__ vout, const uint64_t *__restrict__ n_dev, uint64_t max_n, int shift,
+    uint32_t mask, const uint32_t *__restrict__ hist_scan, uint32_t nblocks) {
     constexpr int NW = RS_THREADS / 32;
     constexpr int PER_WARP = RS_TILE / NW;   // 512 consecutive keys per warp
     __shared__ uint32_t cnt[NW][RS_RADIX];
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     __shared__ uint32_t sv[RS_TILE];
     __shared__ uint32_t shs[33];
 
-    const uint64_t n = *n_dev;
+    const uint64_t n = min(*n_dev, max_n);
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
     if (base >= n) return;   // uniform across the block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -263,12 +266,13 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
         const int shift = 8 * p;
         const int nb = min(8, bits - shift);
         const uint32_t mask = (1u << nb) - 1u;
-        k_radix_hist<<<nblocks, RS_THREADS, 0, s>>>(ki, n_dev, shift, mask, hist, nblocks);
+        k_radix_hist<<<nblocks, RS_THREADS, 0, s>>>(ki, n_dev, max_n, shift, mask, hist, nblocks);
         count_launches(1);
         cudaError_t e = launch_scan(hist, nullptr, hist, (uint64_t)RS_RADIX * nblocks, scan_sums,
                                     nullptr, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n_dev, shift, mask, hist, nblocks);
+        k_radix_scatter<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n_dev, max_n, shift, mask, hist,
+                                                       nblocks);
         count_launches(1);
         uint32_t *t;
         t = ki; ki = ko; ko = t;
@@ -351,6 +355,39 @@ cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64
     if (e != cudaSuccess) return e;
     if (cap == 0) return cudaSuccess;
     k_ranges<<<(unsigned)div_up(cap, 256), 256, 0, s>>>(pkey, counters, cap, ranges);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// work order of the persistent blend: tiles by descending list length
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_tile_keys(const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                                   uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const uint2 r = ranges[t];
+    const uint32_t len = r.y - r.x;
+    keys[t] = 0xFFFFu - min(len >> 2, 0xFFFFu);   // 16-bit, longest first
+    vals[t] = t;
+}
+
+cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, const uint64_t *n_tiles_dev,
+                              uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
+                              uint64_t *scan_sums, cudaStream_t s) {
+    if (n_tiles == 0) return cudaSuccess;
+    k_tile_keys<<<(unsigned)div_up(n_tiles, 256), 256, 0, s>>>(ranges, n_tiles, k0, v0);
+    count_launches(1);
+    // two stable 8-bit passes: the order ends in (k0, v0)
+    return launch_radix_sort(k0, v0, k1, v1, n_tiles_dev, n_tiles, 16, hist, scan_sums, s);
+}
+
+__global__ void k_capacity_status(uint64_t *counters, uint64_t cap) {
+    if (counters[CNT_PAIRS] > cap) counters[CNT_STATUS] = (uint64_t)SG_ERR_CAPACITY;
+}
+
+cudaError_t launch_capacity_status(uint64_t *counters, uint64_t cap, cudaStream_t s) {
+    k_capacity_status<<<1, 1, 0, s>>>(counters, cap);
     count_launches(1);
     return cudaGetLastError();
 }

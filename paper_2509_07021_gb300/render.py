@@ -7,6 +7,7 @@ from __future__ import annotations
 
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import sgsplat as _sg
@@ -123,3 +124,99 @@ def rasterize(scene: DeviceScene, cams):
     return SGRasterize.apply(scene.means, scene.scales, scene.quats, scene.opac, scene.gmask,
                              scene.c0, scene.lobe_off, scene.axis, scene.sharp, scene.amp,
                              scene.lmask, cams)
+
+
+class BatchedRenderer:
+    """Several scenes x cameras in one forward and one backward call.
+
+    view_scene[v] is the scene of camera v. Outputs are flat and packed view
+    after view: img [3 * sum HW] (each view [3][H][W]), T_final and last
+    [sum HW]. The pair capacity is sized once (a probe forward records the
+    need) with `headroom`; afterwards no call synchronises the host, so
+    forward -> loss gradient -> backward can be captured in one CUDA graph.
+    """
+
+    def __init__(self, scenes, cams, view_scene, headroom=1.15, pair_capacity=None):
+        self.scenes = list(scenes)
+        self.cams = list(cams)
+        self.view_scene = [int(v) for v in view_scene]
+        dev = self.scenes[0].means.device
+        self.device = dev
+        self.npix = [int(c.width) * int(c.height) for c in self.cams]
+        self.offsets = np.concatenate([[0], np.cumsum(self.npix)]).astype(np.int64)
+        P = int(self.offsets[-1])
+        self.img = torch.zeros(3 * P, device=dev)
+        self.T_final = torch.ones(P, device=dev)
+        self.last = torch.zeros(P, dtype=torch.int32, device=dev)
+        self.d_img = torch.zeros(3 * P, device=dev)
+        self.grads = [alloc_grads(sc) for sc in self.scenes]
+        if pair_capacity is None:
+            pair_capacity = self._probe_pairs()
+        self.capacity = int(pair_capacity * headroom) + 4096
+        self.sizes = _sg.sg_batched_workspace_query(self.scenes, self.cams, self.view_scene, self.capacity)
+        self.ws = torch.empty(self.sizes["ws_bytes"], dtype=torch.uint8, device=dev)
+        self.bwd = torch.empty(self.sizes["bwd_ws_bytes"], dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    def _probe_pairs(self):
+        q = _sg.sg_batched_workspace_query(self.scenes, self.cams, self.view_scene, 0)
+        ws = torch.empty(q["ws_bytes"], dtype=torch.uint8, device=self.device)
+        _sg.sg_render_batched_forward(self.scenes, self.cams, self.view_scene, ws, self.img,
+                                      self.T_final, self.last)
+        n, _ = _sg.sg_forward_status(ws)
+        return n
+
+    def view_image(self, v):
+        o, n = int(self.offsets[v]), self.npix[v]
+        c = self.cams[v]
+        return self.img[3 * o:3 * (o + n)].view(3, c.height, c.width)
+
+    def forward(self):
+        _sg.sg_render_batched_forward(self.scenes, self.cams, self.view_scene, self.ws, self.img,
+                                      self.T_final, self.last)
+        return self.img
+
+    def backward(self, d_img=None):
+        if d_img is not None and d_img.data_ptr() != self.d_img.data_ptr():
+            self.d_img.copy_(d_img.reshape(-1))
+        _sg.sg_render_batched_backward(self.scenes, self.cams, self.view_scene, self.ws, self.T_final,
+                                       self.last, self.d_img, self.bwd, self.grads)
+        return self.grads
+
+    def status(self):
+        """(pairs the last forward needed, SG_OK or SG_ERR_CAPACITY); synchronises."""
+        return _sg.sg_forward_status(self.ws)
+
+    def step(self, loss_grad=None):
+        """forward, d_img = loss_grad(img) (written in place), backward."""
+        self.forward()
+        if loss_grad is not None:
+            loss_grad(self.img, self.d_img)
+        self.backward()
+
+    def capture(self, loss_grad=None, warmup=2):
+        """Captures step(loss_grad) in a CUDA graph; replay() runs it."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.step(loss_grad)
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step(loss_grad)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+
+
+def l1_loss_grad(renderer: BatchedRenderer, targets):
+    """Upstream gradient of the per-view mean L1 loss against `targets`
+    (flat, packed like img), summed over views: sign(img - target) / (3 H W)."""
+    scale = torch.cat([torch.full((3 * n,), 1.0 / (3 * n), device=renderer.device)
+                       for n in renderer.npix])
+
+    def fn(img, out):
+        torch.mul(torch.sign(img - targets), scale, out=out)
+    return fn

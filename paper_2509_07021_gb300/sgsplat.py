@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_WORKSPACE", 3: "
 EXPORTS = ("sg_version", "sg_last_error", "sg_workspace_query", "sg_workspace_layout",
            "sg_render_forward", "sg_render_backward", "sg_profile_enable", "sg_profile_read",
            "sg_profile_stage_name", "sg_kernel_launches", "sg_render_backward_noalloc",
-           "sg_set_tuning", "sg_get_tuning")
+           "sg_set_tuning", "sg_get_tuning", "sg_batched_workspace_query",
+           "sg_render_batched_forward", "sg_render_batched_backward", "sg_forward_status")
 SG_NOALLOC_SCRATCH_BYTES = 16 << 20
 SG_PROFILE_EVENTS, SG_PROFILE_COUNT, SG_PROFILE_STAGES = 1, 2, 12
 
@@ -74,7 +75,8 @@ class sg_ws_layout(ctypes.Structure):
 
 class sg_tuning(ctypes.Structure):
     _fields_ = [("fwd_pixels_per_thread", ctypes.c_int32), ("bwd_pixels_per_thread", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("fwd_persistent", ctypes.c_int32), ("bwd_persistent", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class SGError(RuntimeError):
@@ -129,6 +131,18 @@ def lib():
         L.sg_set_tuning.restype = ctypes.c_int
         L.sg_get_tuning.argtypes = [ctypes.POINTER(sg_tuning)]
         L.sg_get_tuning.restype = ctypes.c_int
+        PS, PC = ctypes.POINTER(sg_scene), ctypes.POINTER(sg_camera)
+        L.sg_batched_workspace_query.argtypes = [PS, ctypes.c_int, PC, _P, ctypes.c_int, ctypes.c_uint64,
+                                                 ctypes.POINTER(sg_sizes)]
+        L.sg_batched_workspace_query.restype = ctypes.c_int
+        L.sg_render_batched_forward.argtypes = [PS, ctypes.c_int, PC, _P, ctypes.c_int, _P, ctypes.c_size_t,
+                                                _P, _P, _P, _P]
+        L.sg_render_batched_forward.restype = ctypes.c_int
+        L.sg_render_batched_backward.argtypes = [PS, ctypes.c_int, PC, _P, ctypes.c_int, _P, ctypes.c_size_t,
+                                                 _P, _P, _P, _P, ctypes.c_size_t, ctypes.POINTER(sg_grads), _P]
+        L.sg_render_batched_backward.restype = ctypes.c_int
+        L.sg_forward_status.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32), _P]
+        L.sg_forward_status.restype = ctypes.c_int
         L.sg_kernel_launches.argtypes = []
         L.sg_kernel_launches.restype = ctypes.c_int64
         L.sg_profile_stage_name.argtypes = [ctypes.c_int]
@@ -341,15 +355,19 @@ def sg_render_backward_noalloc(scene: DeviceScene, cams, ws, T_final, last, d_im
     return st
 
 
-def sg_set_tuning(fwd_pixels_per_thread=None, bwd_pixels_per_thread=None):
-    """Sets the blend kernels' pixels per thread; no arguments restores the defaults."""
-    if fwd_pixels_per_thread is None and bwd_pixels_per_thread is None:
+def sg_set_tuning(fwd_pixels_per_thread=None, bwd_pixels_per_thread=None, fwd_persistent=None,
+                  bwd_persistent=None):
+    """Sets the blend kernels' shapes (unset fields keep their value); no
+    arguments restores the defaults."""
+    args = (fwd_pixels_per_thread, bwd_pixels_per_thread, fwd_persistent, bwd_persistent)
+    if all(a is None for a in args):
         _check(lib().sg_set_tuning(None))
         return
     cur = sg_get_tuning()
     t = sg_tuning()
-    t.fwd_pixels_per_thread = int(fwd_pixels_per_thread or cur["fwd_pixels_per_thread"])
-    t.bwd_pixels_per_thread = int(bwd_pixels_per_thread or cur["bwd_pixels_per_thread"])
+    for name, val in zip(("fwd_pixels_per_thread", "bwd_pixels_per_thread", "fwd_persistent",
+                          "bwd_persistent"), args):
+        setattr(t, name, int(cur[name] if val is None else val))
     _check(lib().sg_set_tuning(ctypes.byref(t)))
 
 
@@ -357,4 +375,54 @@ def sg_get_tuning() -> dict:
     t = sg_tuning()
     _check(lib().sg_get_tuning(ctypes.byref(t)))
     return {"fwd_pixels_per_thread": int(t.fwd_pixels_per_thread),
-            "bwd_pixels_per_thread": int(t.bwd_pixels_per_thread)}
+            "bwd_pixels_per_thread": int(t.bwd_pixels_per_thread),
+            "fwd_persistent": int(t.fwd_persistent), "bwd_persistent": int(t.bwd_persistent)}
+
+
+# ---------------------------------------------------------------------------
+# batched form
+# ---------------------------------------------------------------------------
+
+def scene_array(scenes):
+    arr = (sg_scene * len(scenes))()
+    for i, sc in enumerate(scenes):
+        arr[i] = sc.struct()
+    return arr
+
+
+def _view_scene_array(view_scene):
+    return (ctypes.c_int32 * len(view_scene))(*[int(v) for v in view_scene])
+
+
+def sg_batched_workspace_query(scenes, cams, view_scene, pair_capacity: int) -> dict:
+    out = sg_sizes()
+    _check(lib().sg_batched_workspace_query(scene_array(scenes), len(scenes), camera_array(cams),
+                                            _view_scene_array(view_scene), len(cams),
+                                            int(pair_capacity), ctypes.byref(out)))
+    return out.as_dict()
+
+
+def sg_render_batched_forward(scenes, cams, view_scene, ws, img, T_final, last, stream=None):
+    _check(lib().sg_render_batched_forward(scene_array(scenes), len(scenes), camera_array(cams),
+                                           _view_scene_array(view_scene), len(cams), _ptr(ws),
+                                           ws.numel(), _ptr(img), _ptr(T_final), _ptr(last),
+                                           _stream_handle(stream)))
+
+
+def sg_render_batched_backward(scenes, cams, view_scene, ws, T_final, last, d_img, bwd_ws,
+                               grads_list, stream=None):
+    g = (sg_grads * len(grads_list))()
+    for i, gd in enumerate(grads_list):
+        g[i] = grads_struct(gd)
+    _check(lib().sg_render_batched_backward(scene_array(scenes), len(scenes), camera_array(cams),
+                                            _view_scene_array(view_scene), len(cams), _ptr(ws),
+                                            ws.numel(), _ptr(T_final), _ptr(last), _ptr(d_img),
+                                            _ptr(bwd_ws), bwd_ws.numel(), g, _stream_handle(stream)))
+
+
+def sg_forward_status(ws, stream=None):
+    """(pairs needed by the last forward on ws, status). Synchronises the stream."""
+    n = ctypes.c_uint64()
+    st = ctypes.c_int32()
+    _check(lib().sg_forward_status(_ptr(ws), ctypes.byref(n), ctypes.byref(st), _stream_handle(stream)))
+    return int(n.value), int(st.value)

@@ -296,3 +296,23 @@ def config4(n=6_000_000, n_cams=16):
                        gauss_zero_frac=0.6, lobe_zero_frac=0.5)
     cams = ring_cameras(n_cams, 8.0, 1600, 1066, 1250.0)
     return scene, cams, rng
+
+
+STORAGE_FAMILIES = {
+    # storage form -> {field: dtype name}; fields not listed stay binary32
+    "f32": {},
+    "f16": {k: "float16" for k in ("means", "scales", "quats", "opac", "axis", "amp", "sharp")},
+    "f16_bf16s": dict({k: "float16" for k in ("means", "scales", "quats", "opac", "axis", "amp")},
+                      sharp="bfloat16"),
+}
+
+
+def round_to_storage(scene: Scene, storage: str) -> Scene:
+    """The binary32 values a scene holds after a round trip through `storage`
+    (what the kernels read back from half-precision arrays)."""
+    import torch
+    out = scene.copy()
+    for k, dt in STORAGE_FAMILIES[storage].items():
+        t = torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32))
+        setattr(out, k, t.to(getattr(torch, dt)).float().numpy())
+    return out

@@ -1,0 +1,132 @@
+"""Batched form vs the FP64 oracle: several scenes of uneven size, cameras at
+mixed resolutions, one forward and one backward call, graph capture, and the
+persistent (work-queue) blend."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_07021_gb300 import render, sgsplat, synth
+from paper_2509_07021_gb300.sgsplat import DeviceScene
+
+from parity_util import check_grads, check_image, masked_dimg
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def _batch(seed=0):
+    rng = np.random.default_rng(700 + seed)
+    scenes = [synth.make_scene(rng, n, lobes=synth.LOBE_MIX, means="cube", cube_side=1.3,
+                               masks="uniform") for n in (2500, 700, 4100)]
+    cams = [synth.make_camera(64, 48, 60.0),
+            synth.make_camera(40, 40, 45.0, viewmat=synth.look_at((0.4, 0.2, 0.1), (0, 0, 4.0))),
+            synth.make_camera(33, 21, 30.0, bg=(0.2, 0.3, 0.4)),
+            synth.make_camera(80, 50, 70.0, viewmat=synth.look_at((-0.5, 0.0, 0.3), (0, 0, 4.0))),
+            synth.make_camera(16, 16, 20.0)]
+    view_scene = [0, 1, 0, 2, 1]
+    return scenes, cams, view_scene
+
+
+def _flat_views(t, cams, ch):
+    a = t.detach().cpu().numpy()
+    out, o = [], 0
+    for c in cams:
+        n = c.width * c.height * ch
+        x = a[o:o + n]
+        out.append(x.reshape(3, c.height, c.width) if ch == 3 else x.reshape(c.height, c.width))
+        o += n
+    return out
+
+
+def _check_batched(br, scenes, cams, view_scene, seed):
+    imgs = _flat_views(br.img, cams, 3)
+    Ts = _flat_views(br.T_final, cams, 1)
+    lasts = _flat_views(br.last, cams, 1)
+    results = []
+    for v, cam in enumerate(cams):
+        res, _ = oracle.render(scenes[view_scene[v]], [cam])
+        results.append(res[0])
+        check_image(imgs[v], Ts[v], lasts[v], res[0], cam)
+    rng = np.random.default_rng(seed)
+    dimgs = masked_dimg(rng, cams, results)
+    br.backward(torch.from_numpy(np.concatenate([d.reshape(-1) for d in dimgs])).cuda())
+    torch.cuda.synchronize()
+    for s, scene in enumerate(scenes):
+        vs = [v for v in range(len(cams)) if view_scene[v] == s]
+        _, g = oracle.render(scene, [cams[v] for v in vs], dimgs=[dimgs[v] for v in vs])
+        check_grads(br.grads[s], g)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_batched_multi_scene_parity(persistent):
+    scenes, cams, view_scene = _batch()
+    ds = [DeviceScene.from_host(s) for s in scenes]
+    old = sgsplat.sg_get_tuning()
+    sgsplat.sg_set_tuning(fwd_persistent=persistent, bwd_persistent=persistent)
+    try:
+        br = render.BatchedRenderer(ds, cams, view_scene)
+        br.forward()
+        n, st = br.status()
+        assert st == sgsplat.SG_OK and 0 < n <= br.capacity
+        _check_batched(br, scenes, cams, view_scene, seed=persistent)
+    finally:
+        sgsplat.sg_set_tuning(**old)
+
+
+def test_persistent_plain_form():
+    scenes, cams, _ = _batch(1)
+    old = sgsplat.sg_get_tuning()
+    sgsplat.sg_set_tuning(fwd_persistent=1, bwd_persistent=1)
+    try:
+        from test_gpu_parity import run_parity
+        run_parity(scenes[2], [cams[3]], seed=5)
+    finally:
+        sgsplat.sg_set_tuning(**old)
+
+
+def test_batched_capacity_overflow_is_reported():
+    scenes, cams, view_scene = _batch(2)
+    ds = [DeviceScene.from_host(s) for s in scenes]
+    br = render.BatchedRenderer(ds, cams, view_scene, pair_capacity=10, headroom=1.0)
+    assert br.capacity == 10 + 4096
+    br.forward()
+    need, st = br.status()
+    big = render.BatchedRenderer(ds, cams, view_scene)
+    big.forward()
+    need2, st2 = big.status()
+    assert st2 == sgsplat.SG_OK
+    if need2 > br.capacity:
+        assert st == sgsplat.SG_ERR_CAPACITY and need == need2
+        # nothing was binned: every pixel shows the background
+        assert torch.all(br.T_final == 1)
+    else:
+        assert st == sgsplat.SG_OK
+
+
+def test_graph_replay_matches_eager():
+    scenes, cams, view_scene = _batch(3)
+    ds = [DeviceScene.from_host(s) for s in scenes]
+    br = render.BatchedRenderer(ds, cams, view_scene)
+    targets = torch.rand(br.img.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    lg = render.l1_loss_grad(br, targets)
+    br.step(lg)
+    torch.cuda.synchronize()
+    eager_img = br.img.clone()
+    eager = [{k: v.clone() for k, v in g.items()} for g in br.grads]
+    br.capture(lg)
+    for g in br.grads:
+        for v in g.values():
+            v.zero_()
+    br.img.zero_()
+    br.replay()
+    br.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(br.img, eager_img)
+    for g, e in zip(br.grads, eager):
+        for k in g:
+            a, b = g[k].double(), e[k].double()
+            # atomics make the summation order differ between runs
+            assert torch.linalg.norm(a - b) <= 1e-5 * torch.linalg.norm(b) + 1e-12, k
+    n, st = br.status()
+    assert st == sgsplat.SG_OK

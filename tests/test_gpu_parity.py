@@ -179,14 +179,27 @@ def test_every_blend_shape(ppt):
     try:
         run_parity(scene, [cam], seed=12)
     finally:
-        sgsplat.sg_set_tuning(old["fwd_pixels_per_thread"], old["bwd_pixels_per_thread"])
+        sgsplat.sg_set_tuning(**old)
+
+
+@pytest.mark.parametrize("storage", ["f16", "f16_bf16s"])
+def test_half_precision_storage(storage):
+    """Geometry and lobes stored in binary16 (sharpness optionally bfloat16),
+    arithmetic in binary32: against the oracle fed the same rounded values."""
+    rng = np.random.default_rng(650)
+    scene = synth.make_scene(rng, 5000, lobes=synth.LOBE_MIX, means="cube", cube_side=1.4,
+                             masks="uniform")
+    ref = synth.round_to_storage(scene, storage)
+    cam = synth.make_camera(70, 50, 70.0, bg=(0.1, 0.1, 0.3))
+    run_parity(scene, [cam], seed=13, storage=storage, ref_scene=ref)
 
 
 def test_tuning_rejects_bad_shapes():
     with pytest.raises(sgsplat.SGError):
         sgsplat.sg_set_tuning(3, 4)
     sgsplat.sg_set_tuning()
-    assert sgsplat.sg_get_tuning() == {"fwd_pixels_per_thread": 1, "bwd_pixels_per_thread": 4}
+    t = sgsplat.sg_get_tuning()
+    assert t["fwd_pixels_per_thread"] == 1 and t["bwd_pixels_per_thread"] == 4
 
 
 def test_capacity_error_and_retry():
