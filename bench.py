@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f16", "f16_bf16s"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP16-storage, batched and stress forms")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default blend shapes")
     ap.add_argument("--cpu-tiles", type=int, default=48,
@@ -349,10 +351,157 @@ def run_ours(args, world, rank, local):
             "stages_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in fl_stages.items()},
             "stage_share": share,
             "pair_evals": evals}
+    if world == 1 and not args.no_forms:
+        forms = run_forms(args, scene, cams, d_img, flush, max(3, args.steps // 2))
+        images = forms.pop("_images")
+        if not args.no_cpu_baseline:
+            errs = oracle_errors(scene, cam, images)
+            forms["plain_f32"]["vs_oracle"] = errs["f32"]
+            forms["plain_f16_bf16s"]["vs_oracle"] = errs["f16_bf16s"]
+        line["forms"] = forms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(scene, cam, d_img_np, args.cpu_tiles)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the other forms of the metric: FP16 storage, batched (config 2), stress (4)
+# ---------------------------------------------------------------------------
+
+def _timed(fn, steps, warmup, flush):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / steps
+
+
+def render_vram(ds, cams, d_img, grads):
+    """Peak bytes held by PyTorch's allocator during a forward only (the
+    paper's rendering-VRAM protocol: static parameters included) and during
+    forward + backward."""
+    import torch
+    from paper_2509_07021_gb300 import render
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats()
+    out = render.render_forward(ds, cams)
+    torch.cuda.synchronize()
+    fwd_peak = torch.cuda.max_memory_allocated()
+    render.render_backward(ds, cams, out, d_img, grads)
+    torch.cuda.synchronize()
+    both = torch.cuda.max_memory_allocated()
+    del out
+    return fwd_peak, both
+
+
+def run_forms(args, scene, cams, d_img, flush, steps):
+    """Timing (and VRAM / error) of the storage and batched forms."""
+    import torch
+    from paper_2509_07021_gb300 import render, sgsplat, synth
+    from paper_2509_07021_gb300.sgsplat import DeviceScene
+    forms = {}
+    cam = cams[0]
+    px = cam.width * cam.height
+
+    # ---- plain FP32 vs FP16/BF16 storage, same scene and view ----
+    base = {}
+    for storage in ("f32", "f16_bf16s"):
+        torch.cuda.empty_cache()
+        ds = DeviceScene.from_host(scene, storage=storage)
+        grads = render.alloc_grads(ds)
+        static = sum(getattr(ds, k).numel() * getattr(ds, k).element_size()
+                     for k in DeviceScene.FLOAT_FIELDS + ("lobe_off",))
+        fwd_peak, both_peak = render_vram(ds, cams, d_img, grads)
+
+        def step():
+            out = render.render_forward(ds, cams)
+            render.render_backward(ds, cams, out, d_img, grads)
+        ms = _timed(step, steps, 2, flush)
+        out = render.render_forward(ds, cams)
+        torch.cuda.synchronize()
+        base[storage] = out.img[0].cpu().numpy()
+        forms[f"plain_{storage}"] = {"ms_per_view": ms, "mpixel_s": px / ms / 1e3,
+                                     "static_mb": static / 2**20, "render_vram_mb": fwd_peak / 2**20,
+                                     "fwd_bwd_vram_mb": both_peak / 2**20}
+        del ds, grads, out
+    f32, f16 = forms["plain_f32"], forms["plain_f16_bf16s"]
+    f16["speedup_vs_plain_f32"] = f32["ms_per_view"] / f16["ms_per_view"]
+    f16["render_vram_reduction"] = 1.0 - f16["render_vram_mb"] / f32["render_vram_mb"]
+    f16["max_abs_img_diff_vs_f32_gpu"] = float(np.abs(base["f16_bf16s"] - base["f32"]).max())
+    forms["_images"] = base   # consumed by the oracle error report, removed before printing
+
+    # ---- batched: 8 uneven scenes x 4 cameras, one CUDA graph ----
+    for name, gen in (("batched_cfg2", synth.config2), ("stress_cfg4", synth.config4)):
+        torch.cuda.empty_cache()
+        if name == "batched_cfg2":
+            scenes, cams_per, rng = gen()
+            all_cams = [c for cs in cams_per for c in cs]
+            view_scene = [s for s, cs in enumerate(cams_per) for _ in cs]
+        else:
+            sc, all_cams, rng = gen()
+            scenes = [sc]
+            view_scene = [0] * len(all_cams)
+        dss = [DeviceScene.from_host(s_) for s_ in scenes]
+        del scenes
+        br = render.BatchedRenderer(dss, all_cams, view_scene)
+        gen_t = torch.Generator(device="cuda").manual_seed(synth.SEED_BASE + 2)
+        targets = torch.rand(br.img.shape, device="cuda", generator=gen_t)
+        lg = render.l1_loss_grad(br, targets)
+        br.capture(lg)
+        ms_b = _timed(br.replay, max(3, steps // 2), 2, flush)
+        n_pairs, status = br.status()
+        P = int(br.offsets[-1])
+        # the same work through the plain single-view renderer, view by view
+        plain_grads = [render.alloc_grads(d) for d in dss]
+
+        def plain_loop():
+            for v, c in enumerate(all_cams):
+                d = dss[view_scene[v]]
+                out = render.render_forward(d, [c])
+                o, n = int(br.offsets[v]), br.npix[v]
+                tgt = targets[3 * o:3 * (o + n)].view(1, 3, c.height, c.width)
+                g = torch.sign(out.img - tgt) / (3 * n)
+                render.render_backward(d, [c], out, g, plain_grads[view_scene[v]])
+        ms_p = _timed(plain_loop, 2, 1, flush)
+        forms[name] = {"views": len(all_cams), "scenes": len(dss),
+                       "gaussians": int(sum(d.n for d in dss)), "mpixels": P / 1e6,
+                       "n_pairs": n_pairs, "status": status,
+                       "ms_per_launch": ms_b, "ms_per_view": ms_b / len(all_cams),
+                       "mpixel_s": P / ms_b / 1e3, "plain_loop_ms": ms_p,
+                       "speedup_vs_plain_loop": ms_p / ms_b,
+                       "tuning": sgsplat.sg_get_tuning()}
+        del br, dss, plain_grads, targets
+        torch.cuda.empty_cache()
+    return forms
+
+
+def oracle_errors(scene, cam, images, n_tiles=24, seed=5):
+    """Max / mean abs image error of the GPU forms against the FP64 oracle on
+    a sample of tiles (oracle fed the original binary32 scene, so the FP16
+    number includes the storage rounding)."""
+    import oracle
+    sel = np.zeros(cam.n_tiles, bool)
+    sel[np.random.default_rng(seed).choice(cam.n_tiles, n_tiles, replace=False)] = True
+    res = oracle.render_forward(scene, cam, tile_sel=sel)
+    m = np.repeat(np.repeat(sel.reshape(cam.tiles_y, cam.tiles_x), 16, 0), 16, 1)
+    m = m[:cam.height, :cam.width] & ~res.ambiguous
+    out = {}
+    for k, img in images.items():
+        err = np.abs(img - res.img)[:, m]
+        out[k] = {"max_abs": float(err.max()), "mean_abs": float(err.mean()), "pixels": int(m.sum())}
+    return out
 
 
 def run_e2e(args, ds, cams, d_img_np, grads, world):
