@@ -387,23 +387,27 @@ def _timed(fn, steps, warmup, flush):
     return tot / steps
 
 
-def render_vram(ds, cams, d_img, grads):
-    """Peak bytes held by PyTorch's allocator during a forward only (the
-    paper's rendering-VRAM protocol: static parameters included) and during
-    forward + backward."""
+def render_vram(ds, cams, d_img, grads, static_bytes):
+    """Rendering VRAM as the paper measures it (PyTorch allocator peak during a
+    render, static parameters included): static parameter bytes + the peak
+    the render adds over what was allocated before it (workspace, outputs).
+    Returned for a forward only and for forward + backward (gradients and
+    upstream gradient buffers are counted as allocated by the caller)."""
     import torch
     from paper_2509_07021_gb300 import render
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    before = torch.cuda.memory_allocated()
     torch.cuda.reset_peak_memory_stats()
     out = render.render_forward(ds, cams)
     torch.cuda.synchronize()
-    fwd_peak = torch.cuda.max_memory_allocated()
+    fwd_peak = torch.cuda.max_memory_allocated() - before
     render.render_backward(ds, cams, out, d_img, grads)
     torch.cuda.synchronize()
-    both = torch.cuda.max_memory_allocated()
+    both = torch.cuda.max_memory_allocated() - before
+    grads_bytes = sum(g.numel() * g.element_size() for g in grads.values())
     del out
-    return fwd_peak, both
+    return static_bytes + fwd_peak, static_bytes + both + grads_bytes + d_img.numel() * 4
 
 
 def run_forms(args, scene, cams, d_img, flush, steps):
@@ -423,7 +427,7 @@ def run_forms(args, scene, cams, d_img, flush, steps):
         grads = render.alloc_grads(ds)
         static = sum(getattr(ds, k).numel() * getattr(ds, k).element_size()
                      for k in DeviceScene.FLOAT_FIELDS + ("lobe_off",))
-        fwd_peak, both_peak = render_vram(ds, cams, d_img, grads)
+        fwd_peak, both_peak = render_vram(ds, cams, d_img, grads, static)
 
         def step():
             out = render.render_forward(ds, cams)

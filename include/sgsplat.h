@@ -258,6 +258,17 @@ int sg_render_forward(const sg_scene *scene, const sg_camera *cams, int n_views,
                       sg_sizes *out, void *stream);
 
 /*
+ * sg_render_forward that also writes, per Gaussian, its importance score
+ * I_i = sum over the pixels of all n_views views of its blend weight
+ * alpha_i T_i (the importance-based selection of the opacity proximal step,
+ * App. A.2). importance: device [N] binary32, overwritten (0 for Gaussians
+ * that reach no pixel). Other arguments as sg_render_forward.
+ */
+int sg_render_forward_importance(const sg_scene *scene, const sg_camera *cams, int n_views,
+                                 void *ws, size_t ws_bytes, float *img, float *T_final,
+                                 int32_t *last, float *importance, sg_sizes *out, void *stream);
+
+/*
  * Backward of sg_render_forward for L = sum(d_img * img): the exact adjoint of
  * the compositing (zero through skips, the early stop and clamped branches).
  * ws: the workspace of the matching forward call (read only).
@@ -282,13 +293,16 @@ int sg_render_backward(const sg_scene *scene, const sg_camera *cams, int n_views
  * and sets its status to SG_ERR_CAPACITY in the workspace, where
  * sg_forward_status reads them (that call synchronises). Gradients: one
  * sg_grads per scene, each overwritten with the sum over that scene's views.
+ * importance: NULL, or a host array of n_scenes device pointers [N_s]
+ * (as in sg_render_forward_importance).
  */
 int sg_batched_workspace_query(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
                                const int32_t *view_scene, int n_views, uint64_t pair_capacity,
                                sg_sizes *out);
 int sg_render_batched_forward(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
                               const int32_t *view_scene, int n_views, void *ws, size_t ws_bytes,
-                              float *img, float *T_final, int32_t *last, void *stream);
+                              float *img, float *T_final, int32_t *last,
+                              float *const *importance, void *stream);
 int sg_render_batched_backward(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
                                const int32_t *view_scene, int n_views, const void *ws,
                                size_t ws_bytes, const float *T_final, const int32_t *last,

@@ -115,29 +115,60 @@ static int walk_pixel(const orc_gauss2d *g, const int64_t *ids, int64_t n,
  * of unselected tiles are left untouched.
  * img: [3][H][W], T_final/last/amb/sig: [H][W].
  */
+/*
+ * Importance (App. A.2, importance-based selection): the sum over rays of a
+ * Gaussian's blend weight w = alpha_i T_i. Added into weight[id] when the
+ * pointer is non-null.
+ */
+static void add_weights(const int64_t *ids, const int64_t *rk, const double *ra,
+                        const double *rT, int64_t nr, double *weight)
+{
+    for (int64_t i = 0; i < nr; ++i) {
+        const double w = ra[i] * rT[i];
+#pragma omp atomic
+        weight[ids[rk[i]]] += w;
+    }
+}
+
 void orc_blend_forward(int W, int H, const int64_t *ranges, const int64_t *ids,
                        const double *xy, const double *conic, const double *op,
                        const double *rgb, const double *bg, const uint8_t *tile_sel,
                        double *img, double *T_final, int64_t *last, uint8_t *amb,
-                       uint64_t *sig)
+                       uint64_t *sig, double *weight)
 {
     const orc_gauss2d g = {xy, conic, op, rgb};
     const int tx_n = (W + ORC_TILE - 1) / ORC_TILE;
     const int ty_n = (H + ORC_TILE - 1) / ORC_TILE;
     const int64_t HW = (int64_t)H * W;
+    int64_t max_len = 0;
+    for (int t = 0; t < tx_n * ty_n; ++t) {
+        const int64_t len = ranges[2 * t + 1] - ranges[2 * t];
+        if (len > max_len) max_len = len;
+    }
 #pragma omp parallel for schedule(dynamic, 4)
     for (int t = 0; t < tx_n * ty_n; ++t) {
         if (tile_sel && !tile_sel[t]) continue;
         const int tx = t % tx_n, ty = t / tx_n;
         const int64_t s = ranges[2 * t], e = ranges[2 * t + 1];
+        int64_t *rk = 0;
+        double *ra = 0, *rT = 0, *rG = 0;
+        int *rc = 0;
+        if (weight) {
+            rk = (int64_t *)malloc(sizeof(int64_t) * (size_t)(max_len + 1));
+            ra = (double *)malloc(sizeof(double) * (size_t)(max_len + 1));
+            rT = (double *)malloc(sizeof(double) * (size_t)(max_len + 1));
+            rG = (double *)malloc(sizeof(double) * (size_t)(max_len + 1));
+            rc = (int *)malloc(sizeof(int) * (size_t)(max_len + 1));
+        }
         for (int py = ty * ORC_TILE; py < (ty + 1) * ORC_TILE && py < H; ++py)
             for (int px = tx * ORC_TILE; px < (tx + 1) * ORC_TILE && px < W; ++px) {
                 double c[3], T;
-                int64_t l;
+                int64_t l, nr = 0;
                 int a;
                 uint64_t h;
                 walk_pixel(&g, ids + s, e - s, (double)px, (double)py, c, &T, &l, &a,
-                           0, 0, 0, 0, 0, 0, &h);
+                           rk, ra, rT, rG, rc, weight ? &nr : 0, &h);
+                if (weight) add_weights(ids + s, rk, ra, rT, nr, weight);
                 const int64_t p = (int64_t)py * W + px;
                 for (int ch = 0; ch < 3; ++ch) img[ch * HW + p] = c[ch] + T * bg[ch];
                 T_final[p] = T;
@@ -145,6 +176,11 @@ void orc_blend_forward(int W, int H, const int64_t *ranges, const int64_t *ids,
                 amb[p] = (uint8_t)a;
                 if (sig) sig[p] = h;
             }
+        free(rk);
+        free(ra);
+        free(rT);
+        free(rG);
+        free(rc);
     }
 }
 

@@ -55,7 +55,7 @@ def lib():
         L = ctypes.CDLL(path)
         P = ctypes.c_void_p
         I = ctypes.c_int
-        L.orc_blend_forward.argtypes = [I, I] + [P] * 13
+        L.orc_blend_forward.argtypes = [I, I] + [P] * 14
         L.orc_blend_forward.restype = None
         L.orc_blend_backward.argtypes = [I, I] + [P] * 13
         L.orc_blend_backward.restype = None
@@ -344,6 +344,7 @@ class ViewResult:
     rgb: np.ndarray          # [N,3]
     tile_sel: np.ndarray | None
     torch_state: tuple | None
+    importance: np.ndarray | None = None   # [N] sum over pixels of alpha T (App. A.2)
 
 
 def render_forward(scene, cam, tile_sel=None, need_grad=False):
@@ -371,11 +372,13 @@ def render_forward(scene, cam, tile_sel=None, need_grad=False):
     sig = np.zeros((H, W), np.uint64)
     bg = _c(cam.bg, np.float64)
     sel = None if tile_sel is None else _c(tile_sel, np.uint8)
+    weight = np.zeros(N)
     lib().orc_blend_forward(W, H, _p(ranges), _p(ids), _p(xy), _p(con), _p(op), _p(rgb),
-                            _p(bg), _p(sel), _p(img), _p(T), _p(last), _p(amb), _p(sig))
+                            _p(bg), _p(sel), _p(img), _p(T), _p(last), _p(amb), _p(sig),
+                            _p(weight))
     state = (P, (xy_t, con_t, op_t, rgb_t), vis_idx) if need_grad else None
     return ViewResult(img, T, last, amb.astype(bool), sig, dec, keys, ids, ranges,
-                      xy, con, op, rgb, sel, state)
+                      xy, con, op, rgb, sel, state, weight)
 
 
 def render_backward(res: ViewResult, scene, cam, dimg):

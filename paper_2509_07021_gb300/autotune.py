@@ -51,20 +51,23 @@ def _store(data):
         pass
 
 
-def tune(ds, cams, d_img, reps=3, use_cache=True, candidates=CANDIDATES):
-    """Picks and sets the fastest pixels-per-thread for the forward and the
-    backward blend on this workload. Returns the choice and the timings (ms)."""
+def tune(ds, cams, d_img, reps=3, use_cache=True, candidates=CANDIDATES, persistent=(0, 1)):
+    """Picks and sets the fastest blend shape (pixels per thread, one block per
+    tile or persistent) for the forward and the backward independently on
+    this workload. Returns the choice and the timings (ms)."""
     key = _key(ds, cams)
     cache = _load() if use_cache else {}
     if use_cache and key in cache:
         c = cache[key]
-        sgsplat.sg_set_tuning(c["fwd_pixels_per_thread"], c["bwd_pixels_per_thread"])
+        sgsplat.sg_set_tuning(c["fwd_pixels_per_thread"], c["bwd_pixels_per_thread"],
+                              c.get("fwd_persistent", 0), c.get("bwd_persistent", 0))
         return dict(c, cached=True)
     grads = render.alloc_grads(ds)
     timings = {}
     prev = sgsplat.sg_get_tuning()
-    for p in candidates:
-        sgsplat.sg_set_tuning(p, p)
+    shapes = [(p, q) for q in persistent for p in candidates]
+    for p, q in shapes:
+        sgsplat.sg_set_tuning(p, p, q, q)
         out = render.render_forward(ds, cams)          # warm-up for this shape
         render.render_backward(ds, cams, out, d_img, grads)
         torch.cuda.synchronize()
@@ -76,12 +79,16 @@ def tune(ds, cams, d_img, reps=3, use_cache=True, candidates=CANDIDATES):
         torch.cuda.synchronize()
         st = sgsplat.sg_profile_read(reset=True)["stages"]
         sgsplat.sg_profile_enable(0)
-        timings[p] = {"blend_fwd": st["blend_fwd"]["ms"] / reps, "blend_bwd": st["blend_bwd"]["ms"] / reps}
-    best_f = min(timings, key=lambda p: timings[p]["blend_fwd"])
-    best_b = min(timings, key=lambda p: timings[p]["blend_bwd"])
-    sgsplat.sg_set_tuning(best_f, best_b)
-    res = {"fwd_pixels_per_thread": best_f, "bwd_pixels_per_thread": best_b,
-           "ms": {str(k): v for k, v in timings.items()}, "previous": prev}
+        # the persistent forms also pay for their tile order (in tile_ranges / bwd_clear)
+        timings[(p, q)] = {"blend_fwd": (st["blend_fwd"]["ms"] + (st["tile_ranges"]["ms"] if q else 0)) / reps,
+                           "blend_bwd": (st["blend_bwd"]["ms"] + (st["bwd_clear"]["ms"] if q else 0)) / reps}
+    best_f = min(timings, key=lambda k: timings[k]["blend_fwd"])
+    best_b = min(timings, key=lambda k: timings[k]["blend_bwd"])
+    sgsplat.sg_set_tuning(best_f[0], best_b[0], best_f[1], best_b[1])
+    res = {"fwd_pixels_per_thread": best_f[0], "bwd_pixels_per_thread": best_b[0],
+           "fwd_persistent": best_f[1], "bwd_persistent": best_b[1],
+           "ms": {f"p{k[0]}{'_persistent' if k[1] else ''}": v for k, v in timings.items()},
+           "previous": prev}
     if use_cache:
         cache[key] = res
         _store(cache)

@@ -335,11 +335,20 @@ void fill_sizes(const Batch &b, const WsLayout &L, uint64_t n_pairs, sg_sizes *o
 // the capacity, overflow recorded on the device, graph capturable).
 int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, const int32_t *view_scene,
                  int n_views, void *ws, size_t ws_bytes, float *img, float *T_final, int32_t *last,
-                 sg_sizes *out, cudaStream_t stream, bool sync) {
+                 float *const *importance, sg_sizes *out, cudaStream_t stream, bool sync) {
     std::unique_ptr<Batch> hb(new Batch);
     int st = build_batch(scenes, n_scenes, cams, view_scene, n_views, true, *hb);
     if (st != SG_OK) return st;
-    const Batch &b = *hb;
+    Batch &b = *hb;
+    bool want_importance = false;
+    if (importance) {
+        for (int s = 0; s < n_scenes; ++s) {
+            if (scenes[s].n > 0 && (!importance[s] || !aligned(importance[s], 4)))
+                return fail(SG_ERR_INVALID_ARG, "importance[%d] is NULL or misaligned", s);
+            b.scene[s].importance = importance[s];
+            want_importance = want_importance || scenes[s].n > 0;
+        }
+    }
     if (!img || !T_final || !last) return fail(SG_ERR_INVALID_ARG, "output pointers must not be NULL");
     if (!aligned(img, 16) || !aligned(T_final, 16) || !aligned(last, 16))
         return fail(SG_ERR_INVALID_ARG, "outputs must be 16-byte aligned");
@@ -434,6 +443,12 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     st = blend_shape(false, reinterpret_cast<uint32_t *>(w + L.tov0),
                      reinterpret_cast<uint32_t *>(counters + CNT_QUEUE), shape);
     if (st != SG_OK) return st;
+    shape.importance = want_importance && !counting;
+    if (shape.importance)
+        for (int s = 0; s < n_scenes; ++s)
+            if (scenes[s].n > 0)
+                SG_CUDA(cudaMemsetAsync(importance[s], 0, (size_t)scenes[s].n * sizeof(float), stream),
+                        "clear importance");
     if (shape.persistent) {
         StageTimer t(ST_RANGES, stream);
         SG_CUDA(launch_tile_order(ranges, b.n_tiles, counters + CNT_TILES, reinterpret_cast<uint32_t *>(w + L.tok0),
@@ -631,7 +646,16 @@ int sg_workspace_layout(const sg_scene *scene, const sg_camera *cams, int n_view
 int sg_render_forward(const sg_scene *scene, const sg_camera *cams, int n_views, void *ws, size_t ws_bytes,
                       float *img, float *T_final, int32_t *last, sg_sizes *out, void *stream) {
     g_err[0] = '\0';
-    return forward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, img, T_final, last, out,
+    return forward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, img, T_final, last, nullptr, out,
+                        static_cast<cudaStream_t>(stream), true);
+}
+
+int sg_render_forward_importance(const sg_scene *scene, const sg_camera *cams, int n_views, void *ws,
+                                 size_t ws_bytes, float *img, float *T_final, int32_t *last, float *importance,
+                                 sg_sizes *out, void *stream) {
+    g_err[0] = '\0';
+    float *const imp[1] = {importance};
+    return forward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, img, T_final, last, imp, out,
                         static_cast<cudaStream_t>(stream), true);
 }
 
@@ -657,11 +681,11 @@ int sg_batched_workspace_query(const sg_scene *scenes, int n_scenes, const sg_ca
 
 int sg_render_batched_forward(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
                               const int32_t *view_scene, int n_views, void *ws, size_t ws_bytes, float *img,
-                              float *T_final, int32_t *last, void *stream) {
+                              float *T_final, int32_t *last, float *const *importance, void *stream) {
     g_err[0] = '\0';
     if (!view_scene) return fail(SG_ERR_INVALID_ARG, "view_scene must not be NULL");
-    return forward_impl(scenes, n_scenes, cams, view_scene, n_views, ws, ws_bytes, img, T_final, last, nullptr,
-                        static_cast<cudaStream_t>(stream), false);
+    return forward_impl(scenes, n_scenes, cams, view_scene, n_views, ws, ws_bytes, img, T_final, last,
+                        importance, nullptr, static_cast<cudaStream_t>(stream), false);
 }
 
 int sg_render_batched_backward(const sg_scene *scenes, int n_scenes, const sg_camera *cams,

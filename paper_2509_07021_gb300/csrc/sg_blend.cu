@@ -151,7 +151,11 @@ __device__ __forceinline__ void add_evals(uint32_t ne, unsigned long long *evals
 // Warp w owns sub-blocks w P .. w P + P - 1 of the tile, one 8x4 sub-block per
 // pixel slot, so that a Gaussian whose reach misses a sub-block is skipped by
 // the whole warp at once (NT = 256 / P threads per tile).
-template <int P, bool COUNT>
+// Forward modes: plain, counting (pair evaluations, no culling), importance
+// (also sums alpha T per Gaussian into its scene's importance array).
+enum : int { FWD_PLAIN = 0, FWD_COUNT = 1, FWD_IMPORTANCE = 2 };
+
+template <int P, int MODE>
 __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, Staged &sm,
                                                const uint2 *__restrict__ ranges,
                                                const uint32_t *__restrict__ pval,
@@ -159,11 +163,14 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
                                                float *__restrict__ T_final, int32_t *__restrict__ last,
                                                uint32_t &ne) {
     constexpr int NT = BLEND_THREADS / P;
+    constexpr bool COUNT = MODE == FWD_COUNT;
+    constexpr bool IMP = MODE == FWD_IMPORTANCE;
     int tx, ty;
     const ViewDesc *vw;
     tile_of_block(b, tile, tx, ty, vw);
     const uint2 rg = ranges[tile];
     const int n = (int)(rg.y - rg.x);
+    float *imp = IMP ? b.scene[vw->scene].importance : nullptr;
 
     float fpx[P], fpy[P], T[P], c0[P], c1[P], c2[P];
     int lastc[P];
@@ -193,12 +200,14 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
             stage<!COUNT>(sm, k, rec[e], e, x0, y0);
         }
         __syncthreads();
-        if (all) continue;
+        // the importance sums are warp collectives: there, only whole warps leave
+        if (IMP ? __all_sync(0xffffffffu, all) : all) continue;
         for (int k = 0; k < cnt; ++k) {
             const uint32_t msk = sm.mask[k] >> sub0;
             if ((msk & ((1u << P) - 1u)) == 0u) continue;   // warp-uniform
             const float4 q = sm.q[k], r = sm.r[k];
             const float bl = sm.s[k];
+            float wsum = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
                 if (!((msk >> j) & 1u)) continue;            // warp-uniform
@@ -215,6 +224,12 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
                 c2[j] = fmaf(bl, w, c2[j]);
                 T[j] = tt;
                 lastc[j] = base + k + 1;
+                if (IMP) wsum += w;
+            }
+            if (IMP && __any_sync(0xffffffffu, wsum != 0.f)) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+                if ((threadIdx.x & 31) == 0) atomicAdd(imp + (sm.id[k] - (uint32_t)vw->ent_off), wsum);
             }
         }
     }
@@ -236,7 +251,7 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
 
 // Persistent form: resident blocks pull tiles from a work counter in the
 // given order (longest lists first); otherwise one block per tile.
-template <int P, bool COUNT, bool PERSIST>
+template <int P, int MODE, bool PERSIST>
 __global__ void __launch_bounds__(BLEND_THREADS / P)
 k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const uint32_t *__restrict__ pval, const Rec *__restrict__ rec,
@@ -248,7 +263,7 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
     const Batch &b = *bp;
     uint32_t ne = 0;
     if (!PERSIST) {
-        blend_fwd_tile<P, COUNT>(b, blockIdx.x, sm, ranges, pval, rec, img, T_final, last, ne);
+        blend_fwd_tile<P, MODE>(b, blockIdx.x, sm, ranges, pval, rec, img, T_final, last, ne);
     } else {
         for (;;) {
             if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
@@ -256,11 +271,11 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const uint32_t item = s_item;
             __syncthreads();
             if (item >= n_tiles) break;
-            blend_fwd_tile<P, COUNT>(b, tile_order ? tile_order[item] : item, sm, ranges, pval, rec, img,
-                                     T_final, last, ne);
+            blend_fwd_tile<P, MODE>(b, tile_order ? tile_order[item] : item, sm, ranges, pval, rec, img,
+                                    T_final, last, ne);
         }
     }
-    if (COUNT) add_evals(ne, evals);
+    if (MODE == FWD_COUNT) add_evals(ne, evals);
 }
 
 template <int P, bool PERSIST>
@@ -269,10 +284,13 @@ static void fwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const 
                   unsigned long long *evals, cudaStream_t s) {
     const unsigned grid = PERSIST ? (unsigned)sh.grid : n_tiles;
     if (evals)
-        k_blend_fwd<P, true, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
+        k_blend_fwd<P, FWD_COUNT, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
             db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, evals);
+    else if (sh.importance)
+        k_blend_fwd<P, FWD_IMPORTANCE, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
+            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, nullptr);
     else
-        k_blend_fwd<P, false, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
+        k_blend_fwd<P, FWD_PLAIN, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
             db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, nullptr);
 }
 
@@ -560,10 +578,10 @@ int blend_persistent_grid(bool backward, int p) {
     int g = 0;
     if (!backward) {
         switch (p) {
-            case 1: g = occupancy_grid(k_blend_fwd<1, false, true>, 256); break;
-            case 2: g = occupancy_grid(k_blend_fwd<2, false, true>, 128); break;
-            case 4: g = occupancy_grid(k_blend_fwd<4, false, true>, 64); break;
-            case 8: g = occupancy_grid(k_blend_fwd<8, false, true>, 32); break;
+            case 1: g = occupancy_grid(k_blend_fwd<1, FWD_PLAIN, true>, 256); break;
+            case 2: g = occupancy_grid(k_blend_fwd<2, FWD_PLAIN, true>, 128); break;
+            case 4: g = occupancy_grid(k_blend_fwd<4, FWD_PLAIN, true>, 64); break;
+            case 8: g = occupancy_grid(k_blend_fwd<8, FWD_PLAIN, true>, 32); break;
         }
     } else {
         switch (p) {

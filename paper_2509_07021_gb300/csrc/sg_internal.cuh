@@ -40,6 +40,7 @@ struct SceneDesc {
     const int32_t *lobe_off;
     const void *axis, *sharp, *amp;
     const float *lmask;
+    float *importance;    // forward output: sum of alpha T per Gaussian (null: not wanted)
     sg_grads grads;
     int64_t n, n_lobes;
     int32_t dtype_geom, dtype_lobe, dtype_sharp;
@@ -139,6 +140,7 @@ struct BlendShape {
     const uint32_t *tile_order;   // persistent: tiles in this order (null: natural order)
     uint32_t *queue;              // persistent: zeroed work counter
     int grid;                     // persistent: resident blocks
+    bool importance;              // forward: accumulate SceneDesc::importance
 };
 
 cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,

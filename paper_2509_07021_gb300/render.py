@@ -43,20 +43,29 @@ def _alloc_outputs(cams, device):
             torch.empty(P, dtype=torch.int32, device=device))
 
 
-def render_forward(scene: DeviceScene, cams, stream=None) -> ForwardOut:
+def render_forward(scene: DeviceScene, cams, stream=None, importance=None) -> ForwardOut:
+    """Plain forward. importance: optional float32 [N] tensor that receives the
+    per-Gaussian importance score (sum of alpha T over the views' pixels)."""
     device = scene.means.device
     img, T, last = _alloc_outputs(cams, device)
     key = _key(scene, cams)
     hint = _PAIR_HINT.get(key)
     if hint is None:
         hint = 8 * scene.n * len(cams)
+
+    def call(ws):
+        if importance is None:
+            return _sg.sg_render_forward(scene, cams, ws, img, T, last, stream, raise_on_error=False)
+        return _sg.sg_render_forward_importance(scene, cams, ws, img, T, last, importance, stream,
+                                                raise_on_error=False)
+
     sizes = _sg.sg_workspace_query(scene, cams, int(hint * PAIR_HEADROOM) + 1024)
     ws = torch.empty(sizes["ws_bytes"], dtype=torch.uint8, device=device)
-    st, out = _sg.sg_render_forward(scene, cams, ws, img, T, last, stream, raise_on_error=False)
+    st, out = call(ws)
     if st == _sg.SG_ERR_CAPACITY:
         sizes = _sg.sg_workspace_query(scene, cams, int(out["n_pairs"] * PAIR_HEADROOM) + 1024)
         ws = torch.empty(sizes["ws_bytes"], dtype=torch.uint8, device=device)
-        st, out = _sg.sg_render_forward(scene, cams, ws, img, T, last, stream, raise_on_error=False)
+        st, out = call(ws)
     if st != _sg.SG_OK:
         raise SGError(st, _sg.sg_last_error())
     _PAIR_HINT[key] = out["n_pairs"]

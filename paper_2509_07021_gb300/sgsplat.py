@@ -27,7 +27,8 @@ EXPORTS = ("sg_version", "sg_last_error", "sg_workspace_query", "sg_workspace_la
            "sg_render_forward", "sg_render_backward", "sg_profile_enable", "sg_profile_read",
            "sg_profile_stage_name", "sg_kernel_launches", "sg_render_backward_noalloc",
            "sg_set_tuning", "sg_get_tuning", "sg_batched_workspace_query",
-           "sg_render_batched_forward", "sg_render_batched_backward", "sg_forward_status")
+           "sg_render_batched_forward", "sg_render_batched_backward", "sg_forward_status",
+           "sg_render_forward_importance")
 SG_NOALLOC_SCRATCH_BYTES = 16 << 20
 SG_PROFILE_EVENTS, SG_PROFILE_COUNT, SG_PROFILE_STAGES = 1, 2, 12
 
@@ -136,7 +137,10 @@ def lib():
                                                  ctypes.POINTER(sg_sizes)]
         L.sg_batched_workspace_query.restype = ctypes.c_int
         L.sg_render_batched_forward.argtypes = [PS, ctypes.c_int, PC, _P, ctypes.c_int, _P, ctypes.c_size_t,
-                                                _P, _P, _P, _P]
+                                                _P, _P, _P, _P, _P]
+        L.sg_render_forward_importance.argtypes = [PS, PC, ctypes.c_int, _P, ctypes.c_size_t, _P, _P, _P,
+                                                   _P, ctypes.POINTER(sg_sizes), _P]
+        L.sg_render_forward_importance.restype = ctypes.c_int
         L.sg_render_batched_forward.restype = ctypes.c_int
         L.sg_render_batched_backward.argtypes = [PS, ctypes.c_int, PC, _P, ctypes.c_int, _P, ctypes.c_size_t,
                                                  _P, _P, _P, _P, ctypes.c_size_t, ctypes.POINTER(sg_grads), _P]
@@ -402,11 +406,28 @@ def sg_batched_workspace_query(scenes, cams, view_scene, pair_capacity: int) -> 
     return out.as_dict()
 
 
-def sg_render_batched_forward(scenes, cams, view_scene, ws, img, T_final, last, stream=None):
+def sg_render_batched_forward(scenes, cams, view_scene, ws, img, T_final, last, importance=None,
+                              stream=None):
+    imp = None
+    if importance is not None:
+        imp = (ctypes.c_void_p * len(scenes))(*[t.data_ptr() if t.numel() else None for t in importance])
     _check(lib().sg_render_batched_forward(scene_array(scenes), len(scenes), camera_array(cams),
                                            _view_scene_array(view_scene), len(cams), _ptr(ws),
                                            ws.numel(), _ptr(img), _ptr(T_final), _ptr(last),
-                                           _stream_handle(stream)))
+                                           imp, _stream_handle(stream)))
+
+
+def sg_render_forward_importance(scene: DeviceScene, cams, ws, img, T_final, last, importance,
+                                 stream=None, raise_on_error=True):
+    s = scene.struct()
+    c = camera_array(cams)
+    out = sg_sizes()
+    st = lib().sg_render_forward_importance(ctypes.byref(s), c, len(cams), _ptr(ws), ws.numel(),
+                                            _ptr(img), _ptr(T_final), _ptr(last), _ptr(importance),
+                                            ctypes.byref(out), _stream_handle(stream))
+    if raise_on_error:
+        _check(st)
+    return st, out.as_dict()
 
 
 def sg_render_batched_backward(scenes, cams, view_scene, ws, T_final, last, d_img, bwd_ws,

@@ -130,3 +130,19 @@ def test_graph_replay_matches_eager():
             assert torch.linalg.norm(a - b) <= 1e-5 * torch.linalg.norm(b) + 1e-12, k
     n, st = br.status()
     assert st == sgsplat.SG_OK
+
+
+def test_batched_importance_per_scene():
+    scenes, cams, view_scene = _batch(4)
+    ds = [DeviceScene.from_host(s) for s in scenes]
+    br = render.BatchedRenderer(ds, cams, view_scene)
+    imps = [torch.zeros(d.n, device="cuda") for d in ds]
+    sgsplat.sg_render_batched_forward(ds, cams, view_scene, br.ws, br.img, br.T_final, br.last,
+                                      importance=imps)
+    torch.cuda.synchronize()
+    for s, scene in enumerate(scenes):
+        vs = [v for v in range(len(cams)) if view_scene[v] == s]
+        results, _ = oracle.render(scene, [cams[v] for v in vs])
+        expect = sum(r.importance for r in results)
+        got = imps[s].cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(got - expect) <= 1e-3 * np.linalg.norm(expect)

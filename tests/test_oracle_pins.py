@@ -364,7 +364,7 @@ def test_weight_sum_and_monotone_T(orc):
         bg = np.zeros(3)
         orc.lib().orc_blend_forward(96, 80, p(r), p(res.ids), p(res.xy), p(res.conic),
                                     p(res.op), p(res.rgb), p(bg), None, p(img), p(T),
-                                    p(last), p(amb), None)
+                                    p(last), p(amb), None, None)
         if prev is not None:
             assert (T <= prev + 1e-15).all()
         prev = T
@@ -529,3 +529,31 @@ def test_adjoint_zero_on_clamped_branches(orc):
     assert r.T_final.max() == pytest.approx(0.01, rel=1e-12)
     assert gr["opac"][0] == 0.0 and gr["gmask"][0] == 0.0
     assert gr["c0"][0, 0] == 0.0 and gr["c0"][1, 0] > 0
+
+
+# ---------------------------------------------------------------------------
+# Importance score (App. A.2): I_i = sum over rays of alpha_i T_i
+# ---------------------------------------------------------------------------
+
+def test_importance_sums_to_coverage(orc):
+    """Sum_i I_i = sum over pixels of (1 - T_final): the blend weights of a pixel
+    add up to its coverage."""
+    rng = np.random.default_rng(31)
+    scene = synth.make_scene(rng, 600, lobes=synth.LOBE_MIX, means="cube", masks="uniform")
+    cam = synth.make_camera(80, 64, 90.0)
+    res = orc.render_forward(scene, cam)
+    assert res.importance.sum() == pytest.approx((1 - res.T_final).sum(), rel=1e-12)
+    assert (res.importance >= 0).all()
+    assert (res.importance[~res.dec.visible] == 0).all()
+
+
+def test_importance_single_gaussian_closed_form(orc):
+    """One Gaussian: I = sum over its pixels of alpha (T = 1 in front of it)."""
+    cam = synth.make_camera(48, 48, 150.0)
+    g = one_gaussian_scene((0.05, 0.02, 4.0), (0.07,) * 3, opac=0.6)
+    res = orc.render_forward(g, cam)
+    assert res.importance[0] == pytest.approx((1 - res.T_final).sum(), rel=1e-12)
+    # brute force over pixels from the image itself: colour 1 in every channel
+    g.c0[:] = 1.0
+    res1 = orc.render_forward(g, cam)
+    assert res.importance[0] == pytest.approx(res1.img[0].sum(), rel=1e-12)
