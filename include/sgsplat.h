@@ -313,6 +313,33 @@ int sg_render_batched_backward(const sg_scene *scenes, int n_scenes, const sg_ca
 int sg_forward_status(const void *ws, uint64_t *n_pairs, int32_t *status, void *stream);
 
 /*
+ * ADMM steps of the memory-constrained optimisation (Alg. 1; Sec. 3.3.2).
+ * All arrays are device binary32 vectors of n entries (opacities: one per
+ * Gaussian; sharpness: one per lobe, amp [3][n_lobes]); the workspace
+ * (sg_admm_workspace_bytes(n), 256-byte aligned) is scratch.
+ *
+ * sg_admm_opacity_step: proximal step of Eq. 8 and dual update. With
+ *   z = opac + lambda, keeps the kappa entries with the largest score --
+ *   importance[i] (the importance-based selection of App. A.2) or, when
+ *   importance is NULL, |z_i| (magnitude-based) -- equal scores by lower
+ *   index: opac_tilde = z there, 0 elsewhere; then lambda += opac - opac_tilde.
+ * sg_admm_sharpness_step: the same for lobe sharpness (Eq. 9) with the score
+ *   D_i = |a_i| |1 - exp(-2 z_i)| (Eq. 10, |a| the Euclidean norm of the RGB
+ *   amplitude).
+ * sg_admm_penalty_grad: the penalty term of the gradient step,
+ *   grad += delta (x - x_tilde + lambda).
+ * n must be below 2^32 - 1; kappa <= 0 keeps nothing, kappa >= n keeps all.
+ */
+size_t sg_admm_workspace_bytes(int64_t n);
+int sg_admm_opacity_step(int64_t n, const float *opac, const float *importance, int64_t kappa,
+                         float *lambda, float *opac_tilde, void *ws, size_t ws_bytes, void *stream);
+int sg_admm_sharpness_step(int64_t n_lobes, const float *sharp, const float *amp, int64_t kappa,
+                           float *lambda, float *sharp_tilde, void *ws, size_t ws_bytes,
+                           void *stream);
+int sg_admm_penalty_grad(int64_t n, const float *x, const float *x_tilde, const float *lambda,
+                         float delta, float *grad, void *stream);
+
+/*
  * Backward without caller scratch. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory at render
  * time -- an engine frame loop or a serving process that reserves all of its

@@ -698,6 +698,54 @@ int sg_render_batched_backward(const sg_scene *scenes, int n_scenes, const sg_ca
                          bwd_ws_bytes, grads, static_cast<cudaStream_t>(stream));
 }
 
+size_t sg_admm_workspace_bytes(int64_t n) { return admm_workspace_bytes(n); }
+
+static int admm_check(int64_t n, const void *ws, size_t ws_bytes) {
+    if (n < 0 || n >= (int64_t)UINT32_MAX) return fail(SG_ERR_INVALID_ARG, "n = %lld out of range", (long long)n);
+    if (n > 0 && (!ws || !aligned(ws, ALIGN)))
+        return fail(SG_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+    if (ws_bytes < admm_workspace_bytes(n))
+        return fail(SG_ERR_WORKSPACE, "workspace of %zu bytes, %zu needed", ws_bytes, admm_workspace_bytes(n));
+    return SG_OK;
+}
+
+int sg_admm_opacity_step(int64_t n, const float *opac, const float *importance, int64_t kappa, float *lambda,
+                         float *opac_tilde, void *ws, size_t ws_bytes, void *stream) {
+    g_err[0] = '\0';
+    int st = admm_check(n, ws, ws_bytes);
+    if (st != SG_OK) return st;
+    if (n > 0 && (!opac || !lambda || !opac_tilde))
+        return fail(SG_ERR_INVALID_ARG, "opac, lambda and opac_tilde must not be NULL");
+    SG_CUDA(launch_admm_step(0, n, opac, importance, nullptr, kappa, lambda, opac_tilde, ws,
+                             static_cast<cudaStream_t>(stream)),
+            "ADMM opacity step");
+    return SG_OK;
+}
+
+int sg_admm_sharpness_step(int64_t n_lobes, const float *sharp, const float *amp, int64_t kappa, float *lambda,
+                           float *sharp_tilde, void *ws, size_t ws_bytes, void *stream) {
+    g_err[0] = '\0';
+    int st = admm_check(n_lobes, ws, ws_bytes);
+    if (st != SG_OK) return st;
+    if (n_lobes > 0 && (!sharp || !amp || !lambda || !sharp_tilde))
+        return fail(SG_ERR_INVALID_ARG, "sharp, amp, lambda and sharp_tilde must not be NULL");
+    SG_CUDA(launch_admm_step(1, n_lobes, sharp, nullptr, amp, kappa, lambda, sharp_tilde, ws,
+                             static_cast<cudaStream_t>(stream)),
+            "ADMM sharpness step");
+    return SG_OK;
+}
+
+int sg_admm_penalty_grad(int64_t n, const float *x, const float *x_tilde, const float *lambda, float delta,
+                         float *grad, void *stream) {
+    g_err[0] = '\0';
+    if (n < 0) return fail(SG_ERR_INVALID_ARG, "n < 0");
+    if (n > 0 && (!x || !x_tilde || !lambda || !grad))
+        return fail(SG_ERR_INVALID_ARG, "x, x_tilde, lambda and grad must not be NULL");
+    SG_CUDA(launch_penalty_grad(n, x, x_tilde, lambda, delta, grad, static_cast<cudaStream_t>(stream)),
+            "ADMM penalty gradient");
+    return SG_OK;
+}
+
 int sg_forward_status(const void *ws, uint64_t *n_pairs, int32_t *status, void *stream) {
     if (!ws || !aligned(ws, ALIGN)) return fail(SG_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
     // the counters sit right after the batch table, whatever the sizes

@@ -152,6 +152,14 @@ cudaError_t launch_blend_backward(const Batch *db, uint32_t n_tiles, const uint2
                                   const int32_t *last, const float *d_img, float *dg,
                                   uint64_t M, const BlendShape &shape, unsigned long long *evals,
                                   cudaStream_t s);
+// ADMM proximal + dual step (kind 0: opacity, 1: sharpness) and the penalty
+// gradient term; workspace bytes for n items.
+size_t admm_workspace_bytes(int64_t n);
+cudaError_t launch_admm_step(int kind, int64_t n, const float *x, const float *score, const float *amp,
+                             int64_t kappa, float *lam, float *x_tilde, void *ws, cudaStream_t s);
+cudaError_t launch_penalty_grad(int64_t n, const float *x, const float *x_tilde, const float *lam, float delta,
+                                float *grad, cudaStream_t s);
+
 // Resident blocks per SM x SMs for the persistent blend of this shape.
 int blend_persistent_grid(bool backward, int pixels_per_thread);
 

@@ -28,7 +28,8 @@ EXPORTS = ("sg_version", "sg_last_error", "sg_workspace_query", "sg_workspace_la
            "sg_profile_stage_name", "sg_kernel_launches", "sg_render_backward_noalloc",
            "sg_set_tuning", "sg_get_tuning", "sg_batched_workspace_query",
            "sg_render_batched_forward", "sg_render_batched_backward", "sg_forward_status",
-           "sg_render_forward_importance")
+           "sg_render_forward_importance", "sg_admm_workspace_bytes", "sg_admm_opacity_step",
+           "sg_admm_sharpness_step", "sg_admm_penalty_grad")
 SG_NOALLOC_SCRATCH_BYTES = 16 << 20
 SG_PROFILE_EVENTS, SG_PROFILE_COUNT, SG_PROFILE_STAGES = 1, 2, 12
 
@@ -147,6 +148,16 @@ def lib():
         L.sg_render_batched_backward.restype = ctypes.c_int
         L.sg_forward_status.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32), _P]
         L.sg_forward_status.restype = ctypes.c_int
+        L.sg_admm_workspace_bytes.argtypes = [ctypes.c_int64]
+        L.sg_admm_workspace_bytes.restype = ctypes.c_size_t
+        L.sg_admm_opacity_step.argtypes = [ctypes.c_int64, _P, _P, ctypes.c_int64, _P, _P, _P,
+                                           ctypes.c_size_t, _P]
+        L.sg_admm_opacity_step.restype = ctypes.c_int
+        L.sg_admm_sharpness_step.argtypes = [ctypes.c_int64, _P, _P, ctypes.c_int64, _P, _P, _P,
+                                             ctypes.c_size_t, _P]
+        L.sg_admm_sharpness_step.restype = ctypes.c_int
+        L.sg_admm_penalty_grad.argtypes = [ctypes.c_int64, _P, _P, _P, ctypes.c_float, _P, _P]
+        L.sg_admm_penalty_grad.restype = ctypes.c_int
         L.sg_kernel_launches.argtypes = []
         L.sg_kernel_launches.restype = ctypes.c_int64
         L.sg_profile_stage_name.argtypes = [ctypes.c_int]
@@ -447,3 +458,43 @@ def sg_forward_status(ws, stream=None):
     st = ctypes.c_int32()
     _check(lib().sg_forward_status(_ptr(ws), ctypes.byref(n), ctypes.byref(st), _stream_handle(stream)))
     return int(n.value), int(st.value)
+
+
+# ---------------------------------------------------------------------------
+# ADMM steps (Alg. 1)
+# ---------------------------------------------------------------------------
+
+def sg_admm_workspace_bytes(n: int) -> int:
+    return int(lib().sg_admm_workspace_bytes(int(n)))
+
+
+def _admm_ws(n, ws, device):
+    need = sg_admm_workspace_bytes(n)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=device)
+    return ws
+
+
+def sg_admm_opacity_step(opac, lam, opac_tilde, kappa, importance=None, ws=None, stream=None):
+    """Proximal step (top-kappa by importance, or by |opac + lambda|) and dual
+    update, in place on lam and opac_tilde."""
+    n = opac.numel()
+    ws = _admm_ws(n, ws, opac.device)
+    _check(lib().sg_admm_opacity_step(n, _ptr(opac), _ptr(importance), int(kappa), _ptr(lam),
+                                      _ptr(opac_tilde), _ptr(ws), ws.numel(), _stream_handle(stream)))
+    return ws
+
+
+def sg_admm_sharpness_step(sharp, amp, lam, sharp_tilde, kappa, ws=None, stream=None):
+    """Proximal step (top-kappa lobes by dynamic range) and dual update."""
+    n = sharp.numel()
+    ws = _admm_ws(n, ws, sharp.device)
+    _check(lib().sg_admm_sharpness_step(n, _ptr(sharp), _ptr(amp), int(kappa), _ptr(lam),
+                                        _ptr(sharp_tilde), _ptr(ws), ws.numel(), _stream_handle(stream)))
+    return ws
+
+
+def sg_admm_penalty_grad(x, x_tilde, lam, delta, grad, stream=None):
+    """grad += delta * (x - x_tilde + lam), in place."""
+    _check(lib().sg_admm_penalty_grad(x.numel(), _ptr(x), _ptr(x_tilde), _ptr(lam), float(delta),
+                                      _ptr(grad), _stream_handle(stream)))
