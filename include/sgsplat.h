@@ -340,6 +340,26 @@ int sg_admm_penalty_grad(int64_t n, const float *x, const float *x_tilde, const 
                          float delta, float *grad, void *stream);
 
 /*
+ * Post-processing after the constrained optimisation (Sec. 3.3.3, Eq. 11-13):
+ * Gaussians whose opacity m_g o is below tau_opacity are removed; lobes of the
+ * others whose sharpness is below tau_sharpness (1 in the paper, App. A.3)
+ * are removed and each removed lobe's mean over the sphere,
+ * m_l a (1 - e^{-2s}) / (2s) (a at s = 0), is added to c0; kept Gaussians and
+ * lobes keep their order. Binary32 scenes only.
+ * sg_postprocess_plan: counts the kept Gaussians and lobes into *n_out and
+ *   *l_out (host; synchronises `stream`). ws: device scratch of
+ *   sg_postprocess_workspace_bytes(in->n) bytes, kept for the apply call.
+ * sg_postprocess_apply: writes the compacted scene into `out` (host struct of
+ *   caller-allocated device arrays with out->n = *n_out and
+ *   out->n_lobes = *l_out; out->lobe_off holds n_out + 1 entries).
+ */
+size_t sg_postprocess_workspace_bytes(int64_t n);
+int sg_postprocess_plan(const sg_scene *in, float tau_opacity, float tau_sharpness, void *ws,
+                        size_t ws_bytes, int64_t *n_out, int64_t *l_out, void *stream);
+int sg_postprocess_apply(const sg_scene *in, float tau_opacity, float tau_sharpness,
+                         const void *ws, size_t ws_bytes, const sg_scene *out, void *stream);
+
+/*
  * Backward without caller scratch. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory at render
  * time -- an engine frame loop or a serving process that reserves all of its

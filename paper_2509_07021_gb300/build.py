@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsgsplat.so")
-SOURCES = ["sg_api.cu", "sg_preprocess.cu", "sg_sort.cu", "sg_blend.cu", "sg_admm.cu"]
+SOURCES = ["sg_api.cu", "sg_preprocess.cu", "sg_sort.cu", "sg_blend.cu", "sg_admm.cu", "sg_post.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -746,6 +746,59 @@ int sg_admm_penalty_grad(int64_t n, const float *x, const float *x_tilde, const 
     return SG_OK;
 }
 
+size_t sg_postprocess_workspace_bytes(int64_t n) { return post_workspace_bytes(n); }
+
+static int post_check(const sg_scene *in, const void *ws, size_t ws_bytes) {
+    if (!in) return fail(SG_ERR_INVALID_ARG, "scene must not be NULL");
+    if (in->n < 0 || in->n >= (int64_t)INT32_MAX || in->n_lobes < 0 || in->n_lobes >= (int64_t)INT32_MAX)
+        return fail(SG_ERR_INVALID_ARG, "sizes out of range");
+    if (in->dtype_geom != SG_F32 || in->dtype_lobe != SG_F32 || in->dtype_sharp != SG_F32)
+        return fail(SG_ERR_INVALID_ARG, "post-processing reads binary32 scenes only");
+    if (in->n > 0) {
+        const void *req[] = {in->means, in->scales, in->quats, in->opac, in->gmask, in->c0, in->lobe_off};
+        for (const void *p : req)
+            if (!p) return fail(SG_ERR_INVALID_ARG, "a Gaussian array is NULL");
+    }
+    if (in->n_lobes > 0 && (!in->axis || !in->sharp || !in->amp || !in->lmask))
+        return fail(SG_ERR_INVALID_ARG, "a lobe array is NULL");
+    if (!ws || !aligned(ws, ALIGN)) return fail(SG_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+    if (ws_bytes < post_workspace_bytes(in->n))
+        return fail(SG_ERR_WORKSPACE, "workspace of %zu bytes, %zu needed", ws_bytes, post_workspace_bytes(in->n));
+    return SG_OK;
+}
+
+int sg_postprocess_plan(const sg_scene *in, float tau_opacity, float tau_sharpness, void *ws, size_t ws_bytes,
+                        int64_t *n_out, int64_t *l_out, void *stream) {
+    g_err[0] = '\0';
+    int st = post_check(in, ws, ws_bytes);
+    if (st != SG_OK) return st;
+    uint64_t totals[2] = {0, 0};
+    SG_CUDA(launch_post_plan(*in, tau_opacity, tau_sharpness, ws, totals, static_cast<cudaStream_t>(stream)),
+            "post-processing plan");
+    if (n_out) *n_out = (int64_t)totals[0];
+    if (l_out) *l_out = (int64_t)totals[1];
+    return SG_OK;
+}
+
+int sg_postprocess_apply(const sg_scene *in, float tau_opacity, float tau_sharpness, const void *ws,
+                         size_t ws_bytes, const sg_scene *out, void *stream) {
+    g_err[0] = '\0';
+    int st = post_check(in, ws, ws_bytes);
+    if (st != SG_OK) return st;
+    if (!out || !out->lobe_off) return fail(SG_ERR_INVALID_ARG, "out and out->lobe_off must not be NULL");
+    if (out->n > 0) {
+        const void *req[] = {out->means, out->scales, out->quats, out->opac, out->gmask, out->c0};
+        for (const void *p : req)
+            if (!p) return fail(SG_ERR_INVALID_ARG, "an output Gaussian array is NULL");
+    }
+    if (out->n_lobes > 0 && (!out->axis || !out->sharp || !out->amp || !out->lmask))
+        return fail(SG_ERR_INVALID_ARG, "an output lobe array is NULL");
+    SG_CUDA(launch_post_apply(*in, tau_opacity, tau_sharpness, ws, *out, out->n, out->n_lobes,
+                              static_cast<cudaStream_t>(stream)),
+            "post-processing apply");
+    return SG_OK;
+}
+
 int sg_forward_status(const void *ws, uint64_t *n_pairs, int32_t *status, void *stream) {
     if (!ws || !aligned(ws, ALIGN)) return fail(SG_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
     // the counters sit right after the batch table, whatever the sizes

@@ -160,6 +160,13 @@ cudaError_t launch_admm_step(int kind, int64_t n, const float *x, const float *s
 cudaError_t launch_penalty_grad(int64_t n, const float *x, const float *x_tilde, const float *lam, float delta,
                                 float *grad, cudaStream_t s);
 
+// Post-processing (Sec. 3.3.3): plan (flags, scans, totals read back) and apply.
+size_t post_workspace_bytes(int64_t n);
+cudaError_t launch_post_plan(const sg_scene &sc, float tau_o, float tau_s, void *ws, uint64_t *totals_host,
+                             cudaStream_t s);
+cudaError_t launch_post_apply(const sg_scene &sc, float tau_o, float tau_s, const void *ws, const sg_scene &out,
+                              int64_t n_out, int64_t l_out, cudaStream_t s);
+
 // Resident blocks per SM x SMs for the persistent blend of this shape.
 int blend_persistent_grid(bool backward, int pixels_per_thread);
 

@@ -29,7 +29,8 @@ EXPORTS = ("sg_version", "sg_last_error", "sg_workspace_query", "sg_workspace_la
            "sg_set_tuning", "sg_get_tuning", "sg_batched_workspace_query",
            "sg_render_batched_forward", "sg_render_batched_backward", "sg_forward_status",
            "sg_render_forward_importance", "sg_admm_workspace_bytes", "sg_admm_opacity_step",
-           "sg_admm_sharpness_step", "sg_admm_penalty_grad")
+           "sg_admm_sharpness_step", "sg_admm_penalty_grad", "sg_postprocess_workspace_bytes",
+           "sg_postprocess_plan", "sg_postprocess_apply")
 SG_NOALLOC_SCRATCH_BYTES = 16 << 20
 SG_PROFILE_EVENTS, SG_PROFILE_COUNT, SG_PROFILE_STAGES = 1, 2, 12
 
@@ -158,6 +159,13 @@ def lib():
         L.sg_admm_sharpness_step.restype = ctypes.c_int
         L.sg_admm_penalty_grad.argtypes = [ctypes.c_int64, _P, _P, _P, ctypes.c_float, _P, _P]
         L.sg_admm_penalty_grad.restype = ctypes.c_int
+        L.sg_postprocess_workspace_bytes.argtypes = [ctypes.c_int64]
+        L.sg_postprocess_workspace_bytes.restype = ctypes.c_size_t
+        L.sg_postprocess_plan.argtypes = [PS, ctypes.c_float, ctypes.c_float, _P, ctypes.c_size_t,
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _P]
+        L.sg_postprocess_plan.restype = ctypes.c_int
+        L.sg_postprocess_apply.argtypes = [PS, ctypes.c_float, ctypes.c_float, _P, ctypes.c_size_t, PS, _P]
+        L.sg_postprocess_apply.restype = ctypes.c_int
         L.sg_kernel_launches.argtypes = []
         L.sg_kernel_launches.restype = ctypes.c_int64
         L.sg_profile_stage_name.argtypes = [ctypes.c_int]
@@ -498,3 +506,34 @@ def sg_admm_penalty_grad(x, x_tilde, lam, delta, grad, stream=None):
     """grad += delta * (x - x_tilde + lam), in place."""
     _check(lib().sg_admm_penalty_grad(x.numel(), _ptr(x), _ptr(x_tilde), _ptr(lam), float(delta),
                                       _ptr(grad), _stream_handle(stream)))
+
+
+# ---------------------------------------------------------------------------
+# post-processing (Sec. 3.3.3)
+# ---------------------------------------------------------------------------
+
+def sg_postprocess(scene: DeviceScene, tau_opacity: float, tau_sharpness: float = 1.0,
+                   stream=None) -> DeviceScene:
+    """Removes low-opacity Gaussians and low-sharpness lobes (with the colour
+    compensation of Eq. 12-13) and returns the compacted binary32 scene."""
+    dev = scene.means.device
+    n = scene.n
+    ws = torch.empty(max(int(lib().sg_postprocess_workspace_bytes(n)), 256), dtype=torch.uint8,
+                     device=dev)
+    s_in = scene.struct()
+    n_out, l_out = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sg_postprocess_plan(ctypes.byref(s_in), float(tau_opacity), float(tau_sharpness),
+                                     _ptr(ws), ws.numel(), ctypes.byref(n_out), ctypes.byref(l_out),
+                                     _stream_handle(stream)))
+    N, L = int(n_out.value), int(l_out.value)
+    f = dict(device=dev, dtype=torch.float32)
+    out = DeviceScene(means=torch.empty(3, N, **f), scales=torch.empty(3, N, **f),
+                      quats=torch.empty(4, N, **f), opac=torch.empty(N, **f), gmask=torch.empty(N, **f),
+                      c0=torch.empty(3, N, **f), lobe_off=torch.empty(N + 1, dtype=torch.int32, device=dev),
+                      axis=torch.empty(3, L, **f), sharp=torch.empty(L, **f), amp=torch.empty(3, L, **f),
+                      lmask=torch.empty(L, **f))
+    s_out = out.struct()
+    s_out.lobe_off = out.lobe_off.data_ptr()
+    _check(lib().sg_postprocess_apply(ctypes.byref(s_in), float(tau_opacity), float(tau_sharpness),
+                                      _ptr(ws), ws.numel(), ctypes.byref(s_out), _stream_handle(stream)))
+    return out
