@@ -12,6 +12,8 @@
 // ranks that writes x~ and the new lambda.
 #include "sg_internal.cuh"
 
+#include <algorithm>
+
 namespace sgk {
 
 // Order-preserving key for a DESCENDING sort through an ascending radix sort.
@@ -95,7 +97,8 @@ static AdmmLayout admm_layout(int64_t n) {
     L.v1 = take(4 * (size_t)n);
     const uint64_t hb = div_up((uint64_t)n, RS_TILE);
     L.hist = take((size_t)RS_RADIX * hb * 4);
-    L.sums = take((div_up((uint64_t)n, SCAN_TILE) + div_up((uint64_t)RS_RADIX * hb, SCAN_TILE) + 1) * 8);
+    L.sums = take(std::max<size_t>((div_up((uint64_t)n, SCAN_TILE) + div_up((uint64_t)RS_RADIX * hb, SCAN_TILE) + 1) * 8,
+                                   SORT_AUX_BYTES));
     L.total = o;
     return L;
 }

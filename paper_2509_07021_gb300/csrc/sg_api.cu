@@ -256,7 +256,7 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     L.hist_blocks = (uint32_t)div_up(items, RS_TILE);
     L.hist = take((size_t)RS_RADIX * L.hist_blocks * 4);
     const uint64_t sums = div_up(items, SCAN_TILE) + div_up((uint64_t)RS_RADIX * L.hist_blocks, SCAN_TILE) + 1;
-    L.scan_sums = take(sums * 8);
+    L.scan_sums = take(std::max<size_t>(sums * 8, SORT_AUX_BYTES));
     L.total = o;
     L.M = M;
     L.n_tiles = T;
@@ -296,7 +296,8 @@ BwdLayout bwd_layout(const Batch &b) {
     L.tov1 = take(T * 4);
     const uint64_t hb = div_up(T, RS_TILE);
     L.hist = take((size_t)RS_RADIX * hb * 4);
-    L.sums = take((div_up(T, SCAN_TILE) + div_up((uint64_t)RS_RADIX * hb, SCAN_TILE) + 1) * 8);
+    L.sums = take(std::max<size_t>((div_up(T, SCAN_TILE) + div_up((uint64_t)RS_RADIX * hb, SCAN_TILE) + 1) * 8,
+                                   SORT_AUX_BYTES));
     L.total = o;
     return L;
 }
@@ -390,7 +391,7 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         // depth digits, once per entry (result back in dkey0/dval0 after 4 passes)
         StageTimer t(ST_DEPTH_SORT, stream);
         SG_CUDA(launch_radix_sort(dkey0, dval0, dkey1, dval1, counters + CNT_ENTRIES, M, 32, hist, sums,
-                                  stream),
+                                  stream, counters + CNT_STATUS),
                 "depth sort");
     }
     {
@@ -399,12 +400,16 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     }
     uint64_t K = cap;   // batched form: grids sized by the capacity, counts read on the device
     if (sync) {
+        uint64_t cnt_host[3] = {0, 0, 0};
         {
             StageTimer t(ST_READ_PAIRS, stream);
-            SG_CUDA(cudaMemcpyAsync(&K, counters + CNT_PAIRS, sizeof(K), cudaMemcpyDeviceToHost, stream),
+            SG_CUDA(cudaMemcpyAsync(cnt_host, counters, sizeof(cnt_host), cudaMemcpyDeviceToHost, stream),
                     "read pairs");
         }
         SG_CUDA(cudaStreamSynchronize(stream), "read pairs");
+        K = cnt_host[CNT_PAIRS];
+        if (cnt_host[CNT_STATUS] == SG_ERR_TIMEOUT)
+            return fail(SG_ERR_TIMEOUT, "depth sort: a bounded device wait expired");
         if (K > cap || K >= (1ull << 32) - 1) {
             const WsLayout need = make_layout(b, K);
             fill_sizes(b, need, K, out);
@@ -429,7 +434,8 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     }
     {
         StageTimer t(ST_TILE_SORT, stream);
-        SG_CUDA(launch_radix_sort(k0, v0, k1, v1, counters + CNT_PAIRS, K, L.tile_bits, hist, sums, stream),
+        SG_CUDA(launch_radix_sort(k0, v0, k1, v1, counters + CNT_PAIRS, K, L.tile_bits, hist, sums, stream,
+                                  counters + CNT_STATUS),
                 "tile sort");
     }
     {

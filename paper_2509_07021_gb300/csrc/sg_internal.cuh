@@ -113,11 +113,15 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
                         uint64_t n, uint64_t *block_sums, uint64_t *total, cudaStream_t s);
 
 // Stable LSD radix sort of (key, val) u32 pairs on bits [0, bits); item count read
-// from *n_dev, at most max_n. Ping-pongs between (k0,v0) and (k1,v1); the
-// sorted result ends in (k0,v0) when the pass count is even, else in (k1,v1).
+// from *n_dev and clamped to max_n (the capacity the launch is sized for, below
+// 2^30). Ping-pongs between (k0,v0) and (k1,v1); the sorted result ends in
+// (k0,v0) when the pass count is even, else in (k1,v1).
+// hist: RS_RADIX x ceil(max_n / RS_TILE) words of look-back flags; aux: at least
+// SORT_AUX_BYTES; status (nullable): set to SG_ERR_TIMEOUT if a look-back gave up.
+constexpr size_t SORT_AUX_BYTES = 16384;
 cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
-                              uint64_t *scan_sums, cudaStream_t s);
+                              uint64_t *aux, cudaStream_t s, uint64_t *status = nullptr);
 int radix_passes(int bits);
 
 cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,

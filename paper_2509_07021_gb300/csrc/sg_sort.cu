@@ -13,6 +13,8 @@
 
 namespace sgk {
 
+__host__ __device__ __forceinline__ int radix_passes_dev(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     return (1u << (threadIdx.x & 31)) - 1u;
 }
@@ -148,36 +150,75 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort, 8-bit digits, 4096 keys per block
+// stable LSD radix sort, 8-bit digits, 4096 keys per block, one sweep per pass
 // ---------------------------------------------------------------------------
-// Item counts come from the device (*n_dev) and are clamped to the capacity
-// the launch was sized for (max_n), so an overflowing count can never index
-// past the buffers.
-__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t *__restrict__ keys,
-                                                           const uint64_t *__restrict__ n_dev,
-                                                           uint64_t max_n, int shift, uint32_t mask,
-                                                           uint32_t *__restrict__ hist,
-                                                           uint32_t nblocks) {
-    __shared__ uint32_t h[RS_RADIX];
-    h[threadIdx.x] = 0u;
+// One kernel histograms every digit position at once; a second turns them into
+// per-pass digit bases. Each pass is then a single kernel: blocks take key
+// tiles in order from an atomic counter, rank their keys stably (warp
+// match_any + per-warp digit counters), publish their digit counts, and get
+// their global offsets by looking back over the tiles before them (decoupled
+// look-back). A look-back spin is bounded: past the bound the block records
+// SG_ERR_TIMEOUT in the status word and carries on with a wrong offset
+// instead of waiting forever.
+
+// packed look-back word: 2 status bits, 30 count bits
+constexpr uint32_t LB_AGG = 1u << 30, LB_INC = 2u << 30, LB_VAL = (1u << 30) - 1u;
+constexpr int LB_SPIN_LIMIT = 1 << 20;
+
+struct SortAux {
+    uint32_t hist[4][RS_RADIX];   // global digit counts per pass
+    uint32_t base[4][RS_RADIX];   // exclusive digit bases per pass
+    uint32_t tile_ctr[4];         // tile counter per pass
+    uint32_t status;              // 0 or SG_ERR_TIMEOUT
+};
+static_assert(sizeof(SortAux) <= SORT_AUX_BYTES, "sort aux region");
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint32_t *__restrict__ keys,
+                                                        const uint64_t *__restrict__ n_dev, uint64_t max_n,
+                                                        int bits, SortAux *aux) {
+    __shared__ uint32_t h[4][RS_RADIX];
+    const int passes = radix_passes_dev(bits);
+    for (int p = 0; p < 4; ++p) h[p][threadIdx.x] = 0u;
     __syncthreads();
     const uint64_t n = min(*n_dev, max_n);
-    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
-    if (base < n) {
-#pragma unroll 4
-        for (int i = 0; i < RS_ITEMS; ++i) {
-            const uint64_t j = base + (uint64_t)i * RS_THREADS + threadIdx.x;
-            if (j < n) atomicAdd(&h[(keys[j] >> shift) & mask], 1u);
+    const uint64_t stride = (uint64_t)gridDim.x * RS_THREADS;
+    for (uint64_t j = (uint64_t)blockIdx.x * RS_THREADS + threadIdx.x; j < n; j += stride) {
+        const uint32_t k = keys[j];
+        for (int p = 0; p < passes; ++p) {
+            const int nb = min(8, bits - 8 * p);
+            atomicAdd(&h[p][(k >> (8 * p)) & ((1u << nb) - 1u)], 1u);
         }
     }
     __syncthreads();
-    hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t c = h[p][threadIdx.x];
+        if (c) atomicAdd(&aux->hist[p][threadIdx.x], c);
+    }
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
+__global__ void __launch_bounds__(RS_RADIX) k_os_base(SortAux *aux, int passes) {
+    __shared__ uint32_t sh[33];
+    for (int p = 0; p < passes; ++p) {
+        uint32_t tot;
+        const uint32_t ex = block_exclusive<uint32_t>(aux->hist[p][threadIdx.x], tot, sh);
+        aux->base[p][threadIdx.x] = ex;
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_os_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, const uint64_t *__restrict__ n_dev, uint64_t max_n, int shift,
-    uint32_t mask, const uint32_t *__restrict__ hist_scan, uint32_t nblocks) {
+    uint32_t *__restrict__ vout, const uint64_t *__restrict__ n_dev, uint64_t max_n, int pass, int shift,
+    uint32_t mask, uint32_t *__restrict__ flags, SortAux *aux) {
     constexpr int NW = RS_THREADS / 32;
     constexpr int PER_WARP = RS_TILE / NW;   // 512 consecutive keys per warp
     __shared__ uint32_t cnt[NW][RS_RADIX];
@@ -186,10 +227,14 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     __shared__ uint32_t sk[RS_TILE];
     __shared__ uint32_t sv[RS_TILE];
     __shared__ uint32_t shs[33];
+    __shared__ uint32_t s_tile;
 
+    if (threadIdx.x == 0) s_tile = atomicAdd(&aux->tile_ctr[pass], 1u);
+    __syncthreads();
+    const uint32_t t = s_tile;
     const uint64_t n = min(*n_dev, max_n);
-    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
-    if (base >= n) return;   // uniform across the block
+    const uint64_t base = (uint64_t)t * RS_TILE;
+    if (base >= n) return;   // uniform across the block; later tiles exit too
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NW; ++i) cnt[i][threadIdx.x] = 0u;
@@ -219,7 +264,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
         __syncwarp();
     }
     __syncthreads();
-    // per digit: exclusive offsets over warps, then over digits
+    // per digit: exclusive offsets over warps, block total, block-local start
     uint32_t run = 0u;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
@@ -227,17 +272,38 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
         cnt[w][threadIdx.x] = run;
         run += c;
     }
+    const uint32_t d = threadIdx.x;
+    // publish this tile's count, then look back for the exclusive prefix
+    uint32_t *my = flags + (uint64_t)t * RS_RADIX + d;
+    st_relaxed(my, LB_AGG | run);
+    uint32_t excl = 0u;
+    int spins = 0;
+    for (int64_t p = (int64_t)t - 1; p >= 0;) {
+        const uint32_t fv = ld_relaxed(flags + (uint64_t)p * RS_RADIX + d);
+        if ((fv & ~LB_VAL) == 0u) {
+            if (++spins > LB_SPIN_LIMIT) {
+                atomicExch(&aux->status, (uint32_t)SG_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        excl += fv & LB_VAL;
+        if (fv & LB_INC) break;
+        --p;
+    }
+    st_relaxed(my, LB_INC | ((excl + run) & LB_VAL));
     uint32_t tot;
     const uint32_t ds = block_exclusive<uint32_t>(run, tot, shs);
-    dstart[threadIdx.x] = ds;
-    gstart[threadIdx.x] = hist_scan[(uint64_t)threadIdx.x * nblocks + blockIdx.x];
+    dstart[d] = ds;
+    gstart[d] = aux->base[pass][d] + excl;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
         const uint64_t j = wbase + (uint64_t)i * 32 + lane;
         if (j < n) {
-            const uint32_t d = (k[i] >> shift) & mask;
-            const uint32_t pos = dstart[d] + cnt[warp][d] + r[i];
+            const uint32_t dd = (k[i] >> shift) & mask;
+            const uint32_t pos = dstart[dd] + cnt[warp][dd] + r[i];
             sk[pos] = k[i];
             sv[pos] = v[i];
         }
@@ -246,8 +312,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     const int items = (n - base) < (uint64_t)RS_TILE ? (int)(n - base) : RS_TILE;
     for (int p = threadIdx.x; p < items; p += RS_THREADS) {
         const uint32_t key = sk[p];
-        const uint32_t d = (key >> shift) & mask;
-        const uint32_t o = gstart[d] + (uint32_t)p - dstart[d];
+        const uint32_t dd = (key >> shift) & mask;
+        const uint32_t o = gstart[dd] + (uint32_t)p - dstart[dd];
         kout[o] = key;
         vout[o] = sv[p];
     }
@@ -255,28 +321,40 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
 
 int radix_passes(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
 
+__global__ void k_os_status(const SortAux *aux, uint64_t *status) {
+    if (aux->status) *status = aux->status;
+}
+
 cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
-                              uint64_t *scan_sums, cudaStream_t s) {
+                              uint64_t *scan_sums, cudaStream_t s, uint64_t *status) {
     const uint32_t nblocks = (uint32_t)div_up(max_n, RS_TILE);
-    if (nblocks == 0) return cudaSuccess;
     const int passes = radix_passes(bits);
+    if (nblocks == 0 || passes == 0) return cudaSuccess;
+    if (max_n > (uint64_t)LB_VAL) return cudaErrorInvalidValue;   // counts must fit the look-back word
+    SortAux *aux = reinterpret_cast<SortAux *>(scan_sums);
+    cudaError_t e = cudaMemsetAsync(aux, 0, sizeof(SortAux), s);
+    if (e != cudaSuccess) return e;
+    const unsigned hgrid = nblocks < 4u * 152u ? nblocks : 4u * 152u;
+    k_os_hist<<<hgrid, RS_THREADS, 0, s>>>(k0, n_dev, max_n, bits, aux);
+    k_os_base<<<1, RS_RADIX, 0, s>>>(aux, passes);
+    count_launches(2);
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         const int nb = min(8, bits - shift);
         const uint32_t mask = (1u << nb) - 1u;
-        k_radix_hist<<<nblocks, RS_THREADS, 0, s>>>(ki, n_dev, max_n, shift, mask, hist, nblocks);
-        count_launches(1);
-        cudaError_t e = launch_scan(hist, nullptr, hist, (uint64_t)RS_RADIX * nblocks, scan_sums,
-                                    nullptr, s);
+        e = cudaMemsetAsync(hist, 0, (size_t)nblocks * RS_RADIX * sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n_dev, max_n, shift, mask, hist,
-                                                       nblocks);
+        k_os_pass<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n_dev, max_n, p, shift, mask, hist, aux);
         count_launches(1);
         uint32_t *t;
         t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
+    }
+    if (status) {
+        k_os_status<<<1, 1, 0, s>>>(aux, status);
+        count_launches(1);
     }
     return cudaGetLastError();
 }
@@ -293,6 +371,11 @@ __device__ __forceinline__ int find_entry_view(const Batch &b, uint64_t e) {
     return lo;
 }
 
+// One block per 256 consecutive entries (depth order). The block's pairs are
+// contiguous in the output; its threads write them in order, each finding the
+// owning entry by binary search over the block's prefix sums, so stores are
+// coalesced and a large rectangle is spread over the whole block. Inside an
+// entry the tiles follow row-major order.
 __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp, uint64_t M,
                                                    const uint32_t *__restrict__ sorted_ent,
                                                    const uint32_t *__restrict__ tiles_touched,
@@ -301,24 +384,51 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
                                                    const uint64_t *__restrict__ counters, uint64_t cap,
                                                    uint32_t *__restrict__ pkey,
                                                    uint32_t *__restrict__ pval) {
-    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= M) return;
-    if (counters[CNT_PAIRS] > cap) return;   // capacity exceeded: the host reports it
-    const uint32_t e = sorted_ent[j];
-    const uint32_t tt = tiles_touched[e];
-    if (tt == 0u) return;
-    const Batch &b = *bp;
-    const ViewDesc &vw = b.view[find_entry_view(b, e)];
-    const uint2 rc = rect[e];
-    const uint32_t x0 = rc.x & 0xFFFFu, x1 = rc.x >> 16, y0 = rc.y & 0xFFFFu, y1 = rc.y >> 16;
-    uint64_t o = offsets[j];
-    for (uint32_t ty = y0; ty < y1; ++ty) {
-        const uint32_t row = vw.tile_off + ty * (uint32_t)vw.tiles_x;
-        for (uint32_t tx = x0; tx < x1; ++tx) {
-            pkey[o] = row + tx;
-            pval[o] = e;
-            ++o;
+    __shared__ uint32_t s_incl[256], s_e[256], s_x0[256], s_wx[256], s_y0[256], s_base[256], s_tx[256];
+    __shared__ uint32_t shs[33];
+    if (counters[CNT_PAIRS] > cap) return;   // capacity exceeded: the host reports it (uniform)
+    const uint64_t j0 = (uint64_t)blockIdx.x * 256;
+    const uint64_t j = j0 + threadIdx.x;
+    uint32_t e = 0, tt = 0, x0 = 0, wx = 1, y0 = 0, tbase = 0, tx = 1;
+    if (j < M) {
+        e = sorted_ent[j];
+        tt = tiles_touched[e];
+        if (tt) {
+            const Batch &b = *bp;
+            const ViewDesc &vw = b.view[find_entry_view(b, e)];
+            const uint2 rc = rect[e];
+            x0 = rc.x & 0xFFFFu;
+            wx = (rc.x >> 16) - x0;
+            y0 = rc.y & 0xFFFFu;
+            tbase = vw.tile_off;
+            tx = (uint32_t)vw.tiles_x;
         }
+    }
+    uint32_t total;
+    const uint32_t excl = block_exclusive<uint32_t>(tt, total, shs);
+    s_incl[threadIdx.x] = excl + tt;
+    s_e[threadIdx.x] = e;
+    s_x0[threadIdx.x] = x0;
+    s_wx[threadIdx.x] = wx;
+    s_y0[threadIdx.x] = y0;
+    s_base[threadIdx.x] = tbase;
+    s_tx[threadIdx.x] = tx;
+    __syncthreads();
+    if (total == 0u) return;
+    const uint64_t out0 = offsets[j0];
+    for (uint32_t q = threadIdx.x; q < total; q += 256) {
+        // first owner o with incl[o] > q
+        int lo = 0, hi = 255;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_incl[mid] > q) hi = mid; else lo = mid + 1;
+        }
+        const uint32_t start = lo ? s_incl[lo - 1] : 0u;
+        const uint32_t li = q - start;
+        const uint32_t w = s_wx[lo];
+        const uint32_t ry = li / w, rx = li - ry * w;
+        pkey[out0 + q] = s_base[lo] + (s_y0[lo] + ry) * s_tx[lo] + s_x0[lo] + rx;
+        pval[out0 + q] = s_e[lo];
     }
 }
 
@@ -379,7 +489,7 @@ cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, const uint6
     k_tile_keys<<<(unsigned)div_up(n_tiles, 256), 256, 0, s>>>(ranges, n_tiles, k0, v0);
     count_launches(1);
     // two stable 8-bit passes: the order ends in (k0, v0)
-    return launch_radix_sort(k0, v0, k1, v1, n_tiles_dev, n_tiles, 16, hist, scan_sums, s);
+    return launch_radix_sort(k0, v0, k1, v1, n_tiles_dev, n_tiles, 16, hist, scan_sums, s, nullptr);
 }
 
 __global__ void k_capacity_status(uint64_t *counters, uint64_t cap) {
