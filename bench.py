@@ -53,6 +53,8 @@ def parse_args():
                     help="skip the FP16-storage, batched and stress forms")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default blend shapes")
+    ap.add_argument("--shape", default="",
+                    help="fixed blend shape fwd_ppt,bwd_ppt,fwd_persistent,bwd_persistent (no autotune)")
     ap.add_argument("--cpu-tiles", type=int, default=48,
                     help="tiles of the frame the CPU oracle blends per sample")
     return ap.parse_args()
@@ -269,7 +271,10 @@ def run_ours(args, world, rank, local):
         return out
 
     tuned = None
-    if not args.no_autotune:
+    if args.shape:
+        f, b, fp, bp = (int(x) for x in args.shape.split(","))
+        sgsplat.sg_set_tuning(f, b, fp, bp)
+    elif not args.no_autotune:
         from paper_2509_07021_gb300 import autotune
         tuned = autotune.tune(ds, cams, d_img, use_cache=False)
     for _ in range(max(args.warmup, 1)):

@@ -164,6 +164,7 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 // packed look-back word: 2 status bits, 30 count bits
 constexpr uint32_t LB_AGG = 1u << 30, LB_INC = 2u << 30, LB_VAL = (1u << 30) - 1u;
 constexpr int LB_SPIN_LIMIT = 1 << 20;
+constexpr int LB_WINDOW = 16;
 
 struct SortAux {
     uint32_t hist[4][RS_RADIX];   // global digit counts per pass
@@ -183,12 +184,17 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
 }
 
+// Per-warp private shared histograms keep the shared-memory atomics of keys
+// with few distinct digits (the high tile bits) from serialising.
 __global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint32_t *__restrict__ keys,
                                                         const uint64_t *__restrict__ n_dev, uint64_t max_n,
                                                         int bits, SortAux *aux) {
-    __shared__ uint32_t h[4][RS_RADIX];
+    constexpr int NW = RS_THREADS / 32;
+    __shared__ uint32_t h[NW][4][RS_RADIX];
     const int passes = radix_passes_dev(bits);
-    for (int p = 0; p < 4; ++p) h[p][threadIdx.x] = 0u;
+    const int warp = threadIdx.x >> 5;
+    for (int w = 0; w < NW; ++w)
+        for (int p = 0; p < 4; ++p) h[w][p][threadIdx.x] = 0u;
     __syncthreads();
     const uint64_t n = min(*n_dev, max_n);
     const uint64_t stride = (uint64_t)gridDim.x * RS_THREADS;
@@ -196,12 +202,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint32_t *__restri
         const uint32_t k = keys[j];
         for (int p = 0; p < passes; ++p) {
             const int nb = min(8, bits - 8 * p);
-            atomicAdd(&h[p][(k >> (8 * p)) & ((1u << nb) - 1u)], 1u);
+            atomicAdd(&h[warp][p][(k >> (8 * p)) & ((1u << nb) - 1u)], 1u);
         }
     }
     __syncthreads();
     for (int p = 0; p < passes; ++p) {
-        const uint32_t c = h[p][threadIdx.x];
+        uint32_t c = 0u;
+        for (int w = 0; w < NW; ++w) c += h[w][p][threadIdx.x];
         if (c) atomicAdd(&aux->hist[p][threadIdx.x], c);
     }
 }
@@ -276,21 +283,35 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_pass(
     // publish this tile's count, then look back for the exclusive prefix
     uint32_t *my = flags + (uint64_t)t * RS_RADIX + d;
     st_relaxed(my, LB_AGG | run);
+    // Look back LB_WINDOW predecessors per step (independent loads in flight):
+    // add counts until the nearest tile that carries its inclusive prefix;
+    // a tile not yet published stops the step and is re-read.
     uint32_t excl = 0u;
     int spins = 0;
     for (int64_t p = (int64_t)t - 1; p >= 0;) {
-        const uint32_t fv = ld_relaxed(flags + (uint64_t)p * RS_RADIX + d);
-        if ((fv & ~LB_VAL) == 0u) {
+        uint32_t fv[LB_WINDOW];
+#pragma unroll
+        for (int i = 0; i < LB_WINDOW; ++i)
+            fv[i] = (p - i >= 0) ? ld_relaxed(flags + (uint64_t)(p - i) * RS_RADIX + d) : LB_INC;
+        int used = 0;
+        bool found = false, stalled = false;
+#pragma unroll
+        for (int i = 0; i < LB_WINDOW; ++i) {
+            if (found || stalled) continue;
+            if ((fv[i] & ~LB_VAL) == 0u) { stalled = true; continue; }
+            excl += fv[i] & LB_VAL;
+            ++used;
+            if (fv[i] & LB_INC) found = true;
+        }
+        if (found) break;
+        p -= used;
+        if (stalled) {
             if (++spins > LB_SPIN_LIMIT) {
                 atomicExch(&aux->status, (uint32_t)SG_ERR_TIMEOUT);
                 break;
             }
             __nanosleep(32);
-            continue;
         }
-        excl += fv & LB_VAL;
-        if (fv & LB_INC) break;
-        --p;
     }
     st_relaxed(my, LB_INC | ((excl + run) & LB_VAL));
     uint32_t tot;
@@ -472,24 +493,56 @@ cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64
 // ---------------------------------------------------------------------------
 // work order of the persistent blend: tiles by descending list length
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_tile_keys(const uint2 *__restrict__ ranges, uint32_t n_tiles,
-                                                   uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_tiles) return;
-    const uint2 r = ranges[t];
-    const uint32_t len = r.y - r.x;
-    keys[t] = 0xFFFFu - min(len >> 2, 0xFFFFu);   // 16-bit, longest first
-    vals[t] = t;
+// Buckets by floor(log2(list length)), longest bucket first; inside a bucket the
+// order is whatever the atomics give (it only steers scheduling).
+__device__ __forceinline__ uint32_t len_bucket(const uint2 r) {
+    return 31u - (uint32_t)__clz((r.y - r.x) | 1u);   // 0..31
+}
+
+__global__ void __launch_bounds__(256) k_tile_bucket_count(const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                                           uint32_t *__restrict__ counts) {
+    __shared__ uint32_t h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0u;
+    __syncthreads();
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
+        atomicAdd(&h[len_bucket(ranges[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) k_tile_bucket_scatter(const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                                             const uint32_t *__restrict__ counts,
+                                                             uint32_t *__restrict__ cursor,
+                                                             uint32_t *__restrict__ order) {
+    __shared__ uint32_t base[32];
+    if (threadIdx.x == 0) {
+        uint32_t run = 0u;
+        for (int b = 31; b >= 0; --b) {   // longest lists first
+            base[b] = run;
+            run += counts[b];
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+        const uint32_t b = len_bucket(ranges[t]);
+        order[base[b] + atomicAdd(&cursor[b], 1u)] = t;
+    }
 }
 
 cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, const uint64_t *n_tiles_dev,
                               uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
                               uint64_t *scan_sums, cudaStream_t s) {
+    (void)n_tiles_dev; (void)k0; (void)k1; (void)v1; (void)hist;
     if (n_tiles == 0) return cudaSuccess;
-    k_tile_keys<<<(unsigned)div_up(n_tiles, 256), 256, 0, s>>>(ranges, n_tiles, k0, v0);
-    count_launches(1);
-    // two stable 8-bit passes: the order ends in (k0, v0)
-    return launch_radix_sort(k0, v0, k1, v1, n_tiles_dev, n_tiles, 16, hist, scan_sums, s, nullptr);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(scan_sums), *cursor = counts + 32;
+    cudaError_t e = cudaMemsetAsync(counts, 0, 64 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const uint64_t want = div_up(n_tiles, 256);
+    const unsigned grid = (unsigned)(want < 608u ? want : 608u);
+    k_tile_bucket_count<<<grid, 256, 0, s>>>(ranges, n_tiles, counts);
+    k_tile_bucket_scatter<<<grid, 256, 0, s>>>(ranges, n_tiles, counts, cursor, v0);
+    count_launches(2);
+    return cudaGetLastError();
 }
 
 __global__ void k_capacity_status(uint64_t *counters, uint64_t cap) {
