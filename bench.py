@@ -451,6 +451,25 @@ def run_forms(args, scene, cams, d_img, flush, steps):
     f16["max_abs_img_diff_vs_f32_gpu"] = float(np.abs(base["f16_bf16s"] - base["f32"]).max())
     forms["_images"] = base   # consumed by the oracle error report, removed before printing
 
+    # ---- the 3DGS baseline colour: degree-3 SH (48 floats per Gaussian) on the same geometry ----
+    torch.cuda.empty_cache()
+    sh_scene = synth.with_sh3_colour(scene, np.random.default_rng(synth.SEED_BASE + 5))
+    ds = DeviceScene.from_host(sh_scene)
+    del sh_scene
+    grads = render.alloc_grads(ds)
+    static = sum(getattr(ds, k).numel() * getattr(ds, k).element_size()
+                 for k in ("means", "scales", "quats", "opac", "gmask", "sh"))
+    fwd_peak, both_peak = render_vram(ds, cams, d_img, grads, static)
+
+    def step_sh():
+        out = render.render_forward(ds, cams)
+        render.render_backward(ds, cams, out, d_img, grads)
+    ms = _timed(step_sh, steps, 2, flush)
+    forms["plain_sh3_f32"] = {"ms_per_view": ms, "mpixel_s": px / ms / 1e3, "static_mb": static / 2**20,
+                              "render_vram_mb": fwd_peak / 2**20, "fwd_bwd_vram_mb": both_peak / 2**20,
+                              "sg_static_reduction": 1.0 - f32["static_mb"] / (static / 2**20)}
+    del ds, grads
+
     # ---- batched: 8 uneven scenes x 4 cameras, one CUDA graph ----
     for name, gen in (("batched_cfg2", synth.config2), ("stress_cfg4", synth.config4)):
         torch.cuda.empty_cache()

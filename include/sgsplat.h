@@ -80,14 +80,23 @@ typedef enum sg_dtype { SG_F32 = 0, SG_F16 = 1, SG_BF16 = 2 } sg_dtype;
  *   lmask  [L]     per-lobe soft mask m_l                            binary32
  * Only SG_F32 (all families), SG_F16 (geom, lobe, sharp) and SG_BF16 (sharp)
  * are accepted.
+ *
+ * color_model: SG_COLOR_SG (0) -- the SG colour of Eq. 2 above -- or
+ * SG_COLOR_SH3 (1) -- degree-3 real spherical harmonics, the 48-float colour
+ * of 3DGS that the paper replaces (Table 3): c(v) = 0.5 + sum_k Y_k(v) sh_k,
+ * rgb = max(c, 0), with sh [3][16][N] binary32 (channel, coefficient,
+ * Gaussian) and c0 / lobe arrays unused (n_lobes = 0). Y_k follow the 3DGS
+ * basis ordering and signs.
  */
+#define SG_COLOR_SG 0
+#define SG_COLOR_SH3 1
 typedef struct sg_scene {
     int64_t n;
     int64_t n_lobes;
     int32_t dtype_geom;
     int32_t dtype_lobe;
     int32_t dtype_sharp;
-    int32_t reserved;
+    int32_t color_model;
     const void *means;
     const void *scales;
     const void *quats;
@@ -99,6 +108,7 @@ typedef struct sg_scene {
     const void *sharp;
     const void *amp;
     const float *lmask;
+    const float *sh;
 } sg_scene;
 
 /*
@@ -130,6 +140,7 @@ typedef struct sg_grads {
     float *sharp;
     float *amp;
     float *lmask;
+    float *sh;
 } sg_grads;
 
 /* Sizes reported by the query and by the forward call. */

@@ -7,6 +7,7 @@ input generator, which holds none of the method's arithmetic).
 
 What it follows:
   * SG lobe and colour model, Eq. 1-2 (Sec. 3.2): c(v) = c0 + sum_i a_i e^{s_i(mu_i.v - 1)}.
+    The degree-3 SH colour of the 3DGS baseline it replaces is in sg_sh_oracle.py.
     Soft-pruning masks (the BASELINE form of Sec. 3.3's soft pruning): m_l multiplies the
     whole lobe term, m_g multiplies opacity.
   * Primitive model and front-to-back compositing, Sec. 3.1: a Gaussian with centre mu,
@@ -33,6 +34,8 @@ from dataclasses import dataclass
 
 import numpy as np
 import torch
+
+from .sg_sh_oracle import sh3_color
 
 F32 = np.float32
 TILE = 16
@@ -243,12 +246,22 @@ def tile_lists(dec: Decisions, cam, tile_offset=0):
 PARAM_NAMES = ("means", "scales", "quats", "opac", "gmask", "c0", "axis", "sharp", "amp", "lmask")
 
 
+def param_names(scene):
+    """The differentiable inputs of a scene: the SG parameters, plus the SH
+    coefficients when the scene uses the SH3 colour model."""
+    return PARAM_NAMES + (("sh",) if getattr(scene, "sh", None) is not None else ())
+
+
 def leaves(scene, requires_grad=True):
-    """FP64 torch leaves, per-Gaussian rows: means [N,3] ... axis [L,3] ..."""
+    """FP64 torch leaves, per-Gaussian rows: means [N,3] ... axis [L,3] ...
+    sh [N,3,16] (from the stored [3][16][N])."""
     out = {}
-    for k in PARAM_NAMES:
+    for k in param_names(scene):
         a = np.asarray(getattr(scene, k), np.float64)
-        a = a.T.copy() if a.ndim == 2 else a.copy()
+        if a.ndim == 3:
+            a = np.ascontiguousarray(a.transpose(2, 0, 1))
+        else:
+            a = a.T.copy() if a.ndim == 2 else a.copy()
         out[k] = torch.from_numpy(a).requires_grad_(requires_grad)
     return out
 
@@ -303,6 +316,8 @@ def project_fp64(P, cam, vis_idx, lobe_off):
     cam_pos = -(Rc.T @ tc)
     d = mean - cam_pos
     v = d / torch.linalg.norm(d, dim=-1, keepdim=True)
+    if "sh" in P:   # the SH3 baseline colour instead of the SG lobes
+        return xy, conic, op, torch.clamp(sh3_color(P["sh"][idx], v), min=0.0)
     off = np.asarray(lobe_off, np.int64)
     counts = np.diff(off)[vis_idx]
     lobe_idx = _lobe_index_fast(off, vis_idx)
@@ -397,16 +412,20 @@ def render_backward(res: ViewResult, scene, cam, dimg):
                              _p(res.conic), _p(res.op), _p(res.rgb), _p(bg), _p(res.tile_sel),
                              _p(dimg64), _p(dxy), _p(dcon), _p(dop), _p(drgb))
     grads_out = [torch.from_numpy(a[vis_idx]) for a in (dxy, dcon, dop, drgb)]
-    leaves_ = [P[k] for k in PARAM_NAMES]
+    names = param_names(scene)
+    leaves_ = [P[k] for k in names]
     gl = torch.autograd.grad(list(outs), leaves_, grad_outputs=grads_out, allow_unused=True)
     out = {}
-    for k, g in zip(PARAM_NAMES, gl):
+    for k, g in zip(names, gl):
         ref = getattr(scene, k)
         if g is None:
             out[k] = np.zeros(ref.shape)
         else:
             g = g.numpy()
-            out[k] = g.T.copy() if g.ndim == 2 else g.copy()
+            if g.ndim == 3:
+                out[k] = np.ascontiguousarray(g.transpose(1, 2, 0))
+            else:
+                out[k] = g.T.copy() if g.ndim == 2 else g.copy()
     return out
 
 

@@ -149,11 +149,18 @@ int build_batch(const sg_scene *scenes, int n_scenes, const sg_camera *cams, con
             return fail(SG_ERR_INVALID_ARG, "scene %d: unsupported dtype combination (%d, %d, %d)", s,
                         sc.dtype_geom, sc.dtype_lobe, sc.dtype_sharp);
         if (s > 0 && (sc.dtype_geom != scenes[0].dtype_geom || sc.dtype_lobe != scenes[0].dtype_lobe ||
-                      sc.dtype_sharp != scenes[0].dtype_sharp))
-            return fail(SG_ERR_INVALID_ARG, "scene %d: all scenes of a call must share storage types", s);
+                      sc.dtype_sharp != scenes[0].dtype_sharp || sc.color_model != scenes[0].color_model))
+            return fail(SG_ERR_INVALID_ARG, "scene %d: all scenes of a call must share storage types and colour model",
+                        s);
+        const bool sh3 = sc.color_model == SG_COLOR_SH3;
+        if (sc.color_model != SG_COLOR_SG && !sh3)
+            return fail(SG_ERR_INVALID_ARG, "scene %d: unknown colour model %d", s, sc.color_model);
+        if (sh3 && (sc.n_lobes != 0 || sc.dtype_geom != SG_F32))
+            return fail(SG_ERR_INVALID_ARG, "scene %d: the SH3 colour model takes binary32 geometry and no lobes", s);
         if (check_ptrs && sc.n > 0) {
-            const void *req[] = {sc.means, sc.scales, sc.quats, sc.opac, sc.gmask, sc.c0, sc.lobe_off};
-            for (const void *p : req)
+            const void *req_sg[] = {sc.means, sc.scales, sc.quats, sc.opac, sc.gmask, sc.c0, sc.lobe_off};
+            const void *req_sh[] = {sc.means, sc.scales, sc.quats, sc.opac, sc.gmask, sc.sh, sc.sh};
+            for (const void *p : (sh3 ? req_sh : req_sg))
                 if (!p || !aligned(p, 16))
                     return fail(SG_ERR_INVALID_ARG, "scene %d: a Gaussian array is NULL or not 16-byte aligned", s);
         }
@@ -167,6 +174,8 @@ int build_batch(const sg_scene *scenes, int n_scenes, const sg_camera *cams, con
         d.means = sc.means; d.scales = sc.scales; d.quats = sc.quats; d.opac = sc.opac;
         d.gmask = sc.gmask; d.c0 = sc.c0; d.lobe_off = sc.lobe_off;
         d.axis = sc.axis; d.sharp = sc.sharp; d.amp = sc.amp; d.lmask = sc.lmask;
+        d.sh = sc.sh;
+        d.color_model = sc.color_model;
         d.n = sc.n; d.n_lobes = sc.n_lobes;
         d.dtype_geom = sc.dtype_geom; d.dtype_lobe = sc.dtype_lobe; d.dtype_sharp = sc.dtype_sharp;
         d.blk_off = (uint32_t)bwd_blk;

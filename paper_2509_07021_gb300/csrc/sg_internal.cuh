@@ -40,10 +40,11 @@ struct SceneDesc {
     const int32_t *lobe_off;
     const void *axis, *sharp, *amp;
     const float *lmask;
+    const float *sh;      // SH3 coefficients [3][16][N] (color_model SH3)
     float *importance;    // forward output: sum of alpha T per Gaussian (null: not wanted)
     sg_grads grads;
     int64_t n, n_lobes;
-    int32_t dtype_geom, dtype_lobe, dtype_sharp;
+    int32_t dtype_geom, dtype_lobe, dtype_sharp, color_model;
     uint32_t blk_off;     // first preprocess-backward block of the scene
 };
 

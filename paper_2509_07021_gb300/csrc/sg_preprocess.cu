@@ -224,9 +224,66 @@ cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStr
 }
 
 // ---------------------------------------------------------------------------
+// degree-3 real spherical harmonics (the 3DGS colour the paper replaces)
+// ---------------------------------------------------------------------------
+// Normalisation constants from their closed forms:
+//   1/(2 sqrt(pi)), sqrt(3/(4 pi)), sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4,
+//   sqrt(35/(2 pi))/4, sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4
+constexpr float SH_C0 = 0.28209479177387814f, SH_C1 = 0.4886025119029199f;
+constexpr float SH_C2A = 1.0925484305920792f, SH_C2B = 0.31539156525252005f, SH_C2C = 0.5462742152960396f;
+constexpr float SH_C3A = 0.5900435899266435f, SH_C3B = 2.890611442640554f, SH_C3C = 0.4570457994644658f,
+                SH_C3D = 0.3731763325901154f, SH_C3E = 1.445305721320277f;
+
+// Y_0..Y_15 at the unit direction (x, y, z), 3DGS ordering and signs.
+__device__ __forceinline__ void sh3_basis(float x, float y, float z, float Y[16]) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = SH_C0;
+    Y[1] = -SH_C1 * y;
+    Y[2] = SH_C1 * z;
+    Y[3] = -SH_C1 * x;
+    Y[4] = SH_C2A * x * y;
+    Y[5] = -SH_C2A * y * z;
+    Y[6] = SH_C2B * (2.f * zz - xx - yy);
+    Y[7] = -SH_C2A * x * z;
+    Y[8] = SH_C2C * (xx - yy);
+    Y[9] = -SH_C3A * y * (3.f * xx - yy);
+    Y[10] = SH_C3B * x * y * z;
+    Y[11] = -SH_C3C * y * (4.f * zz - xx - yy);
+    Y[12] = SH_C3D * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -SH_C3C * x * (4.f * zz - xx - yy);
+    Y[14] = SH_C3E * z * (xx - yy);
+    Y[15] = -SH_C3A * x * (xx - 3.f * yy);
+}
+
+// (gx, gy, gz) += sum_k w_k grad Y_k at (x, y, z), the basis polynomials
+// differentiated in x, y, z as independent variables.
+__device__ __forceinline__ void sh3_grad_acc(float x, float y, float z, const float w[16], float &gx,
+                                             float &gy, float &gz) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gy += -SH_C1 * w[1];
+    gz += SH_C1 * w[2];
+    gx += -SH_C1 * w[3];
+    gx += SH_C2A * y * w[4];            gy += SH_C2A * x * w[4];
+    gy += -SH_C2A * z * w[5];           gz += -SH_C2A * y * w[5];
+    gx += -2.f * SH_C2B * x * w[6];     gy += -2.f * SH_C2B * y * w[6];     gz += 4.f * SH_C2B * z * w[6];
+    gx += -SH_C2A * z * w[7];           gz += -SH_C2A * x * w[7];
+    gx += 2.f * SH_C2C * x * w[8];      gy += -2.f * SH_C2C * y * w[8];
+    gx += -6.f * SH_C3A * x * y * w[9]; gy += -SH_C3A * (3.f * xx - 3.f * yy) * w[9];
+    gx += SH_C3B * y * z * w[10];       gy += SH_C3B * x * z * w[10];       gz += SH_C3B * x * y * w[10];
+    gx += 2.f * SH_C3C * x * y * w[11]; gy += -SH_C3C * (4.f * zz - xx - 3.f * yy) * w[11];
+    gz += -8.f * SH_C3C * y * z * w[11];
+    gx += -6.f * SH_C3D * x * z * w[12]; gy += -6.f * SH_C3D * y * z * w[12];
+    gz += SH_C3D * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+    gx += -SH_C3C * (4.f * zz - 3.f * xx - yy) * w[13]; gy += 2.f * SH_C3C * x * y * w[13];
+    gz += -8.f * SH_C3C * x * z * w[13];
+    gx += 2.f * SH_C3E * x * z * w[14]; gy += -2.f * SH_C3E * y * z * w[14]; gz += SH_C3E * (xx - yy) * w[14];
+    gx += -SH_C3A * (3.f * xx - 3.f * yy) * w[15]; gy += 6.f * SH_C3A * x * y * w[15];
+}
+
+// ---------------------------------------------------------------------------
 // K1 preprocessSG
 // ---------------------------------------------------------------------------
-template <int DG, int DL, int DS>
+template <int DG, int DL, int DS, int CM>
 __global__ void __launch_bounds__(PRE_THREADS)
 k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__restrict__ tiles_touched,
              uint2 *__restrict__ rect, uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
@@ -256,20 +313,32 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
     const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
     dx *= inv; dy *= inv; dz *= inv;
     const int64_t n = sc.n, L = sc.n_lobes;
-    float cr = __ldg(sc.c0 + g), cg = __ldg(sc.c0 + n + g), cbl = __ldg(sc.c0 + 2 * n + g);
-    // CSR bounds clamped to [0, L] so a malformed lobe_off cannot read out of range
-    const int hi = min(__ldg(sc.lobe_off + g + 1), (int)L);
-    const int lo = max(0, min(__ldg(sc.lobe_off + g), hi));
-    for (int k = lo; k < hi; ++k) {
-        const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
-                    az = ldp<DL>(sc.axis, 2 * L + k);
-        const float ia = 1.0f / sqrtf(ax * ax + ay * ay + az * az);
-        const float dot = (ax * dx + ay * dy + az * dz) * ia;
-        const float sh = ldp<DS>(sc.sharp, k);
-        const float wgt = __ldg(sc.lmask + k) * expf(sh * (dot - 1.0f));
-        cr += wgt * ldp<DL>(sc.amp, k);
-        cg += wgt * ldp<DL>(sc.amp, L + k);
-        cbl += wgt * ldp<DL>(sc.amp, 2 * L + k);
+    float cr, cg, cbl;
+    if (CM == SG_COLOR_SH3) {
+        float Y[16];
+        sh3_basis(dx, dy, dz, Y);
+        float c[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) c[ch] = fmaf(Y[k], __ldg(sc.sh + (int64_t)(ch * 16 + k) * n + g), c[ch]);
+        cr = c[0]; cg = c[1]; cbl = c[2];
+    } else {
+        cr = __ldg(sc.c0 + g); cg = __ldg(sc.c0 + n + g); cbl = __ldg(sc.c0 + 2 * n + g);
+        // CSR bounds clamped to [0, L] so a malformed lobe_off cannot read out of range
+        const int hi = min(__ldg(sc.lobe_off + g + 1), (int)L);
+        const int lo = max(0, min(__ldg(sc.lobe_off + g), hi));
+        for (int k = lo; k < hi; ++k) {
+            const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
+                        az = ldp<DL>(sc.axis, 2 * L + k);
+            const float ia = 1.0f / sqrtf(ax * ax + ay * ay + az * az);
+            const float dot = (ax * dx + ay * dy + az * dz) * ia;
+            const float sh = ldp<DS>(sc.sharp, k);
+            const float wgt = __ldg(sc.lmask + k) * expf(sh * (dot - 1.0f));
+            cr += wgt * ldp<DL>(sc.amp, k);
+            cg += wgt * ldp<DL>(sc.amp, L + k);
+            cbl += wgt * ldp<DL>(sc.amp, 2 * L + k);
+        }
     }
     Rec r;
     r.a = make_float4(G.x, G.y, G.conA, G.conB);
@@ -282,11 +351,11 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
     dval[e] = (uint32_t)e;
 }
 
-template <int DG, int DL, int DS>
+template <int DG, int DL, int DS, int CM = SG_COLOR_SG>
 static cudaError_t launch_pre_t(const Batch &hb, const Batch *db, Rec *rec, uint32_t *tt, uint2 *rect,
                                 uint32_t *dkey, uint32_t *dval, cudaStream_t s) {
     if (hb.pre_blocks == 0) return cudaSuccess;
-    k_preprocess<DG, DL, DS><<<hb.pre_blocks, PRE_THREADS, 0, s>>>(db, rec, tt, rect, dkey, dval);
+    k_preprocess<DG, DL, DS, CM><<<hb.pre_blocks, PRE_THREADS, 0, s>>>(db, rec, tt, rect, dkey, dval);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -296,6 +365,10 @@ cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32
     // all scenes of one call share storage types (checked by the API layer)
     const SceneDesc &sc = hb.scene[0];
     const int key = sc.dtype_geom * 9 + sc.dtype_lobe * 3 + sc.dtype_sharp;
+    if (sc.color_model == SG_COLOR_SH3) {
+        if (key != SG_F32 * 9 + SG_F32 * 3 + SG_F32) return cudaErrorInvalidValue;
+        return launch_pre_t<SG_F32, SG_F32, SG_F32, SG_COLOR_SH3>(hb, db, rec, tiles_touched, rect, dkey, dval, s);
+    }
     switch (key) {
         case SG_F32 * 9 + SG_F32 * 3 + SG_F32:
             return launch_pre_t<SG_F32, SG_F32, SG_F32>(hb, db, rec, tiles_touched, rect, dkey, dval, s);
@@ -312,7 +385,7 @@ cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32
 // K8 preprocess backward
 // ---------------------------------------------------------------------------
 // dg layout: planar [9][M]: dx, dy, dA, dB, dC, do', dr, dg, db per entry.
-template <int DG, int DL, int DS>
+template <int DG, int DL, int DS, int CM>
 __global__ void __launch_bounds__(PRE_THREADS)
 k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tiles_touched,
                  const float *__restrict__ dg, uint64_t M) {
@@ -326,9 +399,11 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
     float px, py, pz, s0, s1, s2, q0, q1, q2, q3, o;
     load_geo<DG>(sc, g, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o);
     const float gm = __ldg(sc.gmask + g);
-    const float c00 = __ldg(sc.c0 + g), c01 = __ldg(sc.c0 + n + g), c02 = __ldg(sc.c0 + 2 * n + g);
-    const int hi = min(__ldg(sc.lobe_off + g + 1), (int)L);
-    const int lo = max(0, min(__ldg(sc.lobe_off + g), hi));
+    const bool sh_mode = CM == SG_COLOR_SH3;
+    const float c00 = sh_mode ? 0.f : __ldg(sc.c0 + g), c01 = sh_mode ? 0.f : __ldg(sc.c0 + n + g),
+                c02 = sh_mode ? 0.f : __ldg(sc.c0 + 2 * n + g);
+    const int hi = sh_mode ? 0 : min(__ldg(sc.lobe_off + g + 1), (int)L);
+    const int lo = sh_mode ? 0 : max(0, min(__ldg(sc.lobe_off + g), hi));
 
     float d_mean[3] = {0.f, 0.f, 0.f}, d_scale[3] = {0.f, 0.f, 0.f}, d_q[4] = {0.f, 0.f, 0.f, 0.f};
     float d_opac = 0.f, d_gmask = 0.f, d_c0[3] = {0.f, 0.f, 0.f};
@@ -355,6 +430,38 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
         const float dn = sqrtf(vx * vx + vy * vy + vz * vz);
         const float idn = 1.0f / dn;
         vx *= idn; vy *= idn; vz *= idn;
+        float dvx = 0.f, dvy = 0.f, dvz = 0.f;
+        if (sh_mode) {
+            // c = 0.5 + sum_k Y_k(v) sh_k per channel
+            float Y[16];
+            sh3_basis(vx, vy, vz, Y);
+            float gc[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float c = 0.5f;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) c = fmaf(Y[k], __ldg(sc.sh + (int64_t)(ch * 16 + k) * n + g), c);
+                gc[ch] = c >= 0.f ? grgb[ch] : 0.f;
+            }
+            float w[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                w[k] = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) w[k] = fmaf(gc[ch], __ldg(sc.sh + (int64_t)(ch * 16 + k) * n + g), w[k]);
+            }
+            sh3_grad_acc(vx, vy, vz, w, dvx, dvy, dvz);
+            float *gsh = sc.grads.sh;
+            if (gsh) {
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        float *dst = gsh + (int64_t)(ch * 16 + k) * n + g;
+                        *dst = first ? Y[k] * gc[ch] : *dst + Y[k] * gc[ch];
+                    }
+            }
+        }
         float col[3] = {c00, c01, c02};
         for (int k = lo; k < hi; ++k) {
             const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
@@ -370,9 +477,8 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             gc[ch] = col[ch] >= 0.f ? grgb[ch] : 0.f;   // max(c, 0)
-            d_c0[ch] += gc[ch];
+            if (!sh_mode) d_c0[ch] += gc[ch];
         }
-        float dvx = 0.f, dvy = 0.f, dvz = 0.f;
         for (int k = lo; k < hi; ++k) {
             const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
                         az = ldp<DL>(sc.axis, 2 * L + k);
@@ -509,6 +615,9 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
     }
 
     const sg_grads &gr = sc.grads;
+    if (first && sh_mode && gr.sh) {   // not visible in any view: SH gradients are zero
+        for (int k = 0; k < 48; ++k) gr.sh[(int64_t)k * n + g] = 0.f;
+    }
     if (first) {   // not visible in any view: lobe gradients are zero
         for (int k = lo; k < hi; ++k) {
             if (gr.amp) { gr.amp[k] = 0.f; gr.amp[L + k] = 0.f; gr.amp[2 * L + k] = 0.f; }
@@ -527,11 +636,11 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
     if (gr.c0) { gr.c0[g] = d_c0[0]; gr.c0[n + g] = d_c0[1]; gr.c0[2 * n + g] = d_c0[2]; }
 }
 
-template <int DG, int DL, int DS>
+template <int DG, int DL, int DS, int CM = SG_COLOR_SG>
 static cudaError_t launch_bwd_t(const Batch &hb, const Batch *db, const uint32_t *tt, const float *dg,
                                 uint64_t M, cudaStream_t s) {
     if (hb.bwd_blocks == 0) return cudaSuccess;
-    k_preprocess_bwd<DG, DL, DS><<<hb.bwd_blocks, PRE_THREADS, 0, s>>>(db, tt, dg, M);
+    k_preprocess_bwd<DG, DL, DS, CM><<<hb.bwd_blocks, PRE_THREADS, 0, s>>>(db, tt, dg, M);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -540,6 +649,10 @@ cudaError_t launch_preprocess_backward(const Batch &hb, const Batch *db, const u
                                        const float *dg, uint64_t M, cudaStream_t s) {
     const SceneDesc &sc = hb.scene[0];
     const int key = sc.dtype_geom * 9 + sc.dtype_lobe * 3 + sc.dtype_sharp;
+    if (sc.color_model == SG_COLOR_SH3) {
+        if (key != SG_F32 * 9 + SG_F32 * 3 + SG_F32) return cudaErrorInvalidValue;
+        return launch_bwd_t<SG_F32, SG_F32, SG_F32, SG_COLOR_SH3>(hb, db, tiles_touched, dg, M, s);
+    }
     switch (key) {
         case SG_F32 * 9 + SG_F32 * 3 + SG_F32:
             return launch_bwd_t<SG_F32, SG_F32, SG_F32>(hb, db, tiles_touched, dg, M, s);

@@ -74,7 +74,7 @@ def render_forward(scene: DeviceScene, cams, stream=None, importance=None) -> Fo
 
 def alloc_grads(scene: DeviceScene):
     return {k: torch.empty(getattr(scene, k).shape, dtype=torch.float32, device=scene.means.device)
-            for k in DeviceScene.FLOAT_FIELDS}
+            for k in scene.grad_fields()}
 
 
 def render_backward(scene: DeviceScene, cams, fwd: ForwardOut, d_img, grads=None, stream=None):

@@ -17,6 +17,7 @@ from . import build as _build
 
 SG_OK, SG_ERR_INVALID_ARG, SG_ERR_WORKSPACE, SG_ERR_CAPACITY, SG_ERR_TIMEOUT, SG_ERR_CUDA = range(6)
 SG_F32, SG_F16, SG_BF16 = 0, 1, 2
+SG_COLOR_SG, SG_COLOR_SH3 = 0, 1
 SG_MAX_VIEWS = 128
 SG_MAX_SCENES = 32
 
@@ -40,10 +41,10 @@ _P = ctypes.c_void_p
 class sg_scene(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_lobes", ctypes.c_int64),
                 ("dtype_geom", ctypes.c_int32), ("dtype_lobe", ctypes.c_int32),
-                ("dtype_sharp", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dtype_sharp", ctypes.c_int32), ("color_model", ctypes.c_int32),
                 ("means", _P), ("scales", _P), ("quats", _P), ("opac", _P), ("gmask", _P),
                 ("c0", _P), ("lobe_off", _P), ("axis", _P), ("sharp", _P), ("amp", _P),
-                ("lmask", _P)]
+                ("lmask", _P), ("sh", _P)]
 
 
 class sg_camera(ctypes.Structure):
@@ -55,7 +56,7 @@ class sg_camera(ctypes.Structure):
 
 class sg_grads(ctypes.Structure):
     _fields_ = [(k, _P) for k in ("means", "scales", "quats", "opac", "gmask", "c0", "axis",
-                                  "sharp", "amp", "lmask")]
+                                  "sharp", "amp", "lmask", "sh")]
 
 
 class sg_sizes(ctypes.Structure):
@@ -216,6 +217,14 @@ class DeviceScene:
     dtype_geom: int = SG_F32
     dtype_lobe: int = SG_F32
     dtype_sharp: int = SG_F32
+    sh: torch.Tensor | None = None   # [3][16][N] SH3 coefficients: the SH colour model
+
+    @property
+    def color_model(self):
+        return SG_COLOR_SH3 if self.sh is not None else SG_COLOR_SG
+
+    def grad_fields(self):
+        return self.FLOAT_FIELDS + (("sh",) if self.sh is not None else ())
 
     FLOAT_FIELDS = ("means", "scales", "quats", "opac", "gmask", "c0", "axis", "sharp", "amp",
                     "lmask")
@@ -241,6 +250,8 @@ class DeviceScene:
             a = torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32))
             kw[k] = a.to(device=device, dtype=_TORCH_DT[fam.get(k, SG_F32)]).contiguous()
         kw["lobe_off"] = torch.from_numpy(np.ascontiguousarray(scene.lobe_off, np.int32)).to(device)
+        if getattr(scene, "sh", None) is not None:
+            kw["sh"] = torch.from_numpy(np.ascontiguousarray(scene.sh, np.float32)).to(device)
         return cls(dtype_geom=dg, dtype_lobe=dl, dtype_sharp=ds, **kw)
 
     def struct(self):
@@ -248,9 +259,11 @@ class DeviceScene:
         s.n = self.n
         s.n_lobes = self.n_lobes
         s.dtype_geom, s.dtype_lobe, s.dtype_sharp = self.dtype_geom, self.dtype_lobe, self.dtype_sharp
+        s.color_model = self.color_model
         for k in self.FLOAT_FIELDS + ("lobe_off",):
             t = getattr(self, k)
             setattr(s, k, t.data_ptr() if t.numel() else None)
+        s.sh = self.sh.data_ptr() if self.sh is not None and self.sh.numel() else None
         return s
 
 

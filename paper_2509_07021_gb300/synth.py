@@ -74,6 +74,7 @@ class Scene:
     sharp: np.ndarray
     amp: np.ndarray
     lmask: np.ndarray
+    sh: np.ndarray | None = None   # [3][16][N] SH3 coefficients (SH colour model only)
 
     FLOAT_FIELDS = ("means", "scales", "quats", "opac", "gmask", "c0",
                     "axis", "sharp", "amp", "lmask")
@@ -87,7 +88,10 @@ class Scene:
         return int(self.sharp.shape[0])
 
     def arrays(self) -> dict:
-        return {k: getattr(self, k) for k in self.FLOAT_FIELDS + ("lobe_off",)}
+        out = {k: getattr(self, k) for k in self.FLOAT_FIELDS + ("lobe_off",)}
+        if self.sh is not None:
+            out["sh"] = self.sh
+        return out
 
     def copy(self) -> "Scene":
         return Scene(**{k: np.array(v, copy=True) for k, v in self.arrays().items()})
@@ -315,4 +319,23 @@ def round_to_storage(scene: Scene, storage: str) -> Scene:
     for k, dt in STORAGE_FAMILIES[storage].items():
         t = torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32))
         setattr(out, k, t.to(getattr(torch, dt)).float().numpy())
+    return out
+
+
+def with_sh3_colour(scene: Scene, rng, dc_std=1.0, band_std=0.2) -> Scene:
+    """The same geometry with a degree-3 SH colour instead of SG lobes:
+    coefficients [3][16][N] (DC ~ N(0, dc_std), higher bands ~ N(0, band_std)),
+    no lobes, c0 unused (zeros)."""
+    n = scene.n
+    sh = rng.normal(0.0, band_std, (3, 16, n))
+    sh[:, 0, :] = rng.normal(0.0, dc_std, (3, n))
+    f = np.float32
+    out = scene.copy()
+    out.sh = sh.astype(f)
+    out.c0 = np.zeros((3, n), f)
+    out.lobe_off = np.zeros(n + 1, np.int32)
+    out.axis = np.zeros((3, 0), f)
+    out.sharp = np.zeros(0, f)
+    out.amp = np.zeros((3, 0), f)
+    out.lmask = np.zeros(0, f)
     return out
