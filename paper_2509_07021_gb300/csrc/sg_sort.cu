@@ -493,35 +493,38 @@ cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64
 // ---------------------------------------------------------------------------
 // work order of the persistent blend: tiles by descending list length
 // ---------------------------------------------------------------------------
-// Buckets by floor(log2(list length)), longest bucket first; inside a bucket the
+// Buckets by list length on a log scale with 8 buckets per octave (exponent and
+// the 3 bits below the leading one), longest bucket first; inside a bucket the
 // order is whatever the atomics give (it only steers scheduling).
+constexpr int TB_BUCKETS = 256;
 __device__ __forceinline__ uint32_t len_bucket(const uint2 r) {
-    return 31u - (uint32_t)__clz((r.y - r.x) | 1u);   // 0..31
+    const uint32_t len = (r.y - r.x) | 1u;
+    const uint32_t e = 31u - (uint32_t)__clz(len);              // 0..31
+    const uint32_t m = e >= 3u ? (len >> (e - 3u)) & 7u : (len << (3u - e)) & 7u;
+    return e * 8u + m;                                           // 0..255
 }
 
 __global__ void __launch_bounds__(256) k_tile_bucket_count(const uint2 *__restrict__ ranges, uint32_t n_tiles,
                                                            uint32_t *__restrict__ counts) {
-    __shared__ uint32_t h[32];
-    if (threadIdx.x < 32) h[threadIdx.x] = 0u;
+    __shared__ uint32_t h[TB_BUCKETS];
+    h[threadIdx.x] = 0u;
     __syncthreads();
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
         atomicAdd(&h[len_bucket(ranges[t])], 1u);
     __syncthreads();
-    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+    if (h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
 }
 
 __global__ void __launch_bounds__(256) k_tile_bucket_scatter(const uint2 *__restrict__ ranges, uint32_t n_tiles,
                                                              const uint32_t *__restrict__ counts,
                                                              uint32_t *__restrict__ cursor,
                                                              uint32_t *__restrict__ order) {
-    __shared__ uint32_t base[32];
-    if (threadIdx.x == 0) {
-        uint32_t run = 0u;
-        for (int b = 31; b >= 0; --b) {   // longest lists first
-            base[b] = run;
-            run += counts[b];
-        }
-    }
+    __shared__ uint32_t base[TB_BUCKETS];
+    __shared__ uint32_t shs[33];
+    // longest lists first: exclusive scan over the buckets in reverse
+    const uint32_t c = counts[TB_BUCKETS - 1 - threadIdx.x];
+    uint32_t tot;
+    base[TB_BUCKETS - 1 - threadIdx.x] = block_exclusive<uint32_t>(c, tot, shs);
     __syncthreads();
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
         const uint32_t b = len_bucket(ranges[t]);
@@ -534,8 +537,8 @@ cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, const uint6
                               uint64_t *scan_sums, cudaStream_t s) {
     (void)n_tiles_dev; (void)k0; (void)k1; (void)v1; (void)hist;
     if (n_tiles == 0) return cudaSuccess;
-    uint32_t *counts = reinterpret_cast<uint32_t *>(scan_sums), *cursor = counts + 32;
-    cudaError_t e = cudaMemsetAsync(counts, 0, 64 * sizeof(uint32_t), s);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(scan_sums), *cursor = counts + TB_BUCKETS;
+    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * TB_BUCKETS * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const uint64_t want = div_up(n_tiles, 256);
     const unsigned grid = (unsigned)(want < 608u ? want : 608u);
