@@ -50,13 +50,28 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-struct Staged {
-    float4 q[BATCH];
-    float4 r[BATCH];
-    float s[BATCH];
-    uint32_t id[BATCH];
-    uint32_t mask[BATCH];   // sub-blocks of the tile the Gaussian can reach
+// Gaussians staged per batch in the backward (smaller batches leave room for
+// more resident blocks of the one-warp, 8-pixels-per-thread shape).
+#ifndef SG_BWD_BATCH
+#define SG_BWD_BATCH 128
+#endif
+constexpr int BWD_BATCH = SG_BWD_BATCH;
+static_assert(BWD_BATCH % 32 == 0 && BWD_BATCH <= BATCH, "backward batch");
+// Minimum resident blocks requested for the 8-pixels-per-thread backward.
+#ifndef SG_BWD8_MIN_BLOCKS
+#define SG_BWD8_MIN_BLOCKS 20
+#endif
+
+template <int NB>
+struct StagedN {
+    float4 q[NB];
+    float4 r[NB];
+    float s[NB];
+    uint32_t id[NB];
+    uint32_t mask[NB];   // sub-blocks of the tile the Gaussian can reach
 };
+using Staged = StagedN<BATCH>;
+using StagedB = StagedN<BWD_BATCH>;
 
 // A 16x16 tile is 8 sub-blocks of 8x4 pixels: sub-block s covers columns
 // 8 (s & 1) .. +7 and rows 4 (s >> 1) .. +3 of the tile. Warp w's pixel slot j
@@ -94,8 +109,8 @@ __device__ __forceinline__ uint32_t reach_mask(const Rec &rc, float x0, float y0
     return m;
 }
 
-template <bool CULL>
-__device__ __forceinline__ void stage(Staged &sm, int slot, const Rec &rc, uint32_t e, float x0, float y0) {
+template <bool CULL, int NB>
+__device__ __forceinline__ void stage(StagedN<NB> &sm, int slot, const Rec &rc, uint32_t e, float x0, float y0) {
     sm.q[slot] = make_float4(rc.a.x, rc.a.y, -0.5f * LOG2E * rc.a.z, -LOG2E * rc.a.w);
     sm.r[slot] = make_float4(-0.5f * LOG2E * rc.b.x, rc.b.y, rc.b.z, rc.b.w);
     sm.s[slot] = rc.c.x;
@@ -103,7 +118,8 @@ __device__ __forceinline__ void stage(Staged &sm, int slot, const Rec &rc, uint3
     sm.mask[slot] = CULL ? reach_mask(rc, x0, y0) : 0xFFu;
 }
 
-// Pixel (column, row inside the tile) of slot j of this thread.
+// Pixel (column, row inside the tile) of slot j of this thread. For P >= 2 the
+// slots 2i and 2i + 1 lie in the same pixel row (sub-blocks 2s and 2s + 1).
 template <int P>
 __device__ __forceinline__ void slot_pixel(int j, int &cx, int &cy) {
     const int sub = (int)(threadIdx.x >> 5) * P + j;
@@ -112,19 +128,35 @@ __device__ __forceinline__ void slot_pixel(int j, int &cx, int &cy) {
     cy = SUB_H * (sub >> 1) + (lane / SUB_W);
 }
 
+// Slots that share one pixel row: 2 for P >= 2, else 1.
+template <int P>
+constexpr int row_slots() { return P >= 2 ? 2 : 1; }
+
+// The terms of the quadratic form that depend on the pixel row only:
+//   dy = y_pix - y, u = qc dy, b = qb dy, c = u dy
+struct RowEval {
+    float dy, u, b, c;
+};
+
 struct PairEval {
-    float dx, dy, t, u, p2, G, ag, alpha;
+    float dx, t, p2, G, ag, alpha;
 };
 
 // Every kernel that decides a skip evaluates a pair with this exact sequence of
-// explicitly rounded operations, so the forward and the backward agree.
-__device__ __forceinline__ void eval_pair(float fpx, float fpy, const float4 &q, const float4 &r,
-                                          PairEval &p) {
+// explicitly rounded operations, so the forward and the backward agree:
+//   t = qa dx + qb dy,  power log2(e) = t dx + qc dy^2.
+__device__ __forceinline__ void eval_row(float fpy, const float4 &q, const float4 &r, RowEval &w) {
+    w.dy = __fsub_rn(fpy, q.y);
+    w.u = __fmul_rn(r.x, w.dy);
+    w.b = __fmul_rn(q.w, w.dy);
+    w.c = __fmul_rn(w.u, w.dy);
+}
+
+__device__ __forceinline__ void eval_pixel(float fpx, const float4 &q, const float4 &r, const RowEval &w,
+                                           PairEval &p) {
     p.dx = __fsub_rn(fpx, q.x);
-    p.dy = __fsub_rn(fpy, q.y);
-    p.t = __fmaf_rn(q.w, p.dy, __fmul_rn(q.z, p.dx));      // qa dx + qb dy
-    p.u = __fmul_rn(r.x, p.dy);                             // qc dy
-    p.p2 = __fmaf_rn(p.u, p.dy, __fmul_rn(p.t, p.dx));      // power * log2(e)
+    p.t = __fmaf_rn(q.z, p.dx, w.b);
+    p.p2 = __fmaf_rn(p.t, p.dx, w.c);
     p.G = ex2_approx(p.p2);
     p.ag = __fmul_rn(r.y, p.G);
     p.alpha = fminf(ALPHA_MAX, p.ag);
@@ -208,23 +240,31 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
             const float4 q = sm.q[k], r = sm.r[k];
             const float bl = sm.s[k];
             float wsum = 0.f;
+            constexpr int RS = row_slots<P>();
 #pragma unroll
-            for (int j = 0; j < P; ++j) {
-                if (!((msk >> j) & 1u)) continue;            // warp-uniform
-                if (done[j]) continue;
-                PairEval p;
-                eval_pair(fpx[j], fpy[j], q, r, p);
-                if (COUNT) ++ne;
-                if (p.p2 > 0.f || p.alpha < ALPHA_MIN) continue;
-                const float tt = __fmul_rn(T[j], __fsub_rn(1.f, p.alpha));
-                if (tt < T_STOP) { done[j] = true; continue; }
-                const float w = p.alpha * T[j];
-                c0[j] = fmaf(r.z, w, c0[j]);
-                c1[j] = fmaf(r.w, w, c1[j]);
-                c2[j] = fmaf(bl, w, c2[j]);
-                T[j] = tt;
-                lastc[j] = base + k + 1;
-                if (IMP) wsum += w;
+            for (int j0 = 0; j0 < P; j0 += RS) {
+                if (!((msk >> j0) & ((1u << RS) - 1u))) continue;   // warp-uniform
+                RowEval row;
+                eval_row(fpy[j0], q, r, row);
+#pragma unroll
+                for (int h = 0; h < RS; ++h) {
+                    const int j = j0 + h;
+                    if (!((msk >> j) & 1u)) continue;        // warp-uniform
+                    if (done[j]) continue;
+                    PairEval p;
+                    eval_pixel(fpx[j], q, r, row, p);
+                    if (COUNT) ++ne;
+                    if (p.p2 > 0.f || p.alpha < ALPHA_MIN) continue;
+                    const float tt = __fmul_rn(T[j], __fsub_rn(1.f, p.alpha));
+                    if (tt < T_STOP) { done[j] = true; continue; }
+                    const float w = p.alpha * T[j];
+                    c0[j] = fmaf(r.z, w, c0[j]);
+                    c1[j] = fmaf(r.w, w, c1[j]);
+                    c2[j] = fmaf(bl, w, c2[j]);
+                    T[j] = tt;
+                    lastc[j] = base + k + 1;
+                    if (IMP) wsum += w;
+                }
             }
             if (IMP && __any_sync(0xffffffffu, wsum != 0.f)) {
 #pragma unroll
@@ -368,7 +408,7 @@ __device__ __forceinline__ void warp_sum9_atomic(const float v[9], float *dg, ui
 // atomics. Accumulated per pair (in dg order):
 //   0,1: dL/dx, dL/dy   2..4: dL/dA, dL/dB, dL/dC   5: dL/do'   6..8: dL/drgb
 template <int P, bool COUNT>
-__device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, Staged &sm, int *smax,
+__device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, StagedB &sm, int *smax,
                                                const uint2 *__restrict__ ranges,
                                                const uint32_t *__restrict__ pval,
                                                const Rec *__restrict__ rec,
@@ -384,7 +424,8 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
     const uint64_t HW = (uint64_t)vw->W * (uint64_t)vw->H;
     const float *gi = d_img + 3 * vw->pix_off;
 
-    float fpx[P], fpy[P], T[P], Tfbg[P], g0[P], g1[P], g2[P], Sg[P];
+    // Sg starts at T_final (bg . g), the background's share of every dL/dalpha
+    float fpx[P], fpy[P], T[P], g0[P], g1[P], g2[P], Sg[P];
     int mylast[P];
     int tmax = 0;
 #pragma unroll
@@ -394,7 +435,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
         const int px = tx * TILE + cx, py = ty * TILE + cy;
         fpx[j] = (float)px;
         fpy[j] = (float)py;
-        T[j] = 1.f; Tfbg[j] = 0.f; g0[j] = g1[j] = g2[j] = 0.f; Sg[j] = 0.f; mylast[j] = 0;
+        T[j] = 1.f; g0[j] = g1[j] = g2[j] = 0.f; Sg[j] = 0.f; mylast[j] = 0;
         if (px < vw->W && py < vw->H) {
             const uint64_t pix = (uint64_t)py * (uint64_t)vw->W + (uint64_t)px;
             mylast[j] = last[vw->pix_off + pix];
@@ -403,7 +444,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
             g0[j] = gi[pix];
             g1[j] = gi[HW + pix];
             g2[j] = gi[2 * HW + pix];
-            Tfbg[j] = tf * (g0[j] * vw->bg[0] + g1[j] * vw->bg[1] + g2[j] * vw->bg[2]);
+            Sg[j] = tf * (g0[j] * vw->bg[0] + g1[j] * vw->bg[1] + g2[j] * vw->bg[2]);
         }
         tmax = max(tmax, mylast[j]);
     }
@@ -416,8 +457,8 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
     const int sub0 = (int)(threadIdx.x >> 5) * P;
     const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
 
-    for (int end = maxlast; end > 0; end -= BATCH) {
-        const int start = max(0, end - BATCH);
+    for (int end = maxlast; end > 0; end -= BWD_BATCH) {
+        const int start = max(0, end - BWD_BATCH);
         const int cnt = end - start;
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += NT) {
@@ -437,37 +478,44 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
 #pragma unroll
             for (int i = 0; i < 9; ++i) v[i] = 0.f;
             bool any = false;
+            constexpr int RS = row_slots<P>();
 #pragma unroll
-            for (int j = 0; j < P; ++j) {
-                if (!((msk >> j) & 1u)) continue;            // warp-uniform
-                if (pos >= mylast[j]) continue;
-                PairEval p;
-                eval_pair(fpx[j], fpy[j], q, r, p);
-                if (COUNT) ++ne;
-                if (p.p2 > 0.f || p.alpha < ALPHA_MIN) continue;
-                any = true;
-                const float oma = __fsub_rn(1.f, p.alpha);
-                const float ro = rcp_approx(oma);
-                const float Ti = T[j] * ro;
-                const float w = p.alpha * Ti;
-                const float cg = fmaf(r.z, g0[j], fmaf(r.w, g1[j], bl * g2[j]));
-                const float dal = Ti * cg - (Sg[j] + Tfbg[j]) * ro;
-                Sg[j] = fmaf(cg, w, Sg[j]);
-                T[j] = Ti;
-                v[6] = fmaf(w, g0[j], v[6]);
-                v[7] = fmaf(w, g1[j], v[7]);
-                v[8] = fmaf(w, g2[j], v[8]);
-                if (!(p.ag > ALPHA_MAX)) {
-                    const float dG = dal * p.G;          // dL/do' share of this pixel
-                    const float h = dG * r.y;            // dL/dpower
+            for (int j0 = 0; j0 < P; j0 += RS) {
+                if (!((msk >> j0) & ((1u << RS) - 1u))) continue;   // warp-uniform
+                RowEval row;
+                eval_row(fpy[j0], q, r, row);
+#pragma unroll
+                for (int hh = 0; hh < RS; ++hh) {
+                    const int j = j0 + hh;
+                    if (!((msk >> j) & 1u)) continue;        // warp-uniform
+                    if (pos >= mylast[j]) continue;
+                    PairEval p;
+                    eval_pixel(fpx[j], q, r, row, p);
+                    if (COUNT) ++ne;
+                    if (p.p2 > 0.f || p.alpha < ALPHA_MIN) continue;
+                    any = true;
+                    const float oma = __fsub_rn(1.f, p.alpha);
+                    const float ro = rcp_approx(oma);
+                    const float Ti = T[j] * ro;
+                    const float w = p.alpha * Ti;
+                    const float cg = fmaf(r.z, g0[j], fmaf(r.w, g1[j], bl * g2[j]));
+                    const float dal = Ti * cg - Sg[j] * ro;
+                    Sg[j] = fmaf(cg, w, Sg[j]);
+                    T[j] = Ti;
+                    v[6] = fmaf(w, g0[j], v[6]);
+                    v[7] = fmaf(w, g1[j], v[7]);
+                    v[8] = fmaf(w, g2[j], v[8]);
+                    // dL/do' share of this pixel; none where the 0.99 clamp is active
+                    const float dG = p.ag > ALPHA_MAX ? 0.f : dal * p.G;
+                    const float h = dG * r.y;                // dL/dpower
                     v[5] += dG;
                     // with L = log2 e: qa dx + qb dy = t, so A dx + B dy = -(t + qa dx) / L
                     v[0] = fmaf(h, fmaf(q.z, p.dx, p.t), v[0]);
-                    v[1] = fmaf(h, fmaf(2.f, p.u, q.w * p.dx), v[1]);
+                    v[1] = fmaf(h, fmaf(2.f, row.u, q.w * p.dx), v[1]);
                     const float hx = h * p.dx;
                     v[2] = fmaf(hx, p.dx, v[2]);
-                    v[3] = fmaf(hx, p.dy, v[3]);
-                    v[4] = fmaf(h * p.dy, p.dy, v[4]);
+                    v[3] = fmaf(hx, row.dy, v[3]);
+                    v[4] = fmaf(h * row.dy, row.dy, v[4]);
                 }
             }
             if (__any_sync(0xffffffffu, any)) {
@@ -484,7 +532,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
 }
 
 template <int P, bool COUNT, bool PERSIST>
-__global__ void __launch_bounds__(BLEND_THREADS / P)
+__global__ void __launch_bounds__(BLEND_THREADS / P, P == 8 ? SG_BWD8_MIN_BLOCKS : 1)
 k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const uint32_t *__restrict__ pval, const Rec *__restrict__ rec,
             const float *__restrict__ T_final, const int32_t *__restrict__ last,
@@ -492,7 +540,7 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const uint32_t *__restrict__ tile_order, uint32_t *__restrict__ queue, uint32_t n_tiles,
             unsigned long long *__restrict__ evals) {
     constexpr int NT = BLEND_THREADS / P;
-    __shared__ Staged sm;
+    __shared__ StagedB sm;
     __shared__ int smax[(NT + 31) / 32];
     __shared__ uint32_t s_item;
     const Batch &b = *bp;

@@ -256,20 +256,25 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_pass(
         k[i] = ok ? kin[j] : 0u;
         v[i] = ok ? vin[j] : 0u;
     }
+    // Warp-local stable ranks. Per item, the lowest lane of each group of equal
+    // digits adds the group's size to the warp's counter; shared-memory atomics
+    // of one warp take effect in issue order, so the returned bases follow the
+    // key order. All atomics are issued before any base is broadcast.
     const uint32_t lt = lanemask_lt();
+    uint32_t meta[RS_ITEMS];   // leader lane | (rank inside the group << 5)
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
         const uint64_t j = wbase + (uint64_t)i * 32 + lane;
         const bool ok = j < n;
         const uint32_t d = ok ? ((k[i] >> shift) & mask) : 0x100u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = 0u;
-        if (ok) before = cnt[warp][d];
-        r[i] = before + __popc(peers & lt);
-        __syncwarp();
-        if (ok && (peers & lt) == 0u) cnt[warp][d] = before + __popc(peers);
-        __syncwarp();
+        const uint32_t below = peers & lt;
+        r[i] = (ok && below == 0u) ? atomicAdd(&cnt[warp][d], (uint32_t)__popc(peers)) : 0u;
+        meta[i] = (uint32_t)(__ffs(peers) - 1) | ((uint32_t)__popc(below) << 5);
     }
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i)
+        r[i] = __shfl_sync(0xffffffffu, r[i], (int)(meta[i] & 31u)) + (meta[i] >> 5);
     __syncthreads();
     // per digit: exclusive offsets over warps, block total, block-local start
     uint32_t run = 0u;
