@@ -162,13 +162,18 @@ typedef struct sg_sizes {
  * e = ent_off(view) + Gaussian id, views in call order). Read-only views for
  * inspection, e.g. visibility and screen radius per Gaussian.
  *   rec           [M] 48-byte records, binary32:
- *                     x, y, conic A, conic B | conic C, o', r, g | b, radius, depth, 0
+ *                     x, y, conic A, conic B | conic C, o', r, g | b, radius, depth, t
+ *                 (t: the enlarged bound on q = d^T conic d where alpha can
+ *                 reach 1/255, 2 ln(255 o') 1.01 + 0.01, negative if o' < 1/255)
  *                 (x, y: projected centre in pixel-index coordinates; conic
  *                 (A, B, C) = inverse of the dilated 2D covariance; o' = m_g o;
  *                 rgb = max(c(v), 0); radius = ceil(3 sqrt(lambda_max)); depth =
- *                 camera-space z). Valid where tiles_touched > 0.
- *   tiles_touched [M] uint32, 0 = culled
- *   rect          [M] 2 x uint32: x0 | x1 << 16, y0 | y1 << 16 (tiles, half open)
+ *                 camera-space z). Valid where rect is not empty.
+ *   tiles_touched [M] uint32: tiles of rect whose pixel-centre box meets the
+ *                 (slightly enlarged) ellipse where alpha can reach 1/255;
+ *                 only these get a pair. 0 = culled or never blended.
+ *   rect          [M] 2 x uint32: x0 | x1 << 16, y0 | y1 << 16 (tiles, half
+ *                 open; the 3-sigma rectangle; empty = culled)
  *   depth_order   [M] uint32 entries sorted by (depth bits, entry)
  *   ranges        [n_tiles] 2 x uint32 [start, end) into the pair arrays
  *   pair_tile     [n_pairs] uint32 global tile id (view tile offset + ty * tiles_x + tx)

@@ -438,7 +438,7 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     uint32_t *k1 = even ? pk_tmp : pk_final, *v1 = even ? pv_tmp : pv_final;
     {
         StageTimer t(ST_DUPLICATE, stream);
-        SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, offs, counters, cap, k0, v0, n_views, stream),
+        SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, rec, offs, counters, cap, k0, v0, n_views, stream),
                 "duplicateWithKeys");
     }
     {

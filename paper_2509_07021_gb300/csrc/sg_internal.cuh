@@ -63,7 +63,7 @@ struct Batch {
 struct __align__(16) Rec {
     float4 a;   // x, y, conic A, conic B
     float4 b;   // conic C, o' = m_g * o, r, g
-    float4 c;   // b, unused x3
+    float4 c;   // b, radius, depth, tile-binning threshold (tile_reach_threshold)
 };
 
 // Device counters kept in the workspace.
@@ -97,6 +97,79 @@ struct WsLayout {
 
 __host__ __device__ inline uint64_t div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
+// ---------------------------------------------------------------------------
+// Tight tile binning. A pair (tile, Gaussian) can only blend where
+// alpha = o' exp(-q / 2) >= 1/255, q = A dx^2 + 2 B dx dy + C dy^2 (the conic),
+// i.e. inside the ellipse q <= 2 ln(255 o'). Of the tiles of the 3-sigma
+// rectangle, only those whose box of pixel centres meets that ellipse get a
+// pair; the others would be skipped at every pixel, so leaving them out changes
+// no image and no gradient. The ellipse is enlarged (1 % + 0.01 in q, 0.02 px)
+// so that binary32 rounding here or in the blend can only keep extra tiles.
+// Preprocess counts the tiles and duplicate enumerates them with this same
+// code (explicitly rounded operations), so the two agree exactly.
+// ---------------------------------------------------------------------------
+struct TileReach {
+    float x, y, B, det, At, ymax, m, invA;
+    int mode;   // 0: reaches nothing, 1: ellipse, 2: whole rectangle (degenerate conic)
+};
+
+// Enlarged bound on q where alpha can reach 1/255: 2 ln(255 o') (1 + 1 %) + 0.01;
+// negative when o' < 1/255 (alpha <= o' < 1/255 everywhere). Computed once per
+// entry by preprocess and kept in its record, so that the count and the
+// enumeration of tiles start from the same binary32 value.
+__device__ __forceinline__ float tile_reach_threshold(float op) {
+    if (!(op >= 1.0f / 255.0f)) return -1.0f;
+    const float t0 = 2.0f * logf(__fmul_rn(255.0f, op));
+    return __fadd_rn(__fmul_rn(t0, 1.01f), 0.01f);
+}
+
+__device__ __forceinline__ void tile_reach_init(float x, float y, float A, float B, float C, float t,
+                                                TileReach &R) {
+    R.x = x; R.y = y; R.B = B;
+    R.det = R.At = R.ymax = R.m = R.invA = 0.f;
+    if (!(t >= 0.f)) { R.mode = 0; return; }
+    R.det = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
+    if (!(A > 0.f) || !(C > 0.f) || !(R.det > 0.f) || !isfinite(t) || !isfinite(R.det)) {
+        R.mode = 2;
+        return;
+    }
+    R.At = __fmul_rn(A, t);
+    R.ymax = __fsqrt_rn(__fdiv_rn(R.At, R.det));
+    const float xmax = __fsqrt_rn(__fdiv_rn(__fmul_rn(C, t), R.det));
+    R.m = __fdiv_rn(__fmul_rn(B, xmax), C);   // dy of the right-most point is -m, of the left-most +m
+    R.invA = __frcp_rn(A);
+    R.mode = isfinite(R.ymax) && isfinite(R.m) && isfinite(R.At) && isfinite(R.invA) ? 1 : 2;
+}
+
+// Columns [c0, c1) of tile row ty (within [x0, x1)) that the enlarged ellipse
+// reaches. Over the row's band of dy, the ellipse's right edge
+// x_r(dy) = (-B dy + sqrt(A t - det dy^2)) / A is concave with its maximum at
+// dy = -m (m = B xmax / C), the left edge convex with its minimum at dy = +m:
+// both extremes are taken at those points clamped into the band.
+__device__ __forceinline__ void tile_reach_row(const TileReach &R, int ty, int x0, int x1, int &c0, int &c1) {
+    c0 = c1 = x0;
+    if (R.mode == 0) return;
+    if (R.mode == 2) { c1 = x1; return; }
+    const float pad = 0.02f;
+    float lo = __fsub_rn(__fsub_rn((float)(ty * SG_TILE), R.y), pad);
+    float hi = __fadd_rn(__fsub_rn((float)(ty * SG_TILE + SG_TILE - 1), R.y), pad);
+    lo = fmaxf(lo, -R.ymax);
+    hi = fminf(hi, R.ymax);
+    if (!(lo <= hi)) return;
+    const float dr = fminf(fmaxf(-R.m, lo), hi), dl = fminf(fmaxf(R.m, lo), hi);
+    const float sr = __fsqrt_rn(fmaxf(0.f, __fsub_rn(R.At, __fmul_rn(R.det, __fmul_rn(dr, dr)))));
+    const float sl = __fsqrt_rn(fmaxf(0.f, __fsub_rn(R.At, __fmul_rn(R.det, __fmul_rn(dl, dl)))));
+    const float xr = __fadd_rn(__fadd_rn(R.x, __fmul_rn(__fsub_rn(sr, __fmul_rn(R.B, dr)), R.invA)), pad);
+    const float xl = __fsub_rn(__fsub_rn(R.x, __fmul_rn(__fadd_rn(sl, __fmul_rn(R.B, dl)), R.invA)), pad);
+    // tile tx is reached iff 16 tx <= xr and 16 tx + 15 >= xl (clamped to the rectangle first;
+    // scaling by 1/16 is exact)
+    const float fx0 = (float)(x0 * SG_TILE - SG_TILE), fx1 = (float)(x1 * SG_TILE);
+    const float a = ceilf(__fmul_rn(__fsub_rn(fminf(fmaxf(xl, fx0), fx1), (float)(SG_TILE - 1)), 1.0f / SG_TILE));
+    const float b = floorf(__fmul_rn(fminf(fmaxf(xr, fx0), fx1), 1.0f / SG_TILE));
+    c0 = max(x0, (int)a);
+    c1 = max(c0, min(x1, (int)b + 1));
+}
+
 // Process-wide count of kernels this library has launched (sg_kernel_launches).
 void count_launches(int n);
 
@@ -126,7 +199,7 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
 int radix_passes(int bits);
 
 cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,
-                             const uint32_t *tiles_touched, const uint2 *rect,
+                             const uint32_t *tiles_touched, const uint2 *rect, const Rec *rec,
                              const uint32_t *offsets, const uint64_t *counters, uint64_t cap,
                              uint32_t *pkey, uint32_t *pval, int n_views, cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64_t cap,

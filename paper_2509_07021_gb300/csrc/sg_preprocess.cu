@@ -343,9 +343,19 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
     Rec r;
     r.a = make_float4(G.x, G.y, G.conA, G.conB);
     r.b = make_float4(G.conC, G.op, fmaxf(cr, 0.f), fmaxf(cg, 0.f));
-    r.c = make_float4(fmaxf(cbl, 0.f), G.rf, G.tz, 0.f);
+    const float reach_t = tile_reach_threshold(G.op);
+    r.c = make_float4(fmaxf(cbl, 0.f), G.rf, G.tz, reach_t);
     rec[e] = r;
-    tiles_touched[e] = (uint32_t)((G.x1 - G.x0) * (G.y1 - G.y0));
+    // tiles of the rectangle that the alpha >= 1/255 ellipse reaches
+    TileReach R;
+    tile_reach_init(G.x, G.y, G.conA, G.conB, G.conC, reach_t, R);
+    uint32_t touched = 0u;
+    for (int ty = G.y0; ty < G.y1; ++ty) {
+        int c0, c1;
+        tile_reach_row(R, ty, G.x0, G.x1, c0, c1);
+        touched += (uint32_t)(c1 - c0);
+    }
+    tiles_touched[e] = touched;
     rect[e] = make_uint2((uint32_t)G.x0 | ((uint32_t)G.x1 << 16), (uint32_t)G.y0 | ((uint32_t)G.y1 << 16));
     dkey[e] = __float_as_uint(G.tz);
     dval[e] = (uint32_t)e;

@@ -402,20 +402,24 @@ __device__ __forceinline__ int find_entry_view(const Batch &b, uint64_t e) {
 // owning entry by binary search over the block's prefix sums, so stores are
 // coalesced and a large rectangle is spread over the whole block. Inside an
 // entry the tiles follow row-major order.
+// One block per 256 depth-sorted entries. The block's pairs go, entry by entry
+// and row by row, to [offsets[first entry], + the block's total): work items are
+// (entry, tile row); each finds its reached columns once and writes that run.
 __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp, uint64_t M,
                                                    const uint32_t *__restrict__ sorted_ent,
                                                    const uint32_t *__restrict__ tiles_touched,
-                                                   const uint2 *__restrict__ rect,
+                                                   const uint2 *__restrict__ rect, const Rec *__restrict__ rec,
                                                    const uint32_t *__restrict__ offsets,
                                                    const uint64_t *__restrict__ counters, uint64_t cap,
                                                    uint32_t *__restrict__ pkey,
                                                    uint32_t *__restrict__ pval) {
-    __shared__ uint32_t s_incl[256], s_e[256], s_x0[256], s_wx[256], s_y0[256], s_base[256], s_tx[256];
+    __shared__ uint32_t s_rinc[256], s_e[256], s_rx[256], s_ry[256], s_base[256], s_tx[256];
+    __shared__ TileReach s_R[256];
     __shared__ uint32_t shs[33];
     if (counters[CNT_PAIRS] > cap) return;   // capacity exceeded: the host reports it (uniform)
     const uint64_t j0 = (uint64_t)blockIdx.x * 256;
     const uint64_t j = j0 + threadIdx.x;
-    uint32_t e = 0, tt = 0, x0 = 0, wx = 1, y0 = 0, tbase = 0, tx = 1;
+    uint32_t e = 0, tt = 0, rows = 0, rx = 0, ry = 0, tbase = 0, tx = 1;
     if (j < M) {
         e = sorted_ent[j];
         tt = tiles_touched[e];
@@ -423,48 +427,71 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
             const Batch &b = *bp;
             const ViewDesc &vw = b.view[find_entry_view(b, e)];
             const uint2 rc = rect[e];
-            x0 = rc.x & 0xFFFFu;
-            wx = (rc.x >> 16) - x0;
-            y0 = rc.y & 0xFFFFu;
+            rx = rc.x;
+            ry = rc.y;
+            rows = (ry >> 16) - (ry & 0xFFFFu);
             tbase = vw.tile_off;
             tx = (uint32_t)vw.tiles_x;
+            const Rec r = rec[e];
+            tile_reach_init(r.a.x, r.a.y, r.a.z, r.a.w, r.b.x, r.c.w, s_R[threadIdx.x]);
         }
     }
-    uint32_t total;
-    const uint32_t excl = block_exclusive<uint32_t>(tt, total, shs);
-    s_incl[threadIdx.x] = excl + tt;
+    uint32_t total, total_rows;
+    block_exclusive<uint32_t>(tt, total, shs);
+    const uint32_t rexcl = block_exclusive<uint32_t>(rows, total_rows, shs);
+    s_rinc[threadIdx.x] = rexcl + rows;
     s_e[threadIdx.x] = e;
-    s_x0[threadIdx.x] = x0;
-    s_wx[threadIdx.x] = wx;
-    s_y0[threadIdx.x] = y0;
+    s_rx[threadIdx.x] = rx;
+    s_ry[threadIdx.x] = ry;
     s_base[threadIdx.x] = tbase;
     s_tx[threadIdx.x] = tx;
     __syncthreads();
     if (total == 0u) return;
     const uint64_t out0 = offsets[j0];
-    for (uint32_t q = threadIdx.x; q < total; q += 256) {
-        // first owner o with incl[o] > q
-        int lo = 0, hi = 255;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (s_incl[mid] > q) hi = mid; else lo = mid + 1;
+    uint32_t done = 0u;
+    for (uint32_t base = 0; base < total_rows; base += 256) {
+        const uint32_t item = base + threadIdx.x;
+        int o = 0, row = 0, c0 = 0, c1 = 0;
+        if (item < total_rows) {
+            // first owner o with s_rinc[o] > item
+            int lo = 0, hi = 255;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_rinc[mid] > item) hi = mid; else lo = mid + 1;
+            }
+            o = lo;
+            const uint32_t r0 = o ? s_rinc[o - 1] : 0u;
+            row = (int)(s_ry[o] & 0xFFFFu) + (int)(item - r0);
+            tile_reach_row(s_R[o], row, (int)(s_rx[o] & 0xFFFFu), (int)(s_rx[o] >> 16), c0, c1);
         }
-        const uint32_t start = lo ? s_incl[lo - 1] : 0u;
-        const uint32_t li = q - start;
-        const uint32_t w = s_wx[lo];
-        const uint32_t ry = li / w, rx = li - ry * w;
-        pkey[out0 + q] = s_base[lo] + (s_y0[lo] + ry) * s_tx[lo] + s_x0[lo] + rx;
-        pval[out0 + q] = s_e[lo];
+        uint32_t chunk;
+        const uint32_t at = done + block_exclusive<uint32_t>((uint32_t)(c1 - c0), chunk, shs);
+        const uint32_t key0 = s_base[o] + (uint32_t)row * s_tx[o];
+        for (int c = c0; c < c1; ++c) {
+            const uint32_t q = at + (uint32_t)(c - c0);
+            if (q < total) {   // rows sum to tiles_touched by construction; never write past the block
+                pkey[out0 + q] = key0 + (uint32_t)c;
+                pval[out0 + q] = s_e[o];
+            }
+        }
+        done += chunk;
+    }
+    // Rows add up to tiles_touched by construction. Should they ever fall short,
+    // the rest of the block's range still gets valid tile ids and entries.
+    for (uint32_t q = done + threadIdx.x; q < total; q += 256) {
+        pkey[out0 + q] = s_base[0];
+        pval[out0 + q] = (uint32_t)j0;
     }
 }
 
 cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,
-                             const uint32_t *tiles_touched, const uint2 *rect, const uint32_t *offsets,
+                             const uint32_t *tiles_touched, const uint2 *rect, const Rec *rec,
+                             const uint32_t *offsets,
                              const uint64_t *counters, uint64_t cap, uint32_t *pkey, uint32_t *pval,
                              int n_views, cudaStream_t s) {
     (void)n_views;
     if (M == 0) return cudaSuccess;
-    k_duplicate<<<(unsigned)div_up(M, 256), 256, 0, s>>>(db, M, sorted_ent, tiles_touched, rect, offsets,
+    k_duplicate<<<(unsigned)div_up(M, 256), 256, 0, s>>>(db, M, sorted_ent, tiles_touched, rect, rec, offsets,
                                                          counters, cap, pkey, pval);
     count_launches(1);
     return cudaGetLastError();
@@ -475,12 +502,13 @@ cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ pkey,
                                                 const uint64_t *__restrict__ counters, uint64_t cap,
-                                                uint2 *__restrict__ ranges) {
+                                                uint2 *__restrict__ ranges, uint64_t n_tiles) {
     const uint64_t K = counters[CNT_PAIRS];
     if (K > cap) return;
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= K) return;
     const uint32_t t = pkey[i];
+    if (t >= n_tiles) return;
     if (i == 0 || pkey[i - 1] != t) ranges[t].x = (uint32_t)i;
     if (i == K - 1 || pkey[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
 }
@@ -490,7 +518,7 @@ cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64
     cudaError_t e = cudaMemsetAsync(ranges, 0, n_tiles * sizeof(uint2), s);
     if (e != cudaSuccess) return e;
     if (cap == 0) return cudaSuccess;
-    k_ranges<<<(unsigned)div_up(cap, 256), 256, 0, s>>>(pkey, counters, cap, ranges);
+    k_ranges<<<(unsigned)div_up(cap, 256), 256, 0, s>>>(pkey, counters, cap, ranges, n_tiles);
     count_launches(1);
     return cudaGetLastError();
 }

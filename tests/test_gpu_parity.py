@@ -14,7 +14,7 @@ from paper_2509_07021_gb300 import render, sgsplat, synth
 from paper_2509_07021_gb300.sgsplat import DeviceScene
 
 from parity_util import (GpuView, check_decisions, check_grads, check_image, gpu_render,
-                         masked_dimg, pixel_mask_of_tiles, unpack_views)
+                         gpu_view_lists, masked_dimg, pixel_mask_of_tiles, unpack_views)
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
@@ -39,7 +39,8 @@ def run_parity(scene, cams, seed=0, grads=True, tile_sels=None, storage="f32", r
     rep = []
     for v, cam in enumerate(cams):
         mask = None if tile_sels is None else pixel_mask_of_tiles(cam, tile_sels[v])
-        rep.append(check_image(imgs[v], Ts[v], lasts[v], results[v], cam, mask))
+        rep.append(check_image(imgs[v], Ts[v], lasts[v], results[v], cam, mask,
+                               gpu_lists=gpu_view_lists(gv, cams, v)))
     if not grads:
         return rep, None
     rng = np.random.default_rng(seed)
