@@ -550,7 +550,7 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
     }
     {
         StageTimer t(ST_PRE_BWD, stream);
-        SG_CUDA(launch_preprocess_backward(b, db, tt, dg, M, stream), "preprocess backward");
+        SG_CUDA(launch_preprocess_backward(b, db, tt, rec, dg, M, stream), "preprocess backward");
     }
     if (counting) {
         uint64_t ne = 0;
@@ -910,6 +910,6 @@ extern "C" int sg_render_backward_noalloc(const sg_scene *scene, const sg_camera
     SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M, shape,
                                   nullptr, stream),
             "blend backward");
-    SG_CUDA(launch_preprocess_backward(b, db, tt, dg, M, stream), "preprocess backward");
+    SG_CUDA(launch_preprocess_backward(b, db, tt, rec, dg, M, stream), "preprocess backward");
     return SG_OK;
 }

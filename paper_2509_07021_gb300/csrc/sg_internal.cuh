@@ -178,7 +178,7 @@ cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStr
 cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32_t *tiles_touched,
                               uint2 *rect, uint32_t *dkey, uint32_t *dval, cudaStream_t s);
 cudaError_t launch_preprocess_backward(const Batch &hb, const Batch *db,
-                                       const uint32_t *tiles_touched, const float *dg,
+                                       const uint32_t *tiles_touched, const Rec *rec, const float *dg,
                                        uint64_t M, cudaStream_t s);
 
 // Exclusive scan of `in` (or of tiles_touched[idx[i]] when idx != null) into

@@ -280,6 +280,11 @@ __device__ __forceinline__ void sh3_grad_acc(float x, float y, float z, const fl
     gx += -SH_C3A * (3.f * xx - 3.f * yy) * w[15]; gy += 6.f * SH_C3A * x * y * w[15];
 }
 
+// max(c, 0) as the blend sees it, with the clamp recorded in the sign: c where
+// c >= 0, -0 where c < 0 (or NaN). The backward reads the sign back instead of
+// recomputing the colour.
+__device__ __forceinline__ float clamp_keep_sign(float c) { return c >= 0.f ? fabsf(c) : -0.0f; }
+
 // ---------------------------------------------------------------------------
 // K1 preprocessSG
 // ---------------------------------------------------------------------------
@@ -342,9 +347,9 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
     }
     Rec r;
     r.a = make_float4(G.x, G.y, G.conA, G.conB);
-    r.b = make_float4(G.conC, G.op, fmaxf(cr, 0.f), fmaxf(cg, 0.f));
+    r.b = make_float4(G.conC, G.op, clamp_keep_sign(cr), clamp_keep_sign(cg));
     const float reach_t = tile_reach_threshold(G.op);
-    r.c = make_float4(fmaxf(cbl, 0.f), G.rf, G.tz, reach_t);
+    r.c = make_float4(clamp_keep_sign(cbl), G.rf, G.tz, reach_t);
     rec[e] = r;
     // tiles of the rectangle that the alpha >= 1/255 ellipse reaches
     TileReach R;
@@ -395,10 +400,16 @@ cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32
 // K8 preprocess backward
 // ---------------------------------------------------------------------------
 // dg layout: planar [9][M]: dx, dy, dA, dB, dC, do', dr, dg, db per entry.
+// Resident blocks per SM requested for the preprocess adjoint (it is bound by
+// the latency of its parameter loads, so occupancy matters more than registers).
+#ifndef SG_PRE_BWD_MIN_BLOCKS
+#define SG_PRE_BWD_MIN_BLOCKS 3
+#endif
+
 template <int DG, int DL, int DS, int CM>
-__global__ void __launch_bounds__(PRE_THREADS)
+__global__ void __launch_bounds__(PRE_THREADS, SG_PRE_BWD_MIN_BLOCKS)
 k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tiles_touched,
-                 const float *__restrict__ dg, uint64_t M) {
+                 const Rec *__restrict__ rec, const float *__restrict__ dg, uint64_t M) {
     const Batch &b = *bp;
     const int si = find_block_scene(b, blockIdx.x);
     const SceneDesc &sc = b.scene[si];
@@ -410,8 +421,6 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
     load_geo<DG>(sc, g, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o);
     const float gm = __ldg(sc.gmask + g);
     const bool sh_mode = CM == SG_COLOR_SH3;
-    const float c00 = sh_mode ? 0.f : __ldg(sc.c0 + g), c01 = sh_mode ? 0.f : __ldg(sc.c0 + n + g),
-                c02 = sh_mode ? 0.f : __ldg(sc.c0 + 2 * n + g);
     const int hi = sh_mode ? 0 : min(__ldg(sc.lobe_off + g + 1), (int)L);
     const int lo = sh_mode ? 0 : max(0, min(__ldg(sc.lobe_off + g), hi));
 
@@ -423,13 +432,17 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
         const ViewDesc &vw = b.view[v];
         if (vw.scene != si) continue;
         const uint64_t e = vw.ent_off + (uint64_t)g;
-        if (tiles_touched[e] == 0u) continue;
+        // every load of this view is issued before the visibility test
+        const uint32_t tte = tiles_touched[e];
         const float gx = dg[e], gy = dg[M + e], gA = dg[2 * M + e], gB = dg[3 * M + e],
                     gC = dg[4 * M + e], gop = dg[5 * M + e];
         const float grgb[3] = {dg[6 * M + e], dg[7 * M + e], dg[8 * M + e]};
-
-        Geo G;
-        project_recipe(vw, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o, gm, G);
+        const float4 rb = rec[e].b;
+        const float rcb = rec[e].c.x;
+        if (tte == 0u) continue;
+        // the forward's clamp max(c, 0), read back from the sign of its record
+        const float gc[3] = {signbit(rb.z) ? 0.f : grgb[0], signbit(rb.w) ? 0.f : grgb[1],
+                             signbit(rcb) ? 0.f : grgb[2]};
 
         // o' = m_g * o
         d_opac += gm * gop;
@@ -445,14 +458,6 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
             // c = 0.5 + sum_k Y_k(v) sh_k per channel
             float Y[16];
             sh3_basis(vx, vy, vz, Y);
-            float gc[3];
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float c = 0.5f;
-#pragma unroll
-                for (int k = 0; k < 16; ++k) c = fmaf(Y[k], __ldg(sc.sh + (int64_t)(ch * 16 + k) * n + g), c);
-                gc[ch] = c >= 0.f ? grgb[ch] : 0.f;
-            }
             float w[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -472,22 +477,10 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
                     }
             }
         }
-        float col[3] = {c00, c01, c02};
-        for (int k = lo; k < hi; ++k) {
-            const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
-                        az = ldp<DL>(sc.axis, 2 * L + k);
-            const float ia = 1.0f / sqrtf(ax * ax + ay * ay + az * az);
-            const float dot = (ax * vx + ay * vy + az * vz) * ia;
-            const float wgt = __ldg(sc.lmask + k) * expf(ldp<DS>(sc.sharp, k) * (dot - 1.0f));
-            col[0] += wgt * ldp<DL>(sc.amp, k);
-            col[1] += wgt * ldp<DL>(sc.amp, L + k);
-            col[2] += wgt * ldp<DL>(sc.amp, 2 * L + k);
-        }
-        float gc[3];
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            gc[ch] = col[ch] >= 0.f ? grgb[ch] : 0.f;   // max(c, 0)
-            if (!sh_mode) d_c0[ch] += gc[ch];
+        if (!sh_mode) {
+            d_c0[0] += gc[0];
+            d_c0[1] += gc[1];
+            d_c0[2] += gc[2];
         }
         for (int k = lo; k < hi; ++k) {
             const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
@@ -531,6 +524,11 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
             d_mean[1] += (dvy - vy * pr) * idn;
             d_mean[2] += (dvz - vz * pr) * idn;
         }
+
+        // ---- geometry: recompute the projection (after the colour part, so that
+        // its intermediates are not live across the lobe loop) ----
+        Geo G;
+        project_recipe(vw, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o, gm, G);
 
         // ---- projected centre: x = fx t_x / t_z + cx - 0.5 ----
         const float itz = 1.0f / G.tz;
@@ -647,29 +645,29 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
 }
 
 template <int DG, int DL, int DS, int CM = SG_COLOR_SG>
-static cudaError_t launch_bwd_t(const Batch &hb, const Batch *db, const uint32_t *tt, const float *dg,
-                                uint64_t M, cudaStream_t s) {
+static cudaError_t launch_bwd_t(const Batch &hb, const Batch *db, const uint32_t *tt, const Rec *rec,
+                                const float *dg, uint64_t M, cudaStream_t s) {
     if (hb.bwd_blocks == 0) return cudaSuccess;
-    k_preprocess_bwd<DG, DL, DS, CM><<<hb.bwd_blocks, PRE_THREADS, 0, s>>>(db, tt, dg, M);
+    k_preprocess_bwd<DG, DL, DS, CM><<<hb.bwd_blocks, PRE_THREADS, 0, s>>>(db, tt, rec, dg, M);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_preprocess_backward(const Batch &hb, const Batch *db, const uint32_t *tiles_touched,
-                                       const float *dg, uint64_t M, cudaStream_t s) {
+                                       const Rec *rec, const float *dg, uint64_t M, cudaStream_t s) {
     const SceneDesc &sc = hb.scene[0];
     const int key = sc.dtype_geom * 9 + sc.dtype_lobe * 3 + sc.dtype_sharp;
     if (sc.color_model == SG_COLOR_SH3) {
         if (key != SG_F32 * 9 + SG_F32 * 3 + SG_F32) return cudaErrorInvalidValue;
-        return launch_bwd_t<SG_F32, SG_F32, SG_F32, SG_COLOR_SH3>(hb, db, tiles_touched, dg, M, s);
+        return launch_bwd_t<SG_F32, SG_F32, SG_F32, SG_COLOR_SH3>(hb, db, tiles_touched, rec, dg, M, s);
     }
     switch (key) {
         case SG_F32 * 9 + SG_F32 * 3 + SG_F32:
-            return launch_bwd_t<SG_F32, SG_F32, SG_F32>(hb, db, tiles_touched, dg, M, s);
+            return launch_bwd_t<SG_F32, SG_F32, SG_F32>(hb, db, tiles_touched, rec, dg, M, s);
         case SG_F16 * 9 + SG_F16 * 3 + SG_F16:
-            return launch_bwd_t<SG_F16, SG_F16, SG_F16>(hb, db, tiles_touched, dg, M, s);
+            return launch_bwd_t<SG_F16, SG_F16, SG_F16>(hb, db, tiles_touched, rec, dg, M, s);
         case SG_F16 * 9 + SG_F16 * 3 + SG_BF16:
-            return launch_bwd_t<SG_F16, SG_F16, SG_BF16>(hb, db, tiles_touched, dg, M, s);
+            return launch_bwd_t<SG_F16, SG_F16, SG_BF16>(hb, db, tiles_touched, rec, dg, M, s);
         default:
             return cudaErrorInvalidValue;
     }
