@@ -36,6 +36,42 @@ L2_FLUSH_BYTES = 512 << 20
 # Algorithmic FP32 work per evaluated (pixel, Gaussian) pair, FMA = 2 flops
 # (derivation in the design doc): forward 23, backward 69.
 FLOPS_PER_EVAL = {"blend_fwd": 23.0, "blend_bwd": 69.0}
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic_1m_1080p.md")
+
+
+def kernel_source_digest():
+    """sha256 over the CUDA sources (any kernel change invalidates recorded counters)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2509_07021_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(stage):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu summary,
+    or None when the sources changed since the capture (or no capture exists).
+    Table rows: | stage | kernel | dram bytes per launch | ... |, with a line
+    'source sha256: <digest>' naming the sources the counters were taken on."""
+    try:
+        text = open(TRAFFIC_TABLE).read()
+    except OSError:
+        return None
+    import re
+    m = re.search(r"source sha256:\s*`?([0-9a-f]{64})", text)
+    if not m or m.group(1) != kernel_source_digest():
+        return None
+    for line in text.splitlines():
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] == stage:
+            try:
+                return float(cells[2].replace(",", ""))
+            except ValueError:
+                return None
+    return None
 # GB300 FP32 (non-tensor) peak: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
@@ -329,7 +365,7 @@ def run_ours(args, world, rank, local):
         ev = evals["forward" if dom == "blend_fwd" else "backward"]
         achieved = ev * FLOPS_PER_EVAL[dom] / (avg_ms / 1e3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": recorded_traffic(dom),
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz (FP32 non-tensor)",
                 "pair_evals": ev, "flops_per_eval": FLOPS_PER_EVAL[dom], "avg_ms": avg_ms}
     else:
@@ -340,7 +376,7 @@ def run_ours(args, world, rank, local):
             pass
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
-                "frac": None, "traffic": None, "avg_ms": avg_ms}
+                "frac": None, "traffic": recorded_traffic(dom), "avg_ms": avg_ms}
 
     # ---- end to end through the public API with host buffers ----
     e2e = run_e2e(args, ds, cams, d_img_np, grads, world)
