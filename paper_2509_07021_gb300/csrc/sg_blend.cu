@@ -505,26 +505,30 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
                     v[6] = fmaf(w, g0[j], v[6]);
                     v[7] = fmaf(w, g1[j], v[7]);
                     v[8] = fmaf(w, g2[j], v[8]);
-                    // dL/do' share of this pixel; none where the 0.99 clamp is active
+                    // dL/do' share of this pixel; none where the 0.99 clamp is active.
+                    // dL/dpower = o' dG: the factor o' is applied once per Gaussian.
                     const float dG = p.ag > ALPHA_MAX ? 0.f : dal * p.G;
-                    const float h = dG * r.y;                // dL/dpower
                     v[5] += dG;
-                    // with L = log2 e: qa dx + qb dy = t, so A dx + B dy = -(t + qa dx) / L
-                    v[0] = fmaf(h, fmaf(q.z, p.dx, p.t), v[0]);
-                    v[1] = fmaf(h, fmaf(2.f, row.u, q.w * p.dx), v[1]);
-                    const float hx = h * p.dx;
-                    v[2] = fmaf(hx, p.dx, v[2]);
-                    v[3] = fmaf(hx, row.dy, v[3]);
-                    v[4] = fmaf(h * row.dy, row.dy, v[4]);
+                    const float hx = dG * p.dx, hy = dG * row.dy;
+                    v[0] += hx;                               // sum dG dx
+                    v[1] += hy;                               // sum dG dy
+                    v[2] = fmaf(hx, p.dx, v[2]);              // sum dG dx^2
+                    v[3] = fmaf(hx, row.dy, v[3]);            // sum dG dx dy
+                    v[4] = fmaf(hy, row.dy, v[4]);            // sum dG dy^2
                 }
             }
             if (__any_sync(0xffffffffu, any)) {
-                // constant factors of the accumulated forms
-                v[0] *= -1.f / LOG2E;
-                v[1] *= -1.f / LOG2E;
-                v[2] *= -0.5f;
-                v[3] *= -1.f;
-                v[4] *= -0.5f;
+                // power log2(e) = qa dx^2 + qb dx dy + qc dy^2 with (qa, qb, qc) =
+                // -log2(e) (A/2, B, C/2), dL/dpower = o' dG and d/dx = -d/d(dx):
+                //   dL/dx = -o' sum dG (2 qa dx + qb dy) / log2(e), likewise dL/dy,
+                //   dL/dA = -o' sum dG dx^2 / 2, dL/dB = -o' sum dG dx dy, dL/dC = -o' sum dG dy^2 / 2
+                const float o = r.y, kxy = -o * (1.f / LOG2E);
+                const float sx = v[0], sy = v[1];
+                v[0] = kxy * fmaf(2.f * q.z, sx, q.w * sy);
+                v[1] = kxy * fmaf(2.f * r.x, sy, q.w * sx);
+                v[2] *= -0.5f * o;
+                v[3] *= -o;
+                v[4] *= -0.5f * o;
                 warp_sum9_atomic(v, dg, M, sm.id[k]);
             }
         }
