@@ -175,7 +175,8 @@ typedef struct sg_sizes {
  *                 only these get a pair. 0 = culled or never blended.
  *   rect          [M] 2 x uint32: x0 | x1 << 16, y0 | y1 << 16 (tiles, half
  *                 open; the 3-sigma rectangle; empty = culled)
- *   depth_order   [M] uint32 entries sorted by (depth bits, entry)
+ *   depth_order   [M] uint32: the entries with tiles_touched > 0 sorted by
+ *                 (depth bits, entry), first; the rest of the array is scratch
  *   ranges        [n_tiles] 2 x uint32 [start, end) into the pair arrays
  *   pair_tile     [n_pairs] uint32 global tile id (view tile offset + ty * tiles_x + tx)
  *   pair_entry    [n_pairs] uint32 entry of each pair, sorted by (tile, depth bits, entry)
@@ -213,6 +214,10 @@ int sg_workspace_layout(const sg_scene *scene, const sg_camera *cams, int n_view
 #define SG_PROFILE_STAGES 12
 int sg_profile_enable(int flags);
 int sg_profile_read(double *ms, int64_t *launches, int64_t *pair_evals, int reset);
+/* Which stages SG_PROFILE_EVENTS brackets: bit i for stage i (default: all).
+ * Timing only the stage of interest keeps the event records from adding gaps
+ * to the others. Returns SG_OK. */
+int sg_profile_set_stages(uint32_t stage_mask);
 /*
  * Kernel shapes (process wide, not synchronised with renders in flight):
  * pixels each blend thread owns, 1, 2, 4 or 8 (the block has 256 / P threads

@@ -57,6 +57,7 @@ const char *const kStageNames[ST_N] = {"setup", "preprocess", "depth_sort", "pai
 struct Profiler {
     std::mutex mu;
     int flags = 0;
+    uint32_t stage_mask = 0xFFFFFFFFu;
     std::vector<cudaEvent_t> pool;
     struct Pending { int stage; cudaEvent_t a, b; };
     std::vector<Pending> pending;
@@ -84,7 +85,7 @@ struct StageTimer {
     cudaEvent_t a = nullptr;
     StageTimer(int st, cudaStream_t stream) : stage(st), s(stream) {
         Profiler &p = prof();
-        if (!(p.flags & SG_PROFILE_EVENTS)) return;
+        if (!(p.flags & SG_PROFILE_EVENTS) || !((p.stage_mask >> st) & 1u)) return;
         std::lock_guard<std::mutex> g(p.mu);
         a = p.get();
         if (a) cudaEventRecord(a, s);
@@ -101,7 +102,7 @@ struct StageTimer {
 };
 
 // Process-wide kernel shape choices (sg_set_tuning); defaults from measurement.
-constexpr sg_tuning kDefaultTuning = {1, 4, 0, 0, {0, 0, 0, 0}};
+constexpr sg_tuning kDefaultTuning = {1, 8, 0, 1, {0, 0, 0, 0}};
 sg_tuning &tuning() {
     static sg_tuning t = kDefaultTuning;
     return t;
@@ -399,13 +400,15 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     {
         // depth digits, once per entry (result back in dkey0/dval0 after 4 passes)
         StageTimer t(ST_DEPTH_SORT, stream);
+        // entries that reach no tile carry the drop key and are left out of the order
         SG_CUDA(launch_radix_sort(dkey0, dval0, dkey1, dval1, counters + CNT_ENTRIES, M, 32, hist, sums,
-                                  stream, counters + CNT_STATUS),
+                                  stream, counters + CNT_STATUS, counters + CNT_VISIBLE),
                 "depth sort");
     }
     {
         StageTimer t(ST_OFFSETS, stream);
-        SG_CUDA(launch_scan(tt, dval0, offs, M, sums, counters + CNT_PAIRS, stream), "pair offsets");
+        SG_CUDA(launch_scan(tt, dval0, offs, M, sums, counters + CNT_PAIRS, stream, counters + CNT_VISIBLE),
+                "pair offsets");
     }
     uint64_t K = cap;   // batched form: grids sized by the capacity, counts read on the device
     if (sync) {
@@ -570,6 +573,13 @@ int sg_profile_enable(int flags) {
     Profiler &p = prof();
     std::lock_guard<std::mutex> g(p.mu);
     p.flags = flags & (SG_PROFILE_EVENTS | SG_PROFILE_COUNT);
+    return SG_OK;
+}
+
+int sg_profile_set_stages(uint32_t stage_mask) {
+    Profiler &p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.stage_mask = stage_mask;
     return SG_OK;
 }
 

@@ -74,13 +74,17 @@ enum : int {
     CNT_EVALS = 3,     // pair evaluations (counting kernels)
     CNT_TILES = 4,     // tiles
     CNT_QUEUE = 5,     // persistent-blend work counter
+    CNT_VISIBLE = 6,   // entries with at least one pair (the depth order's length)
     CNT_N = 8
 };
 
 // Radix sort / scan geometry.
 constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;   // 4096 keys per block
+#ifndef SG_RS_ITEMS
+#define SG_RS_ITEMS 12
+#endif
+constexpr int RS_ITEMS = SG_RS_ITEMS;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;   // 3072 keys per block
 constexpr int RS_RADIX = 256;
 constexpr int SCAN_TILE = 4096;
 
@@ -182,9 +186,11 @@ cudaError_t launch_preprocess_backward(const Batch &hb, const Batch *db,
                                        uint64_t M, cudaStream_t s);
 
 // Exclusive scan of `in` (or of tiles_touched[idx[i]] when idx != null) into
-// `out`, total written to *total. n items (host known).
+// `out`, total written to *total. n items (host known), or min(n, *n_dev) when
+// n_dev is given.
 cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t *out,
-                        uint64_t n, uint64_t *block_sums, uint64_t *total, cudaStream_t s);
+                        uint64_t n, uint64_t *block_sums, uint64_t *total, cudaStream_t s,
+                        const uint64_t *n_dev = nullptr);
 
 // Stable LSD radix sort of (key, val) u32 pairs on bits [0, bits); item count read
 // from *n_dev and clamped to max_n (the capacity the launch is sized for, below
@@ -192,10 +198,14 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 // (k0,v0) when the pass count is even, else in (k1,v1).
 // hist: RS_RADIX x ceil(max_n / RS_TILE) words of look-back flags; aux: at least
 // SORT_AUX_BYTES; status (nullable): set to SG_ERR_TIMEOUT if a look-back gave up.
+// kept_out (nullable): drop mode — keys equal to SORT_DROP_KEY are left out, the
+// sorted kept keys fill positions [0, *kept_out) and *kept_out receives their count.
 constexpr size_t SORT_AUX_BYTES = 16384;
+constexpr uint32_t SORT_DROP_KEY = 0xFFFFFFFFu;
 cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
-                              uint64_t *aux, cudaStream_t s, uint64_t *status = nullptr);
+                              uint64_t *aux, cudaStream_t s, uint64_t *status = nullptr,
+                              uint64_t *kept_out = nullptr);
 int radix_passes(int bits);
 
 cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,

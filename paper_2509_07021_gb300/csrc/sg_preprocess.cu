@@ -308,7 +308,7 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
     if (!G.visible) {
         tiles_touched[e] = 0u;
         rect[e] = make_uint2(0u, 0u);
-        dkey[e] = 0xFFFFFFFFu;
+        dkey[e] = SORT_DROP_KEY;
         dval[e] = (uint32_t)e;
         return;
     }
@@ -362,7 +362,7 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
     }
     tiles_touched[e] = touched;
     rect[e] = make_uint2((uint32_t)G.x0 | ((uint32_t)G.x1 << 16), (uint32_t)G.y0 | ((uint32_t)G.y1 << 16));
-    dkey[e] = __float_as_uint(G.tz);
+    dkey[e] = touched ? __float_as_uint(G.tz) : SORT_DROP_KEY;   // no pair: not depth-sorted
     dval[e] = (uint32_t)e;
 }
 

@@ -62,8 +62,10 @@ __device__ __forceinline__ uint32_t scan_load(const uint32_t *in, const uint32_t
 
 __global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *__restrict__ in,
                                                      const uint32_t *__restrict__ idx, uint64_t n,
+                                                     const uint64_t *__restrict__ n_dev,
                                                      uint64_t *__restrict__ sums) {
     __shared__ uint64_t sh[33];
+    if (n_dev) n = min(n, *n_dev);
     const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     uint64_t acc = 0;
 #pragma unroll 4
@@ -95,8 +97,10 @@ __global__ void __launch_bounds__(1024) k_scan_spine(uint64_t *__restrict__ sums
 
 __global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ in,
                                                    const uint32_t *__restrict__ idx, uint64_t n,
+                                                   const uint64_t *__restrict__ n_dev,
                                                    const uint64_t *__restrict__ sums,
                                                    uint32_t *__restrict__ out) {
+    if (n_dev) n = min(n, *n_dev);
     // each thread owns 16 consecutive items, staged through shared memory
     __shared__ uint32_t buf[SCAN_TILE + SCAN_TILE / 32];
     __shared__ uint64_t sh[33];
@@ -134,17 +138,17 @@ __global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ 
 }
 
 cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t *out, uint64_t n,
-                        uint64_t *block_sums, uint64_t *total, cudaStream_t s) {
+                        uint64_t *block_sums, uint64_t *total, cudaStream_t s, const uint64_t *n_dev) {
     const uint64_t nb = div_up(n, SCAN_TILE);
     if (nb == 0) {
         if (total) return cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
         return cudaSuccess;
     }
-    k_scan_reduce<<<(unsigned)nb, 256, 0, s>>>(in, gather_idx, n, block_sums);
+    k_scan_reduce<<<(unsigned)nb, 256, 0, s>>>(in, gather_idx, n, n_dev, block_sums);
     count_launches(1);
     k_scan_spine<<<1, 1024, 0, s>>>(block_sums, nb, total);
     count_launches(1);
-    k_scan_down<<<(unsigned)nb, 256, 0, s>>>(in, gather_idx, n, block_sums, out);
+    k_scan_down<<<(unsigned)nb, 256, 0, s>>>(in, gather_idx, n, n_dev, block_sums, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -171,6 +175,8 @@ struct SortAux {
     uint32_t base[4][RS_RADIX];   // exclusive digit bases per pass
     uint32_t tile_ctr[4];         // tile counter per pass
     uint32_t status;              // 0 or SG_ERR_TIMEOUT
+    uint32_t pad;
+    uint64_t kept;                // keys other than SORT_DROP_KEY (drop mode)
 };
 static_assert(sizeof(SortAux) <= SORT_AUX_BYTES, "sort aux region");
 
@@ -188,7 +194,7 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
 // with few distinct digits (the high tile bits) from serialising.
 __global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint32_t *__restrict__ keys,
                                                         const uint64_t *__restrict__ n_dev, uint64_t max_n,
-                                                        int bits, SortAux *aux) {
+                                                        int bits, bool drop, SortAux *aux) {
     constexpr int NW = RS_THREADS / 32;
     __shared__ uint32_t h[NW][4][RS_RADIX];
     const int passes = radix_passes_dev(bits);
@@ -198,12 +204,20 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint32_t *__restri
     __syncthreads();
     const uint64_t n = min(*n_dev, max_n);
     const uint64_t stride = (uint64_t)gridDim.x * RS_THREADS;
+    uint32_t kept = 0u;
     for (uint64_t j = (uint64_t)blockIdx.x * RS_THREADS + threadIdx.x; j < n; j += stride) {
         const uint32_t k = keys[j];
+        if (drop && k == SORT_DROP_KEY) continue;
+        ++kept;
         for (int p = 0; p < passes; ++p) {
             const int nb = min(8, bits - 8 * p);
             atomicAdd(&h[warp][p][(k >> (8 * p)) & ((1u << nb) - 1u)], 1u);
         }
+    }
+    if (drop) {
+        const uint32_t wk = __reduce_add_sync(0xffffffffu, kept);
+        if ((threadIdx.x & 31) == 0 && wk)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&aux->kept), (unsigned long long)wk);
     }
     __syncthreads();
     for (int p = 0; p < passes; ++p) {
@@ -225,7 +239,7 @@ __global__ void __launch_bounds__(RS_RADIX) k_os_base(SortAux *aux, int passes) 
 __global__ void __launch_bounds__(RS_THREADS) k_os_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint64_t *__restrict__ n_dev, uint64_t max_n, int pass, int shift,
-    uint32_t mask, uint32_t *__restrict__ flags, SortAux *aux) {
+    uint32_t mask, bool drop, uint32_t *__restrict__ flags, SortAux *aux) {
     constexpr int NW = RS_THREADS / 32;
     constexpr int PER_WARP = RS_TILE / NW;   // 512 consecutive keys per warp
     __shared__ uint32_t cnt[NW][RS_RADIX];
@@ -265,7 +279,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_pass(
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
         const uint64_t j = wbase + (uint64_t)i * 32 + lane;
-        const bool ok = j < n;
+        const bool ok = j < n && !(drop && k[i] == SORT_DROP_KEY);
         const uint32_t d = ok ? ((k[i] >> shift) & mask) : 0x100u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t below = peers & lt;
@@ -327,7 +341,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_pass(
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
         const uint64_t j = wbase + (uint64_t)i * 32 + lane;
-        if (j < n) {
+        if (j < n && !(drop && k[i] == SORT_DROP_KEY)) {
             const uint32_t dd = (k[i] >> shift) & mask;
             const uint32_t pos = dstart[dd] + cnt[warp][dd] + r[i];
             sk[pos] = k[i];
@@ -335,7 +349,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_pass(
         }
     }
     __syncthreads();
-    const int items = (n - base) < (uint64_t)RS_TILE ? (int)(n - base) : RS_TILE;
+    const int items = (int)tot;   // the block's kept keys
     for (int p = threadIdx.x; p < items; p += RS_THREADS) {
         const uint32_t key = sk[p];
         const uint32_t dd = (key >> shift) & mask;
@@ -347,13 +361,14 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_pass(
 
 int radix_passes(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
 
-__global__ void k_os_status(const SortAux *aux, uint64_t *status) {
-    if (aux->status) *status = aux->status;
+__global__ void k_os_finish(const SortAux *aux, uint64_t *status, uint64_t *kept_out) {
+    if (status && aux->status) *status = aux->status;
+    if (kept_out) *kept_out = aux->kept;
 }
 
 cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
-                              uint64_t *scan_sums, cudaStream_t s, uint64_t *status) {
+                              uint64_t *scan_sums, cudaStream_t s, uint64_t *status, uint64_t *kept_out) {
     const uint32_t nblocks = (uint32_t)div_up(max_n, RS_TILE);
     const int passes = radix_passes(bits);
     if (nblocks == 0 || passes == 0) return cudaSuccess;
@@ -362,7 +377,8 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
     cudaError_t e = cudaMemsetAsync(aux, 0, sizeof(SortAux), s);
     if (e != cudaSuccess) return e;
     const unsigned hgrid = nblocks < 4u * 152u ? nblocks : 4u * 152u;
-    k_os_hist<<<hgrid, RS_THREADS, 0, s>>>(k0, n_dev, max_n, bits, aux);
+    const bool drop = kept_out != nullptr;
+    k_os_hist<<<hgrid, RS_THREADS, 0, s>>>(k0, n_dev, max_n, bits, drop, aux);
     k_os_base<<<1, RS_RADIX, 0, s>>>(aux, passes);
     count_launches(2);
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
@@ -372,14 +388,17 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
         const uint32_t mask = (1u << nb) - 1u;
         e = cudaMemsetAsync(hist, 0, (size_t)nblocks * RS_RADIX * sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
-        k_os_pass<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n_dev, max_n, p, shift, mask, hist, aux);
+        // with drop, pass 0 leaves SORT_DROP_KEY out and later passes see only the kept keys
+        const uint64_t *np = (drop && p > 0) ? &aux->kept : n_dev;
+        k_os_pass<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, np, max_n, p, shift, mask, drop && p == 0,
+                                                 hist, aux);
         count_launches(1);
         uint32_t *t;
         t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
     }
-    if (status) {
-        k_os_status<<<1, 1, 0, s>>>(aux, status);
+    if (status || kept_out) {
+        k_os_finish<<<1, 1, 0, s>>>(aux, status, kept_out);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -419,8 +438,9 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
     if (counters[CNT_PAIRS] > cap) return;   // capacity exceeded: the host reports it (uniform)
     const uint64_t j0 = (uint64_t)blockIdx.x * 256;
     const uint64_t j = j0 + threadIdx.x;
+    const uint64_t V = min(M, counters[CNT_VISIBLE]);   // entries in depth order with at least one pair
     uint32_t e = 0, tt = 0, rows = 0, rx = 0, ry = 0, tbase = 0, tx = 1;
-    if (j < M) {
+    if (j < V) {
         e = sorted_ent[j];
         tt = tiles_touched[e];
         if (tt) {

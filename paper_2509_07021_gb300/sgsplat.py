@@ -125,6 +125,8 @@ def lib():
         L.sg_render_backward.restype = ctypes.c_int
         L.sg_profile_enable.argtypes = [ctypes.c_int]
         L.sg_profile_enable.restype = ctypes.c_int
+        L.sg_profile_set_stages.argtypes = [ctypes.c_uint32]
+        L.sg_profile_set_stages.restype = ctypes.c_int
         L.sg_profile_read.argtypes = [_P, _P, _P, ctypes.c_int]
         L.sg_profile_read.restype = ctypes.c_int
         L.sg_render_backward_noalloc.argtypes = [ctypes.POINTER(sg_scene), ctypes.POINTER(sg_camera),
@@ -352,6 +354,11 @@ def sg_render_backward(scene: DeviceScene, cams, ws, T_final, last, d_img, bwd_w
 
 def sg_profile_enable(flags: int):
     _check(lib().sg_profile_enable(int(flags)))
+
+
+def sg_profile_set_stages(stage_mask: int):
+    """Bit i: stage i is bracketed by events when SG_PROFILE_EVENTS is on (default all)."""
+    _check(lib().sg_profile_set_stages(ctypes.c_uint32(stage_mask & 0xFFFFFFFF)))
 
 
 def sg_profile_stage_name(i: int):

@@ -200,7 +200,8 @@ def test_tuning_rejects_bad_shapes():
         sgsplat.sg_set_tuning(3, 4)
     sgsplat.sg_set_tuning()
     t = sgsplat.sg_get_tuning()
-    assert t["fwd_pixels_per_thread"] == 1 and t["bwd_pixels_per_thread"] == 4
+    assert (t["fwd_pixels_per_thread"], t["bwd_pixels_per_thread"], t["fwd_persistent"],
+            t["bwd_persistent"]) == (1, 8, 0, 1)
 
 
 def test_capacity_error_and_retry():
