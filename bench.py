@@ -600,7 +600,7 @@ def oracle_errors(scene, cam, images, n_tiles=24, seed=5):
 def run_e2e(args, ds, cams, d_img_np, grads, world):
     """Same metric through the public API with pinned host inputs and outputs:
     every step copies the scene and the upstream gradient host->device and the
-    image and all gradients device->host."""
+    image and all gradients device->host (render.HostStep)."""
     import torch
     from paper_2509_07021_gb300 import render
     from paper_2509_07021_gb300.sgsplat import DeviceScene
@@ -608,22 +608,10 @@ def run_e2e(args, ds, cams, d_img_np, grads, world):
     fields = list(DeviceScene.FLOAT_FIELDS) + ["lobe_off"]
     host_in = {k: getattr(ds, k).cpu().pin_memory() for k in fields}
     host_dimg = torch.from_numpy(d_img_np)[None].pin_memory()
-    dev_dimg = torch.empty_like(host_dimg, device="cuda")
     host_img = torch.empty((1, 3, cams[0].height, cams[0].width), dtype=torch.float32).pin_memory()
     host_grads = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in grads.items()}
-    h2d = sum(t.numel() * t.element_size() for t in host_in.values()) + host_dimg.numel() * 4
-    d2h = host_img.numel() * 4 + sum(t.numel() * 4 for t in host_grads.values())
-
-    def step():
-        for k in fields:
-            getattr(ds, k).copy_(host_in[k], non_blocking=True)
-        dev_dimg.copy_(host_dimg, non_blocking=True)
-        out = render.render_forward(ds, cams)
-        render.render_backward(ds, cams, out, dev_dimg, grads)
-        host_img.copy_(out.img, non_blocking=True)
-        for k, v in grads.items():
-            host_grads[k].copy_(v, non_blocking=True)
-        torch.cuda.synchronize()
+    step = render.HostStep(ds, cams, host_in, host_dimg, host_img, host_grads)
+    h2d, d2h = step.bytes_moved()
 
     for _ in range(max(1, args.warmup)):
         step()

@@ -87,6 +87,56 @@ def render_backward(scene: DeviceScene, cams, fwd: ForwardOut, d_img, grads=None
     return grads
 
 
+class HostStep:
+    """One forward + backward of a scene whose parameters and upstream gradient
+    live in pinned host memory, with the image and every gradient copied back
+    (a host-side training or serving loop).
+
+    Copies that do not gate the next kernel overlap with it on a second stream:
+    the upstream gradient goes up while the forward runs and the image comes
+    down while the backward runs. The scene's parameters go up before the
+    forward and the gradients come down after the backward, on the caller's
+    stream; __call__ returns once everything is back on the host.
+    """
+
+    def __init__(self, scene: DeviceScene, cams, host_scene: dict, host_d_img, host_img, host_grads: dict):
+        self.scene, self.cams = scene, cams
+        self.host_scene, self.host_d_img = host_scene, host_d_img
+        self.host_img, self.host_grads = host_img, host_grads
+        dev = scene.means.device
+        self.d_img = torch.empty(host_d_img.shape, dtype=host_d_img.dtype, device=dev)
+        self.grads = alloc_grads(scene)
+        self.side = torch.cuda.Stream(device=dev)
+
+    def bytes_moved(self):
+        up = sum(t.numel() * t.element_size() for t in self.host_scene.values())
+        up += self.host_d_img.numel() * self.host_d_img.element_size()
+        down = self.host_img.numel() * self.host_img.element_size()
+        down += sum(t.numel() * t.element_size() for t in self.host_grads.values())
+        return up, down
+
+    def __call__(self):
+        main = torch.cuda.current_stream()
+        for k, t in self.host_scene.items():
+            getattr(self.scene, k).copy_(t, non_blocking=True)
+        self.side.wait_stream(main)
+        with torch.cuda.stream(self.side):
+            self.d_img.copy_(self.host_d_img, non_blocking=True)
+            d_img_ready = self.side.record_event()
+        out = render_forward(self.scene, self.cams)
+        self.side.wait_stream(main)
+        with torch.cuda.stream(self.side):
+            self.host_img.copy_(out.img.view(self.host_img.shape), non_blocking=True)
+        out.img.record_stream(self.side)
+        main.wait_event(d_img_ready)
+        render_backward(self.scene, self.cams, out, self.d_img, self.grads)
+        for k, t in self.host_grads.items():
+            t.copy_(self.grads[k], non_blocking=True)
+        main.synchronize()
+        self.side.synchronize()
+        return self.host_img, self.host_grads
+
+
 class SGRasterize(torch.autograd.Function):
     """img, T_final, last = SGRasterize.apply(means, scales, quats, opac, gmask, c0,
     lobe_off, axis, sharp, amp, lmask, cams)
