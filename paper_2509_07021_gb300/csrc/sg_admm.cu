@@ -96,7 +96,7 @@ static AdmmLayout admm_layout(int64_t n) {
     L.k1 = take(4 * (size_t)n);
     L.v1 = take(4 * (size_t)n);
     const uint64_t hb = div_up((uint64_t)n, RS_TILE);
-    L.hist = take((size_t)RS_RADIX * hb * 4);
+    L.hist = take((size_t)4 * RS_RADIX * hb * 4);   // look-back flags of the 4 passes
     L.sums = take(std::max<size_t>((div_up((uint64_t)n, SCAN_TILE) + div_up((uint64_t)RS_RADIX * hb, SCAN_TILE) + 1) * 8,
                                    SORT_AUX_BYTES));
     L.total = o;

@@ -264,7 +264,7 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     L.pkey_tmp = take(cap * 4);
     const uint64_t items = std::max<uint64_t>(std::max<uint64_t>(M, cap), T);
     L.hist_blocks = (uint32_t)div_up(items, RS_TILE);
-    L.hist = take((size_t)RS_RADIX * L.hist_blocks * 4);
+    L.hist = take((size_t)4 * RS_RADIX * L.hist_blocks * 4);   // look-back flags of up to 4 passes
     const uint64_t sums = div_up(items, SCAN_TILE) + div_up((uint64_t)RS_RADIX * L.hist_blocks, SCAN_TILE) + 1;
     L.scan_sums = take(std::max<size_t>(sums * 8, SORT_AUX_BYTES));
     L.total = o;

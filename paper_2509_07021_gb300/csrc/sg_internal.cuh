@@ -196,7 +196,8 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 // from *n_dev and clamped to max_n (the capacity the launch is sized for, below
 // 2^30). Ping-pongs between (k0,v0) and (k1,v1); the sorted result ends in
 // (k0,v0) when the pass count is even, else in (k1,v1).
-// hist: RS_RADIX x ceil(max_n / RS_TILE) words of look-back flags; aux: at least
+// hist: 4 x RS_RADIX x ceil(max_n / RS_TILE) words of look-back flags (one region
+// per pass, zeroed by the sort itself); aux: at least
 // SORT_AUX_BYTES; status (nullable): set to SG_ERR_TIMEOUT if a look-back gave up.
 // kept_out (nullable): drop mode — keys equal to SORT_DROP_KEY are left out, the
 // sorted kept keys fill positions [0, *kept_out) and *kept_out receives their count.

@@ -172,7 +172,6 @@ constexpr int LB_WINDOW = 16;
 
 struct SortAux {
     uint32_t hist[4][RS_RADIX];   // global digit counts per pass
-    uint32_t base[4][RS_RADIX];   // exclusive digit bases per pass
     uint32_t tile_ctr[4];         // tile counter per pass
     uint32_t status;              // 0 or SG_ERR_TIMEOUT
     uint32_t pad;
@@ -194,10 +193,15 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
 // with few distinct digits (the high tile bits) from serialising.
 __global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint32_t *__restrict__ keys,
                                                         const uint64_t *__restrict__ n_dev, uint64_t max_n,
-                                                        int bits, bool drop, SortAux *aux) {
+                                                        int bits, bool drop, SortAux *aux,
+                                                        uint32_t *__restrict__ flags, uint64_t flag_words) {
     constexpr int NW = RS_THREADS / 32;
     __shared__ uint32_t h[NW][4][RS_RADIX];
     const int passes = radix_passes_dev(bits);
+    // the look-back flags of every pass start at zero (the passes run after this kernel)
+    for (uint64_t i = (uint64_t)blockIdx.x * RS_THREADS + threadIdx.x; i < flag_words;
+         i += (uint64_t)gridDim.x * RS_THREADS)
+        flags[i] = 0u;
     const int warp = threadIdx.x >> 5;
     for (int w = 0; w < NW; ++w)
         for (int p = 0; p < 4; ++p) h[w][p][threadIdx.x] = 0u;
@@ -224,15 +228,6 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint32_t *__restri
         uint32_t c = 0u;
         for (int w = 0; w < NW; ++w) c += h[w][p][threadIdx.x];
         if (c) atomicAdd(&aux->hist[p][threadIdx.x], c);
-    }
-}
-
-__global__ void __launch_bounds__(RS_RADIX) k_os_base(SortAux *aux, int passes) {
-    __shared__ uint32_t sh[33];
-    for (int p = 0; p < passes; ++p) {
-        uint32_t tot;
-        const uint32_t ex = block_exclusive<uint32_t>(aux->hist[p][threadIdx.x], tot, sh);
-        aux->base[p][threadIdx.x] = ex;
     }
 }
 
@@ -333,10 +328,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_pass(
         }
     }
     st_relaxed(my, LB_INC | ((excl + run) & LB_VAL));
-    uint32_t tot;
+    uint32_t tot, all;
     const uint32_t ds = block_exclusive<uint32_t>(run, tot, shs);
+    // global start of digit d in this pass: keys of smaller digits (all tiles) + earlier tiles
+    const uint32_t dbase = block_exclusive<uint32_t>(aux->hist[pass][d], all, shs);
     dstart[d] = ds;
-    gstart[d] = aux->base[pass][d] + excl;
+    gstart[d] = dbase + excl;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
@@ -378,20 +375,18 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
     if (e != cudaSuccess) return e;
     const unsigned hgrid = nblocks < 4u * 152u ? nblocks : 4u * 152u;
     const bool drop = kept_out != nullptr;
-    k_os_hist<<<hgrid, RS_THREADS, 0, s>>>(k0, n_dev, max_n, bits, drop, aux);
-    k_os_base<<<1, RS_RADIX, 0, s>>>(aux, passes);
-    count_launches(2);
+    const uint64_t pass_words = (uint64_t)nblocks * RS_RADIX;
+    k_os_hist<<<hgrid, RS_THREADS, 0, s>>>(k0, n_dev, max_n, bits, drop, aux, hist, pass_words * passes);
+    count_launches(1);
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         const int nb = min(8, bits - shift);
         const uint32_t mask = (1u << nb) - 1u;
-        e = cudaMemsetAsync(hist, 0, (size_t)nblocks * RS_RADIX * sizeof(uint32_t), s);
-        if (e != cudaSuccess) return e;
         // with drop, pass 0 leaves SORT_DROP_KEY out and later passes see only the kept keys
         const uint64_t *np = (drop && p > 0) ? &aux->kept : n_dev;
         k_os_pass<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, np, max_n, p, shift, mask, drop && p == 0,
-                                                 hist, aux);
+                                                 hist + pass_words * p, aux);
         count_launches(1);
         uint32_t *t;
         t = ki; ki = ko; ko = t;
