@@ -267,6 +267,7 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     L.hist = take((size_t)4 * RS_RADIX * L.hist_blocks * 4);   // look-back flags of up to 4 passes
     const uint64_t sums = div_up(items, SCAN_TILE) + div_up((uint64_t)RS_RADIX * L.hist_blocks, SCAN_TILE) + 1;
     L.scan_sums = take(std::max<size_t>(sums * 8, SORT_AUX_BYTES));
+    L.aux_tile = take(SORT_AUX_BYTES);
     L.total = o;
     L.M = M;
     L.n_tiles = T;
@@ -389,9 +390,18 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     const uint64_t M = L.M;
 
     const bool counting = (prof().flags & SG_PROFILE_COUNT) != 0;
+    uint64_t *aux_tile = reinterpret_cast<uint64_t *>(w + L.aux_tile);
     {
+        // the setup kernel also clears the tile ranges and both sorts' scratch
+        ZeroRegions z;
+        z.ptr[0] = reinterpret_cast<uint32_t *>(ranges);
+        z.words[0] = 2 * L.n_tiles;
+        z.ptr[1] = reinterpret_cast<uint32_t *>(sums);
+        z.words[1] = SORT_AUX_BYTES / 4;
+        z.ptr[2] = reinterpret_cast<uint32_t *>(aux_tile);
+        z.words[2] = SORT_AUX_BYTES / 4;
         StageTimer t(ST_SETUP, stream);
-        SG_CUDA(launch_setup(b, db, counters, stream), "setup");
+        SG_CUDA(launch_setup(b, db, counters, stream, z), "setup");
     }
     {
         StageTimer t(ST_PRE, stream);
@@ -402,7 +412,7 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         StageTimer t(ST_DEPTH_SORT, stream);
         // entries that reach no tile carry the drop key and are left out of the order
         SG_CUDA(launch_radix_sort(dkey0, dval0, dkey1, dval1, counters + CNT_ENTRIES, M, 32, hist, sums,
-                                  stream, counters + CNT_STATUS, counters + CNT_VISIBLE),
+                                  stream, counters + CNT_STATUS, counters + CNT_VISIBLE, true),
                 "depth sort");
     }
     {
@@ -446,8 +456,8 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     }
     {
         StageTimer t(ST_TILE_SORT, stream);
-        SG_CUDA(launch_radix_sort(k0, v0, k1, v1, counters + CNT_PAIRS, K, L.tile_bits, hist, sums, stream,
-                                  counters + CNT_STATUS),
+        SG_CUDA(launch_radix_sort(k0, v0, k1, v1, counters + CNT_PAIRS, K, L.tile_bits, hist, aux_tile, stream,
+                                  counters + CNT_STATUS, nullptr, true),
                 "tile sort");
     }
     {

@@ -92,7 +92,7 @@ constexpr int SCAN_TILE = 4096;
 // forward and the backward of one call).
 struct WsLayout {
     size_t batch, counters, rec, tiles_touched, rect, dkey0, dval0, dkey1, dval1,
-        offsets, ranges, tok0, tov0, tok1, tov1, scan_sums, hist, fixed_end;
+        offsets, ranges, tok0, tov0, tok1, tov1, scan_sums, hist, aux_tile, fixed_end;
     size_t pval_final, pkey_final, pval_tmp, pkey_tmp, total;
     uint64_t M, n_tiles, cap;
     uint32_t hist_blocks;     // radix blocks of the larger sort
@@ -178,7 +178,14 @@ __device__ __forceinline__ void tile_reach_row(const TileReach &R, int ty, int x
 void count_launches(int n);
 
 // ---- launchers (host side, defined in the .cu files) ----
-cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStream_t s);
+// Up to N device regions of 32-bit words that the setup kernel zeroes.
+struct ZeroRegions {
+    static constexpr int N = 3;
+    uint32_t *ptr[N] = {nullptr, nullptr, nullptr};
+    uint64_t words[N] = {0, 0, 0};
+};
+cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStream_t s,
+                         const ZeroRegions &z = ZeroRegions());
 cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32_t *tiles_touched,
                               uint2 *rect, uint32_t *dkey, uint32_t *dval, cudaStream_t s);
 cudaError_t launch_preprocess_backward(const Batch &hb, const Batch *db,
@@ -203,16 +210,18 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 // sorted kept keys fill positions [0, *kept_out) and *kept_out receives their count.
 constexpr size_t SORT_AUX_BYTES = 16384;
 constexpr uint32_t SORT_DROP_KEY = 0xFFFFFFFFu;
+// aux_zeroed: the caller has already zeroed the aux region in this stream.
 cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
                               uint64_t *aux, cudaStream_t s, uint64_t *status = nullptr,
-                              uint64_t *kept_out = nullptr);
+                              uint64_t *kept_out = nullptr, bool aux_zeroed = false);
 int radix_passes(int bits);
 
 cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,
                              const uint32_t *tiles_touched, const uint2 *rect, const Rec *rec,
                              const uint32_t *offsets, const uint64_t *counters, uint64_t cap,
                              uint32_t *pkey, uint32_t *pval, int n_views, cudaStream_t s);
+// ranges must be zero on entry (the forward's setup kernel clears them).
 cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64_t cap,
                           uint2 *ranges, uint64_t n_tiles, cudaStream_t s);
 // Tiles sorted by descending list length into v0 (k0..v1: n_tiles each).

@@ -13,6 +13,8 @@
 // scene input and writes the sums (no atomics).
 #include "sg_internal.cuh"
 
+#include <cstring>
+
 namespace sgk {
 
 // ---------------------------------------------------------------------------
@@ -196,31 +198,58 @@ __device__ __forceinline__ int find_block_scene(const Batch &b, uint32_t blk) {
 // ---------------------------------------------------------------------------
 // setup: copy the batch table into the workspace, seed the counters
 // ---------------------------------------------------------------------------
-__global__ void k_setup(const Batch b, Batch *dst, uint64_t *counters) {
-    // header and the used views / scenes only
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(&b);
+// The batch table travels as a kernel parameter sized for the call: the header,
+// then NV views and NS scenes (only the used ones are copied on the host).
+template <int NV, int NS>
+struct BatchParam {
+    unsigned char head[offsetof(Batch, view)];
+    ViewDesc view[NV];
+    SceneDesc scene[NS];
+};
+static_assert(offsetof(Batch, view) % 8 == 0, "batch header");
+
+// Writes the table into the workspace, zeroes the counters and the regions the
+// caller names (e.g. tile ranges, sort scratch), and seeds the entry and tile
+// counts. One block.
+template <int NV, int NS>
+__global__ void __launch_bounds__(256) k_setup(const BatchParam<NV, NS> p, Batch *dst, uint64_t *counters,
+                                               ZeroRegions z) {
+    const Batch &hb = *reinterpret_cast<const Batch *>(p.head);   // header fields only
+    const int n_views = hb.n_views, n_scenes = hb.n_scenes;
     uint32_t *d = reinterpret_cast<uint32_t *>(dst);
-    const int head = (int)(offsetof(Batch, view) / 4);
-    const int vw0 = head, vw1 = (int)((offsetof(Batch, view) + b.n_views * sizeof(ViewDesc)) / 4);
-    const int sc0 = (int)(offsetof(Batch, scene) / 4);
-    const int sc1 = (int)((offsetof(Batch, scene) + b.n_scenes * sizeof(SceneDesc)) / 4);
-    for (int i = threadIdx.x; i < head; i += blockDim.x) d[i] = src[i];
-    for (int i = vw0 + threadIdx.x; i < vw1; i += blockDim.x) d[i] = src[i];
-    for (int i = sc0 + threadIdx.x; i < sc1; i += blockDim.x) d[i] = src[i];
+    const uint32_t *ph = reinterpret_cast<const uint32_t *>(p.head);
+    for (int i = threadIdx.x; i < (int)(offsetof(Batch, view) / 4); i += blockDim.x) d[i] = ph[i];
+    const uint32_t *pv = reinterpret_cast<const uint32_t *>(p.view);
+    uint32_t *dv = reinterpret_cast<uint32_t *>(&dst->view[0]);
+    for (int i = threadIdx.x; i < (int)(n_views * sizeof(ViewDesc) / 4); i += blockDim.x) dv[i] = pv[i];
+    const uint32_t *ps = reinterpret_cast<const uint32_t *>(p.scene);
+    uint32_t *ds = reinterpret_cast<uint32_t *>(&dst->scene[0]);
+    for (int i = threadIdx.x; i < (int)(n_scenes * sizeof(SceneDesc) / 4); i += blockDim.x) ds[i] = ps[i];
+    for (int r = 0; r < ZeroRegions::N; ++r)
+        for (uint64_t i = threadIdx.x; i < z.words[r]; i += blockDim.x) z.ptr[r][i] = 0u;
     if (threadIdx.x < CNT_N) counters[threadIdx.x] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
-        counters[CNT_ENTRIES] = b.n_entries;
-        counters[CNT_TILES] = b.n_tiles;
+        counters[CNT_ENTRIES] = hb.n_entries;
+        counters[CNT_TILES] = hb.n_tiles;
     }
 }
 
-cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStream_t s) {
-    static_assert(sizeof(Batch) % 4 == 0, "batch size");
-    static_assert(sizeof(Batch) < 32000, "batch must fit the kernel parameter space");
-    k_setup<<<1, 256, 0, s>>>(b, dst, counters);
+template <int NV, int NS>
+static cudaError_t setup_t(const Batch &b, Batch *dst, uint64_t *counters, const ZeroRegions &z, cudaStream_t s) {
+    BatchParam<NV, NS> p;
+    std::memcpy(p.head, &b, sizeof(p.head));
+    std::memcpy(p.view, b.view, (size_t)b.n_views * sizeof(ViewDesc));
+    std::memcpy(p.scene, b.scene, (size_t)b.n_scenes * sizeof(SceneDesc));
+    k_setup<NV, NS><<<1, 256, 0, s>>>(p, dst, counters, z);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStream_t s, const ZeroRegions &z) {
+    static_assert(sizeof(BatchParam<SG_MAX_VIEWS, SG_MAX_SCENES>) < 32000, "batch must fit the kernel parameters");
+    if (b.n_views <= 4 && b.n_scenes <= 2) return setup_t<4, 2>(b, dst, counters, z, s);
+    return setup_t<SG_MAX_VIEWS, SG_MAX_SCENES>(b, dst, counters, z, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -365,14 +365,17 @@ __global__ void k_os_finish(const SortAux *aux, uint64_t *status, uint64_t *kept
 
 cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
-                              uint64_t *scan_sums, cudaStream_t s, uint64_t *status, uint64_t *kept_out) {
+                              uint64_t *scan_sums, cudaStream_t s, uint64_t *status, uint64_t *kept_out,
+                              bool aux_zeroed) {
     const uint32_t nblocks = (uint32_t)div_up(max_n, RS_TILE);
     const int passes = radix_passes(bits);
     if (nblocks == 0 || passes == 0) return cudaSuccess;
     if (max_n > (uint64_t)LB_VAL) return cudaErrorInvalidValue;   // counts must fit the look-back word
     SortAux *aux = reinterpret_cast<SortAux *>(scan_sums);
-    cudaError_t e = cudaMemsetAsync(aux, 0, sizeof(SortAux), s);
-    if (e != cudaSuccess) return e;
+    if (!aux_zeroed) {
+        const cudaError_t e = cudaMemsetAsync(aux, 0, sizeof(SortAux), s);
+        if (e != cudaSuccess) return e;
+    }
     const unsigned hgrid = nblocks < 4u * 152u ? nblocks : 4u * 152u;
     const bool drop = kept_out != nullptr;
     const uint64_t pass_words = (uint64_t)nblocks * RS_RADIX;
@@ -530,8 +533,6 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ pke
 
 cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64_t cap, uint2 *ranges,
                           uint64_t n_tiles, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(ranges, 0, n_tiles * sizeof(uint2), s);
-    if (e != cudaSuccess) return e;
     if (cap == 0) return cudaSuccess;
     k_ranges<<<(unsigned)div_up(cap, 256), 256, 0, s>>>(pkey, counters, cap, ranges, n_tiles);
     count_launches(1);
