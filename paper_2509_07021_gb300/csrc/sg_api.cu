@@ -102,7 +102,7 @@ struct StageTimer {
 };
 
 // Process-wide kernel shape choices (sg_set_tuning); defaults from measurement.
-constexpr sg_tuning kDefaultTuning = {1, 8, 0, 1, {0, 0, 0, 0}};
+constexpr sg_tuning kDefaultTuning = {2, 8, 0, 1, {0, 0, 0, 0}};
 sg_tuning &tuning() {
     static sg_tuning t = kDefaultTuning;
     return t;

@@ -36,7 +36,10 @@ __device__ __forceinline__ int find_tile_view(const Batch &b, uint32_t t) {
 // with (qa, qb, qc) = -log2(e) * (A/2, B, C/2), so that
 //   power * log2(e) = qa dx^2 + qb dx dy + qc dy^2   and   exp(power) = 2^(that).
 constexpr float LOG2E = 1.4426950408889634f;
-constexpr int BATCH = 256;   // Gaussians staged per shared-memory batch
+#ifndef SG_FWD_BATCH
+#define SG_FWD_BATCH 64
+#endif
+constexpr int BATCH = SG_FWD_BATCH;   // Gaussians staged per shared-memory batch (forward)
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -56,7 +59,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
 #define SG_BWD_BATCH 128
 #endif
 constexpr int BWD_BATCH = SG_BWD_BATCH;
-static_assert(BWD_BATCH % 32 == 0 && BWD_BATCH <= BATCH, "backward batch");
+static_assert(BWD_BATCH % 32 == 0 && BWD_BATCH <= 256, "backward batch");
+static_assert(BATCH % 32 == 0 && BATCH <= 1024, "forward batch");
 // Minimum resident blocks requested for the 8-pixels-per-thread backward.
 #ifndef SG_BWD8_MIN_BLOCKS
 #define SG_BWD8_MIN_BLOCKS 20
