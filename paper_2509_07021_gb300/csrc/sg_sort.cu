@@ -209,15 +209,26 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint32_t *__restri
     const uint64_t n = min(*n_dev, max_n);
     const uint64_t stride = (uint64_t)gridDim.x * RS_THREADS;
     uint32_t kept = 0u;
-    for (uint64_t j = (uint64_t)blockIdx.x * RS_THREADS + threadIdx.x; j < n; j += stride) {
-        const uint32_t k = keys[j];
-        if (drop && k == SORT_DROP_KEY) continue;
+    auto count = [&](uint32_t k) {
+        if (drop && k == SORT_DROP_KEY) return;
         ++kept;
         for (int p = 0; p < passes; ++p) {
             const int nb = min(8, bits - 8 * p);
             atomicAdd(&h[warp][p][(k >> (8 * p)) & ((1u << nb) - 1u)], 1u);
         }
+    };
+    // four keys per 16-byte load (the key arrays are 256-byte aligned), then the tail
+    const uint64_t n4 = n / 4;
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);
+    for (uint64_t j = (uint64_t)blockIdx.x * RS_THREADS + threadIdx.x; j < n4; j += stride) {
+        const uint4 q = k4[j];
+        count(q.x);
+        count(q.y);
+        count(q.z);
+        count(q.w);
     }
+    for (uint64_t j = 4 * n4 + (uint64_t)blockIdx.x * RS_THREADS + threadIdx.x; j < n; j += stride)
+        count(keys[j]);
     if (drop) {
         const uint32_t wk = __reduce_add_sync(0xffffffffu, kept);
         if ((threadIdx.x & 31) == 0 && wk)
