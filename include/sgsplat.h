@@ -167,8 +167,7 @@ typedef struct sg_sizes {
  *                 reach 1/255, 2 ln(255 o') 1.01 + 0.01, negative if o' < 1/255)
  *                 (x, y: projected centre in pixel-index coordinates; conic
  *                 (A, B, C) = inverse of the dilated 2D covariance; o' = m_g o;
- *                 rgb = max(c(v), 0), stored as -0 where c(v) < 0 so that the
- *                 backward reads the clamp back; radius = ceil(3 sqrt(lambda_max)); depth =
+ *                 rgb = max(c(v), 0); radius = ceil(3 sqrt(lambda_max)); depth =
  *                 camera-space z). Valid where rect is not empty.
  *   tiles_touched [M] uint32: tiles of rect whose pixel-centre box meets the
  *                 (slightly enlarged) ellipse where alpha can reach 1/255;

@@ -246,6 +246,7 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     L.rec = take(M * sizeof(Rec));
     L.tiles_touched = take(M * 4);
     L.rect = take(M * 8);
+    L.clamp = take(M);
     L.dkey0 = take(M * 4);
     L.dval0 = take(M * 4);
     L.dkey1 = take(M * 4);
@@ -405,7 +406,9 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     }
     {
         StageTimer t(ST_PRE, stream);
-        SG_CUDA(launch_preprocess(b, db, rec, tt, rect, dkey0, dval0, stream), "preprocessSG");
+        SG_CUDA(launch_preprocess(b, db, rec, tt, rect, dkey0, dval0, reinterpret_cast<uint8_t *>(w + L.clamp),
+                                  stream),
+                "preprocessSG");
     }
     {
         // depth digits, once per entry (result back in dkey0/dval0 after 4 passes)
@@ -563,7 +566,7 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
     }
     {
         StageTimer t(ST_PRE_BWD, stream);
-        SG_CUDA(launch_preprocess_backward(b, db, tt, rec, dg, M, stream), "preprocess backward");
+        SG_CUDA(launch_preprocess_backward(b, db, tt, reinterpret_cast<const uint8_t *>(w + L.clamp), dg, M, stream), "preprocess backward");
     }
     if (counting) {
         uint64_t ne = 0;
@@ -930,6 +933,6 @@ extern "C" int sg_render_backward_noalloc(const sg_scene *scene, const sg_camera
     SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M, shape,
                                   nullptr, stream),
             "blend backward");
-    SG_CUDA(launch_preprocess_backward(b, db, tt, rec, dg, M, stream), "preprocess backward");
+    SG_CUDA(launch_preprocess_backward(b, db, tt, reinterpret_cast<const uint8_t *>(w + L.clamp), dg, M, stream), "preprocess backward");
     return SG_OK;
 }

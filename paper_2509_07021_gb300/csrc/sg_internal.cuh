@@ -91,7 +91,7 @@ constexpr int SCAN_TILE = 4096;
 // Byte offsets of every workspace buffer (host computed, identical for the
 // forward and the backward of one call).
 struct WsLayout {
-    size_t batch, counters, rec, tiles_touched, rect, dkey0, dval0, dkey1, dval1,
+    size_t batch, counters, rec, tiles_touched, rect, clamp, dkey0, dval0, dkey1, dval1,
         offsets, ranges, tok0, tov0, tok1, tov1, scan_sums, hist, aux_tile, fixed_end;
     size_t pval_final, pkey_final, pval_tmp, pkey_tmp, total;
     uint64_t M, n_tiles, cap;
@@ -186,10 +186,11 @@ struct ZeroRegions {
 };
 cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStream_t s,
                          const ZeroRegions &z = ZeroRegions());
+// clamp [M]: bit ch set where colour channel ch was clamped by max(c, 0)
 cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32_t *tiles_touched,
-                              uint2 *rect, uint32_t *dkey, uint32_t *dval, cudaStream_t s);
+                              uint2 *rect, uint32_t *dkey, uint32_t *dval, uint8_t *clamp, cudaStream_t s);
 cudaError_t launch_preprocess_backward(const Batch &hb, const Batch *db,
-                                       const uint32_t *tiles_touched, const Rec *rec, const float *dg,
+                                       const uint32_t *tiles_touched, const uint8_t *clamp, const float *dg,
                                        uint64_t M, cudaStream_t s);
 
 // Exclusive scan of `in` (or of tiles_touched[idx[i]] when idx != null) into

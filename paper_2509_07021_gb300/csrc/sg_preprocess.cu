@@ -309,18 +309,14 @@ __device__ __forceinline__ void sh3_grad_acc(float x, float y, float z, const fl
     gx += -SH_C3A * (3.f * xx - 3.f * yy) * w[15]; gy += 6.f * SH_C3A * x * y * w[15];
 }
 
-// max(c, 0) as the blend sees it, with the clamp recorded in the sign: c where
-// c >= 0, -0 where c < 0 (or NaN). The backward reads the sign back instead of
-// recomputing the colour.
-__device__ __forceinline__ float clamp_keep_sign(float c) { return c >= 0.f ? fabsf(c) : -0.0f; }
-
 // ---------------------------------------------------------------------------
 // K1 preprocessSG
 // ---------------------------------------------------------------------------
 template <int DG, int DL, int DS, int CM>
 __global__ void __launch_bounds__(PRE_THREADS)
 k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__restrict__ tiles_touched,
-             uint2 *__restrict__ rect, uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
+             uint2 *__restrict__ rect, uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
+             uint8_t *__restrict__ clamp) {
     const Batch &b = *bp;
     const int v = find_block_view(b, blockIdx.x);
     const ViewDesc &vw = b.view[v];
@@ -376,9 +372,11 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
     }
     Rec r;
     r.a = make_float4(G.x, G.y, G.conA, G.conB);
-    r.b = make_float4(G.conC, G.op, clamp_keep_sign(cr), clamp_keep_sign(cg));
+    r.b = make_float4(G.conC, G.op, fmaxf(cr, 0.f), fmaxf(cg, 0.f));
+    // channels clamped by max(c, 0) (not c >= 0, NaN included): the backward reads these bits
+    clamp[e] = (uint8_t)((cr >= 0.f ? 0u : 1u) | (cg >= 0.f ? 0u : 2u) | (cbl >= 0.f ? 0u : 4u));
     const float reach_t = tile_reach_threshold(G.op);
-    r.c = make_float4(clamp_keep_sign(cbl), G.rf, G.tz, reach_t);
+    r.c = make_float4(fmaxf(cbl, 0.f), G.rf, G.tz, reach_t);
     rec[e] = r;
     // tiles of the rectangle that the alpha >= 1/255 ellipse reaches
     TileReach R;
@@ -397,29 +395,29 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
 
 template <int DG, int DL, int DS, int CM = SG_COLOR_SG>
 static cudaError_t launch_pre_t(const Batch &hb, const Batch *db, Rec *rec, uint32_t *tt, uint2 *rect,
-                                uint32_t *dkey, uint32_t *dval, cudaStream_t s) {
+                                uint32_t *dkey, uint32_t *dval, uint8_t *clamp, cudaStream_t s) {
     if (hb.pre_blocks == 0) return cudaSuccess;
-    k_preprocess<DG, DL, DS, CM><<<hb.pre_blocks, PRE_THREADS, 0, s>>>(db, rec, tt, rect, dkey, dval);
+    k_preprocess<DG, DL, DS, CM><<<hb.pre_blocks, PRE_THREADS, 0, s>>>(db, rec, tt, rect, dkey, dval, clamp);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32_t *tiles_touched,
-                              uint2 *rect, uint32_t *dkey, uint32_t *dval, cudaStream_t s) {
+                              uint2 *rect, uint32_t *dkey, uint32_t *dval, uint8_t *clamp, cudaStream_t s) {
     // all scenes of one call share storage types (checked by the API layer)
     const SceneDesc &sc = hb.scene[0];
     const int key = sc.dtype_geom * 9 + sc.dtype_lobe * 3 + sc.dtype_sharp;
     if (sc.color_model == SG_COLOR_SH3) {
         if (key != SG_F32 * 9 + SG_F32 * 3 + SG_F32) return cudaErrorInvalidValue;
-        return launch_pre_t<SG_F32, SG_F32, SG_F32, SG_COLOR_SH3>(hb, db, rec, tiles_touched, rect, dkey, dval, s);
+        return launch_pre_t<SG_F32, SG_F32, SG_F32, SG_COLOR_SH3>(hb, db, rec, tiles_touched, rect, dkey, dval, clamp, s);
     }
     switch (key) {
         case SG_F32 * 9 + SG_F32 * 3 + SG_F32:
-            return launch_pre_t<SG_F32, SG_F32, SG_F32>(hb, db, rec, tiles_touched, rect, dkey, dval, s);
+            return launch_pre_t<SG_F32, SG_F32, SG_F32>(hb, db, rec, tiles_touched, rect, dkey, dval, clamp, s);
         case SG_F16 * 9 + SG_F16 * 3 + SG_F16:
-            return launch_pre_t<SG_F16, SG_F16, SG_F16>(hb, db, rec, tiles_touched, rect, dkey, dval, s);
+            return launch_pre_t<SG_F16, SG_F16, SG_F16>(hb, db, rec, tiles_touched, rect, dkey, dval, clamp, s);
         case SG_F16 * 9 + SG_F16 * 3 + SG_BF16:
-            return launch_pre_t<SG_F16, SG_F16, SG_BF16>(hb, db, rec, tiles_touched, rect, dkey, dval, s);
+            return launch_pre_t<SG_F16, SG_F16, SG_BF16>(hb, db, rec, tiles_touched, rect, dkey, dval, clamp, s);
         default:
             return cudaErrorInvalidValue;
     }
@@ -438,7 +436,7 @@ cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32
 template <int DG, int DL, int DS, int CM>
 __global__ void __launch_bounds__(PRE_THREADS, SG_PRE_BWD_MIN_BLOCKS)
 k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tiles_touched,
-                 const Rec *__restrict__ rec, const float *__restrict__ dg, uint64_t M) {
+                 const uint8_t *__restrict__ clamp, const float *__restrict__ dg, uint64_t M) {
     const Batch &b = *bp;
     const int si = find_block_scene(b, blockIdx.x);
     const SceneDesc &sc = b.scene[si];
@@ -466,12 +464,10 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
         const float gx = dg[e], gy = dg[M + e], gA = dg[2 * M + e], gB = dg[3 * M + e],
                     gC = dg[4 * M + e], gop = dg[5 * M + e];
         const float grgb[3] = {dg[6 * M + e], dg[7 * M + e], dg[8 * M + e]};
-        const float4 rb = rec[e].b;
-        const float rcb = rec[e].c.x;
+        const uint32_t cl = clamp[e];
         if (tte == 0u) continue;
-        // the forward's clamp max(c, 0), read back from the sign of its record
-        const float gc[3] = {signbit(rb.z) ? 0.f : grgb[0], signbit(rb.w) ? 0.f : grgb[1],
-                             signbit(rcb) ? 0.f : grgb[2]};
+        // the forward's clamp max(c, 0) per channel, read back from its bits
+        const float gc[3] = {(cl & 1u) ? 0.f : grgb[0], (cl & 2u) ? 0.f : grgb[1], (cl & 4u) ? 0.f : grgb[2]};
 
         // o' = m_g * o
         d_opac += gm * gop;
@@ -674,29 +670,29 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
 }
 
 template <int DG, int DL, int DS, int CM = SG_COLOR_SG>
-static cudaError_t launch_bwd_t(const Batch &hb, const Batch *db, const uint32_t *tt, const Rec *rec,
+static cudaError_t launch_bwd_t(const Batch &hb, const Batch *db, const uint32_t *tt, const uint8_t *clamp,
                                 const float *dg, uint64_t M, cudaStream_t s) {
     if (hb.bwd_blocks == 0) return cudaSuccess;
-    k_preprocess_bwd<DG, DL, DS, CM><<<hb.bwd_blocks, PRE_THREADS, 0, s>>>(db, tt, rec, dg, M);
+    k_preprocess_bwd<DG, DL, DS, CM><<<hb.bwd_blocks, PRE_THREADS, 0, s>>>(db, tt, clamp, dg, M);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_preprocess_backward(const Batch &hb, const Batch *db, const uint32_t *tiles_touched,
-                                       const Rec *rec, const float *dg, uint64_t M, cudaStream_t s) {
+                                       const uint8_t *clamp, const float *dg, uint64_t M, cudaStream_t s) {
     const SceneDesc &sc = hb.scene[0];
     const int key = sc.dtype_geom * 9 + sc.dtype_lobe * 3 + sc.dtype_sharp;
     if (sc.color_model == SG_COLOR_SH3) {
         if (key != SG_F32 * 9 + SG_F32 * 3 + SG_F32) return cudaErrorInvalidValue;
-        return launch_bwd_t<SG_F32, SG_F32, SG_F32, SG_COLOR_SH3>(hb, db, tiles_touched, rec, dg, M, s);
+        return launch_bwd_t<SG_F32, SG_F32, SG_F32, SG_COLOR_SH3>(hb, db, tiles_touched, clamp, dg, M, s);
     }
     switch (key) {
         case SG_F32 * 9 + SG_F32 * 3 + SG_F32:
-            return launch_bwd_t<SG_F32, SG_F32, SG_F32>(hb, db, tiles_touched, rec, dg, M, s);
+            return launch_bwd_t<SG_F32, SG_F32, SG_F32>(hb, db, tiles_touched, clamp, dg, M, s);
         case SG_F16 * 9 + SG_F16 * 3 + SG_F16:
-            return launch_bwd_t<SG_F16, SG_F16, SG_F16>(hb, db, tiles_touched, rec, dg, M, s);
+            return launch_bwd_t<SG_F16, SG_F16, SG_F16>(hb, db, tiles_touched, clamp, dg, M, s);
         case SG_F16 * 9 + SG_F16 * 3 + SG_BF16:
-            return launch_bwd_t<SG_F16, SG_F16, SG_BF16>(hb, db, tiles_touched, rec, dg, M, s);
+            return launch_bwd_t<SG_F16, SG_F16, SG_BF16>(hb, db, tiles_touched, clamp, dg, M, s);
         default:
             return cudaErrorInvalidValue;
     }
