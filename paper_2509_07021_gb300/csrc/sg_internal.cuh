@@ -117,14 +117,42 @@ struct TileReach {
     int mode;   // 0: reaches nothing, 1: ellipse, 2: whole rectangle (degenerate conic)
 };
 
+// The tile binning is a decision recipe like cull and rectangle: every step is
+// one binary32 operation with round-to-nearest (no contraction), so that the
+// FP64 oracle, repeating it in numpy float32, gets the same tiles. Its
+// constants are exact binary32 values (hexadecimal literals).
+constexpr float TR_C7 = 0x1.24924ap-3f;      // 1/7
+constexpr float TR_C5 = 0x1.99999ap-3f;      // 1/5
+constexpr float TR_C3 = 0x1.555556p-2f;      // 1/3
+constexpr float TR_INV_LN2 = 0x1.715476p+0f; // 1/ln 2
+constexpr float TR_LN2X2 = 0x1.62e430p+0f;   // 2 ln 2
+constexpr float TR_GROW = 0x1.028f5cp+0f;    // 1.01
+constexpr float TR_ADD = 0x1.47ae14p-7f;     // 0.01
+constexpr float TR_PAD = 0x1.47ae14p-6f;     // 0.02 px
+
+// log2 of a positive normal x: exponent plus ln(m) / ln 2 for the mantissa
+// m in [1, 2), ln m = 2 atanh(s) with s = (m - 1) / (m + 1) <= 1/3, summed to
+// s^7 (relative error below 1e-5, far inside the 1 % enlargement below).
+__device__ __forceinline__ float log2_recipe(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const float e = (float)((int)((u >> 23) & 255u) - 127);
+    const float m = __uint_as_float((u & 0x007FFFFFu) | 0x3F800000u);
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float s2 = __fmul_rn(s, s);
+    float P = __fadd_rn(__fmul_rn(s2, TR_C7), TR_C5);
+    P = __fadd_rn(__fmul_rn(P, s2), TR_C3);
+    P = __fadd_rn(__fmul_rn(P, s2), 1.0f);
+    const float lnm = __fmul_rn(__fmul_rn(2.0f, s), P);
+    return __fadd_rn(e, __fmul_rn(lnm, TR_INV_LN2));
+}
+
 // Enlarged bound on q where alpha can reach 1/255: 2 ln(255 o') (1 + 1 %) + 0.01;
 // negative when o' < 1/255 (alpha <= o' < 1/255 everywhere). Computed once per
-// entry by preprocess and kept in its record, so that the count and the
-// enumeration of tiles start from the same binary32 value.
+// entry by preprocess and kept in its record.
 __device__ __forceinline__ float tile_reach_threshold(float op) {
     if (!(op >= 1.0f / 255.0f)) return -1.0f;
-    const float t0 = 2.0f * logf(__fmul_rn(255.0f, op));
-    return __fadd_rn(__fmul_rn(t0, 1.01f), 0.01f);
+    const float t0 = __fmul_rn(TR_LN2X2, log2_recipe(__fmul_rn(255.0f, op)));
+    return __fadd_rn(__fmul_rn(t0, TR_GROW), TR_ADD);
 }
 
 __device__ __forceinline__ void tile_reach_init(float x, float y, float A, float B, float C, float t,
@@ -154,7 +182,7 @@ __device__ __forceinline__ void tile_reach_row(const TileReach &R, int ty, int x
     c0 = c1 = x0;
     if (R.mode == 0) return;
     if (R.mode == 2) { c1 = x1; return; }
-    const float pad = 0.02f;
+    const float pad = TR_PAD;
     float lo = __fsub_rn(__fsub_rn((float)(ty * SG_TILE), R.y), pad);
     float hi = __fadd_rn(__fsub_rn((float)(ty * SG_TILE + SG_TILE - 1), R.y), pad);
     lo = fmaxf(lo, -R.ymax);
