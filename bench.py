@@ -245,13 +245,104 @@ def oracle_sample(scene, cam, d_img, n_tiles, seed=0):
 
 
 def cpu_baseline_line(scene, cam, d_img, n_tiles):
+    """The oracle on the host cores: all cores (the reported value), then one
+    thread on a smaller sample, then the small forward-only workload in full."""
+    import oracle
+    import torch
     total, est_full, threads = oracle_sample(scene, cam, d_img, n_tiles)
     mpx = cam.width * cam.height / 1e6
-    return {"value": mpx / est_full, "unit": UNIT, "cores": threads, "kind": "oracle",
+    line = {"value": mpx / est_full, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": (f"FP64 oracle: full-frame preprocess + tile sort, forward+backward blend on "
                        f"{n_tiles} of {cam.n_tiles} random tiles ({total:.1f} s wall), blend time "
                        f"scaled to the frame; {threads} OpenMP threads for the blend, numpy/torch "
                        f"for the rest")}
+    torch_threads = torch.get_num_threads()
+    try:
+        oracle.set_num_threads(1)
+        torch.set_num_threads(1)
+        n1 = max(4, n_tiles // 4)
+        total1, est1, _ = oracle_sample(scene, cam, d_img, n1, seed=1)
+        line["single_thread"] = {"value": mpx / est1, "unit": UNIT, "cores": 1,
+                                 "sample": f"same, {n1} random tiles, one thread ({total1:.1f} s wall)"}
+    finally:
+        oracle.set_num_threads(threads)
+        torch.set_num_threads(torch_threads)
+    from paper_2509_07021_gb300 import synth
+    s0, c0 = synth.config0()
+    t0 = time.perf_counter()
+    oracle.render_forward(s0, c0[0])
+    dt = time.perf_counter() - t0
+    line["small_forward"] = {"ms_per_view": 1e3 * dt, "workload": "1,000 Gaussians x 3 lobes, 128x128, "
+                             "forward only, whole frame", "cores": threads}
+    return line
+
+
+def gpu_errors_vs_oracle(scene, cam, d_img, storages=("f32", "f16_bf16s"), n_tiles=24, seed=5):
+    """Image max / mean abs error and per-tensor gradient relative L2 of the GPU
+    forms against the FP64 oracle on a sample of tiles: the upstream gradient is
+    d_img on those tiles (zero elsewhere and at the oracle's ambiguous pixels),
+    and the oracle is fed the original binary32 scene (so the half-storage
+    numbers include the storage rounding)."""
+    import oracle
+    import torch
+    from paper_2509_07021_gb300 import render
+    from paper_2509_07021_gb300.sgsplat import DeviceScene
+    sel = np.zeros(cam.n_tiles, bool)
+    sel[np.random.default_rng(seed).choice(cam.n_tiles, n_tiles, replace=False)] = True
+    res = oracle.render_forward(scene, cam, tile_sel=sel, need_grad=True)
+    m = np.repeat(np.repeat(sel.reshape(cam.tiles_y, cam.tiles_x), 16, 0), 16, 1)
+    m = m[:cam.height, :cam.width] & ~res.ambiguous
+    dimg = (d_img * m[None]).astype(np.float32)
+    g_orc = oracle.render_backward(res, scene, cam, dimg)
+    out = {}
+    for storage in storages:
+        ds = DeviceScene.from_host(scene, storage=storage)
+        fwd = render.render_forward(ds, [cam])
+        g = render.render_backward(ds, [cam], fwd, torch.from_numpy(dimg)[None].cuda())
+        torch.cuda.synchronize()
+        img = fwd.img[0].cpu().numpy()
+        err = np.abs(img - res.img)[:, m]
+        rel = {}
+        for k, ref in g_orc.items():
+            got = g[k].cpu().numpy().astype(np.float64)
+            nr = np.linalg.norm(ref)
+            if ref.size and nr > 0:
+                rel[k] = float(np.linalg.norm(got - ref) / nr)
+        out[storage] = {"img_max_abs": float(err.max()), "img_mean_abs": float(err.mean()),
+                        "pixels": int(m.sum()), "grad_rel_l2_max": max(rel.values()), "grad_rel_l2": rel}
+        del ds, fwd, g
+    return out
+
+
+def stage_rooflines(stages_ms, counts, evals, hbm_gbs):
+    """Achieved fraction of roofline for every stage: algorithmic bytes (HBM
+    stages) or flops (blend) per step over the stage's event time per step.
+    counts: N Gaussians, L lobes, M entries, V entries with pairs, K pairs, T tiles."""
+    N, L, M, V, K, T = (counts[k] for k in ("N", "L", "M", "V", "K", "T"))
+    by = {
+        "preprocess": 64 * N + 32 * L + 69 * M,                 # params in; record, tt, rect, clamp, key, value out
+        "depth_sort": 4 * M + 8 * M + 8 * V + 3 * 16 * V,       # histogram, pass 0 (drops), passes 1-3
+        "pair_offsets": 12 * V,                                 # sorted id + tt in, offset out
+        "duplicate": 64 * V + 8 * K,                            # id, tt, rect, record in; pairs out
+        "tile_sort": 4 * K + 2 * 16 * K,                        # histogram, two passes
+        "tile_ranges": 4 * K + 8 * T,
+        "bwd_clear": 36 * M,
+        "preprocess_bwd": 64 * N + 32 * L + 41 * M + 60 * N + 32 * L,
+    }
+    out = {}
+    for k, ms in stages_ms.items():
+        if ms <= 0:
+            continue
+        if k in FLOPS_PER_EVAL:
+            ev = evals["forward" if k == "blend_fwd" else "backward"]
+            a = ev * FLOPS_PER_EVAL[k] / (ms / 1e3) / 1e12
+            out[k] = {"bound": "alu", "achieved": round(a, 2), "unit": "TFLOP/s",
+                      "frac": round(a / FP32_PEAK_TFLOPS, 3)}
+        elif k in by:
+            a = by[k] / (ms / 1e3) / 1e9
+            out[k] = {"bound": "hbm", "achieved": round(a, 1), "unit": "GB/s", "frac": round(a / hbm_gbs, 3),
+                      "bytes": int(by[k])}
+    return out
 
 
 def run_reference(args, world, rank):
@@ -393,6 +484,19 @@ def run_ours(args, world, rank, local):
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
                 "frac": None, "traffic": recorded_traffic(dom), "avg_ms": avg_ms}
 
+    # ---- every stage against its roofline (stage times from the breakdown pass) ----
+    lay = sgsplat.sg_workspace_layout(ds, cams, out.ws.numel())
+    M = out.sizes["n_entries"]
+    tt = out.ws[lay["tiles_touched"]:lay["tiles_touched"] + 4 * M].view(torch.int32)
+    counts = {"N": scene.n, "L": scene.n_lobes, "M": M, "V": int((tt != 0).sum().item()),
+              "K": n_pairs, "T": cam.n_tiles}
+    hbm_peak = 6800.0
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        pass
+    kernel_roofs = stage_rooflines(stages_ms, counts, evals, hbm_peak)
+
     # ---- end to end through the public API with host buffers ----
     e2e = run_e2e(args, ds, cams, d_img_np, grads, world)
 
@@ -406,12 +510,13 @@ def run_ours(args, world, rank, local):
             "gpu_launches": int(launches),
             "stages_ms_per_step": stages_ms,
             "stage_share": share,
+            "kernel_rooflines": {"counts": counts, "hbm_peak_gbs": hbm_peak, "stages": kernel_roofs},
             "pair_evals": evals}
     if world == 1 and not args.no_forms:
         forms = run_forms(args, scene, cams, d_img, flush, max(3, args.steps // 2))
-        images = forms.pop("_images")
+        forms.pop("_images")
         if not args.no_cpu_baseline:
-            errs = oracle_errors(scene, cam, images)
+            errs = gpu_errors_vs_oracle(scene, cam, d_img_np)
             forms["plain_f32"]["vs_oracle"] = errs["f32"]
             forms["plain_f16_bf16s"]["vs_oracle"] = errs["f16_bf16s"]
         line["forms"] = forms
@@ -578,23 +683,6 @@ def run_forms(args, scene, cams, d_img, flush, steps):
         del br, dss, plain_grads, targets
         torch.cuda.empty_cache()
     return forms
-
-
-def oracle_errors(scene, cam, images, n_tiles=24, seed=5):
-    """Max / mean abs image error of the GPU forms against the FP64 oracle on
-    a sample of tiles (oracle fed the original binary32 scene, so the FP16
-    number includes the storage rounding)."""
-    import oracle
-    sel = np.zeros(cam.n_tiles, bool)
-    sel[np.random.default_rng(seed).choice(cam.n_tiles, n_tiles, replace=False)] = True
-    res = oracle.render_forward(scene, cam, tile_sel=sel)
-    m = np.repeat(np.repeat(sel.reshape(cam.tiles_y, cam.tiles_x), 16, 0), 16, 1)
-    m = m[:cam.height, :cam.width] & ~res.ambiguous
-    out = {}
-    for k, img in images.items():
-        err = np.abs(img - res.img)[:, m]
-        out[k] = {"max_abs": float(err.max()), "mean_abs": float(err.mean()), "pixels": int(m.sum())}
-    return out
 
 
 def run_e2e(args, ds, cams, d_img_np, grads, world):

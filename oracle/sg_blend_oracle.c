@@ -366,3 +366,14 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads the blend loops use from now on (n >= 1). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -68,6 +68,8 @@ def lib():
         L.orc_set_bands.restype = None
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = I
+        L.orc_set_num_threads.argtypes = [I]
+        L.orc_set_num_threads.restype = None
         _LIB = L
     return _LIB
 
@@ -584,3 +586,8 @@ def set_bands(alpha=2e-5, T=5e-5, power=1e-6):
 
 def num_threads():
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n):
+    """Threads of the C blend loops (OpenMP) from now on."""
+    lib().orc_set_num_threads(int(n))
