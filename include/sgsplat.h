@@ -237,6 +237,24 @@ typedef struct sg_tuning {
 int sg_set_tuning(const sg_tuning *t);
 int sg_get_tuning(sg_tuning *t);
 
+/*
+ * Autotuner: times every blend shape (pixels per thread 1, 2, 4, 8, one block
+ * per tile or persistent) on this workload with the caller's buffers (the
+ * arguments of sg_render_forward and sg_render_backward; the workspace must
+ * already be large enough, else the forward's SG_ERR_CAPACITY is returned).
+ * Each candidate runs one untimed forward + backward, then `reps` (1..100)
+ * timed ones (CUDA events on `stream`, synchronised here). The forward and the
+ * backward each take their fastest shape; the choice is installed as by
+ * sg_set_tuning and written to *chosen. times_ms (nullable, 16 floats) receives
+ * the mean forward times of candidates c = 0..7 (P = 2^(c/2), persistent =
+ * c % 2), then their mean backward times. The outputs and gradients hold the
+ * last call's results. On an error the previous tuning is restored.
+ */
+int sg_autotune(const sg_scene *scene, const sg_camera *cams, int n_views, void *ws, size_t ws_bytes,
+                float *img, float *T_final, int32_t *last, const float *d_img, void *bwd_ws,
+                size_t bwd_ws_bytes, const sg_grads *grads, int reps, sg_tuning *chosen, float *times_ms,
+                void *stream);
+
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t sg_kernel_launches(void);
 /* Name of stage i ("preprocess", "depth_sort", ..., "preprocess_bwd"); NULL if out of range. */

@@ -705,6 +705,77 @@ int sg_render_backward(const sg_scene *scene, const sg_camera *cams, int n_views
                          bwd_ws_bytes, grads, static_cast<cudaStream_t>(stream));
 }
 
+// Times every blend shape (pixels per thread 1, 2, 4, 8; one block per tile or
+// persistent) on the caller's workload: each candidate runs `reps` forward and
+// backward calls after one untimed pair; the forward and the backward pick
+// their fastest shape independently (only the blend kernels differ between
+// candidates, so whole-call times rank them). The choice is installed with
+// sg_set_tuning and written to *chosen; times_ms (nullable) receives [2][8]
+// mean milliseconds, forward then backward, candidate c = 2 * log2(P) + persistent.
+int sg_autotune(const sg_scene *scene, const sg_camera *cams, int n_views, void *ws, size_t ws_bytes,
+                float *img, float *T_final, int32_t *last, const float *d_img, void *bwd_ws,
+                size_t bwd_ws_bytes, const sg_grads *grads, int reps, sg_tuning *chosen, float *times_ms,
+                void *stream) {
+    g_err[0] = '\0';
+    if (!chosen) return fail(SG_ERR_INVALID_ARG, "chosen must not be NULL");
+    if (reps < 1 || reps > 100) return fail(SG_ERR_INVALID_ARG, "reps = %d out of [1, 100]", reps);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const sg_tuning saved = tuning();
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            for (auto &x : ev) if (x) cudaEventDestroy(x);
+            return cuda_fail(cudaGetLastError(), "autotune events");
+        }
+    float best_f = 1e30f, best_b = 1e30f;
+    int bf = 0, bb = 0;
+    int st = SG_OK;
+    for (int c = 0; c < 8 && st == SG_OK; ++c) {
+        sg_tuning t = saved;
+        t.fwd_pixels_per_thread = t.bwd_pixels_per_thread = 1 << (c >> 1);
+        t.fwd_persistent = t.bwd_persistent = c & 1;
+        tuning() = t;
+        float tf = 0.f, tb = 0.f;
+        for (int r = 0; r <= reps && st == SG_OK; ++r) {
+            sg_sizes sz{};
+            cudaEventRecord(ev[0], s);
+            st = forward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, img, T_final, last, nullptr, &sz, s,
+                              true);
+            if (st != SG_OK) break;
+            cudaEventRecord(ev[1], s);
+            st = backward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, T_final, last, d_img, bwd_ws,
+                               bwd_ws_bytes, grads, s);
+            if (st != SG_OK) break;
+            cudaEventRecord(ev[2], s);
+            const cudaError_t e = cudaEventSynchronize(ev[2]);
+            if (e != cudaSuccess) { st = cuda_fail(e, "autotune"); break; }
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[0], ev[1]);
+            cudaEventElapsedTime(&b, ev[1], ev[2]);
+            if (r > 0) { tf += a; tb += b; }   // the first pair is untimed
+        }
+        if (st != SG_OK) break;
+        tf /= (float)reps;
+        tb /= (float)reps;
+        if (times_ms) { times_ms[c] = tf; times_ms[8 + c] = tb; }
+        if (tf < best_f) { best_f = tf; bf = c; }
+        if (tb < best_b) { best_b = tb; bb = c; }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st != SG_OK) {
+        tuning() = saved;
+        return st;
+    }
+    sg_tuning t = saved;
+    t.fwd_pixels_per_thread = 1 << (bf >> 1);
+    t.fwd_persistent = bf & 1;
+    t.bwd_pixels_per_thread = 1 << (bb >> 1);
+    t.bwd_persistent = bb & 1;
+    tuning() = t;
+    *chosen = t;
+    return SG_OK;
+}
+
 int sg_batched_workspace_query(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
                                const int32_t *view_scene, int n_views, uint64_t pair_capacity, sg_sizes *out) {
     if (!out) return fail(SG_ERR_INVALID_ARG, "out must not be NULL");

@@ -123,6 +123,10 @@ def lib():
                                          ctypes.c_int, _P, ctypes.c_size_t, _P, _P, _P, _P,
                                          ctypes.c_size_t, ctypes.POINTER(sg_grads), _P]
         L.sg_render_backward.restype = ctypes.c_int
+        L.sg_autotune.argtypes = [ctypes.POINTER(sg_scene), ctypes.POINTER(sg_camera), ctypes.c_int,
+                                  _P, ctypes.c_size_t, _P, _P, _P, _P, _P, ctypes.c_size_t,
+                                  ctypes.POINTER(sg_grads), ctypes.c_int, ctypes.POINTER(sg_tuning), _P, _P]
+        L.sg_autotune.restype = ctypes.c_int
         L.sg_profile_enable.argtypes = [ctypes.c_int]
         L.sg_profile_enable.restype = ctypes.c_int
         L.sg_profile_set_stages.argtypes = [ctypes.c_uint32]
@@ -350,6 +354,24 @@ def sg_render_backward(scene: DeviceScene, cams, ws, T_final, last, d_img, bwd_w
     _check(lib().sg_render_backward(ctypes.byref(s), c, len(cams), _ptr(ws), ws.numel(),
                                     _ptr(T_final), _ptr(last), _ptr(d_img), _ptr(bwd_ws),
                                     bwd_ws.numel(), ctypes.byref(g), _stream_handle(stream)))
+
+
+def sg_autotune(scene: DeviceScene, cams, ws, img, T_final, last, d_img, bwd_ws, grads: dict, reps=3,
+                stream=None) -> dict:
+    """Times every blend shape on this workload and installs the fastest (see
+    sgsplat.h). Returns the choice and the per-candidate mean times (ms)."""
+    s = scene.struct()
+    c = camera_array(cams)
+    g = grads_struct(grads)
+    t = sg_tuning()
+    times = (ctypes.c_float * 16)()
+    _check(lib().sg_autotune(ctypes.byref(s), c, len(cams), _ptr(ws), ws.numel(), _ptr(img), _ptr(T_final),
+                             _ptr(last), _ptr(d_img), _ptr(bwd_ws), bwd_ws.numel(), ctypes.byref(g),
+                             int(reps), ctypes.byref(t), ctypes.cast(times, _P), _stream_handle(stream)))
+    names = [f"p{1 << (k >> 1)}" + ("_persistent" if k & 1 else "") for k in range(8)]
+    return {"fwd_pixels_per_thread": t.fwd_pixels_per_thread, "bwd_pixels_per_thread": t.bwd_pixels_per_thread,
+            "fwd_persistent": t.fwd_persistent, "bwd_persistent": t.bwd_persistent,
+            "ms": {names[k]: {"fwd_call": times[k], "bwd_call": times[8 + k]} for k in range(8)}}
 
 
 def sg_profile_enable(flags: int):
