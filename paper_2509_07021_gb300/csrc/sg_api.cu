@@ -253,10 +253,7 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     L.dval1 = take(M * 4);
     L.offsets = take(M * 4);
     L.ranges = take(T * 8);
-    L.tok0 = take(T * 4);
-    L.tov0 = take(T * 4);
-    L.tok1 = take(T * 4);
-    L.tov1 = take(T * 4);
+    L.order = take(T * 4);
     L.fixed_end = o;
     // pair-capacity dependent tail; the backward only reads pval_final
     L.pval_final = take(cap * 4);
@@ -291,7 +288,7 @@ uint64_t capacity_for(const Batch &b, size_t ws_bytes) {
 // Backward scratch: batch table, counters, [9][M] 2D gradients, then the
 // persistent blend's tile order (4 x T) and its radix histograms.
 struct BwdLayout {
-    size_t batch, counters, dg, tok0, tov0, tok1, tov1, hist, sums, total;
+    size_t batch, counters, dg, order, sums, total;
 };
 
 BwdLayout bwd_layout(const Batch &b) {
@@ -302,14 +299,8 @@ BwdLayout bwd_layout(const Batch &b) {
     L.batch = take(sizeof(Batch));
     L.counters = take(CNT_N * sizeof(uint64_t));
     L.dg = take(9 * b.n_entries * sizeof(float));
-    L.tok0 = take(T * 4);
-    L.tov0 = take(T * 4);
-    L.tok1 = take(T * 4);
-    L.tov1 = take(T * 4);
-    const uint64_t hb = div_up(T, RS_TILE);
-    L.hist = take((size_t)RS_RADIX * hb * 4);
-    L.sums = take(std::max<size_t>((div_up(T, SCAN_TILE) + div_up((uint64_t)RS_RADIX * hb, SCAN_TILE) + 1) * 8,
-                                   SORT_AUX_BYTES));
+    L.order = take(T * 4);
+    L.sums = take(2 * 256 * 4);   // tile-order bucket counters
     L.total = o;
     return L;
 }
@@ -471,7 +462,7 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         counting ? reinterpret_cast<unsigned long long *>(counters + CNT_EVALS) : nullptr;
     if (counting) SG_CUDA(cudaMemsetAsync(evals, 0, 8, stream), "clear counter");
     BlendShape shape{};
-    st = blend_shape(false, reinterpret_cast<uint32_t *>(w + L.tov0),
+    st = blend_shape(false, reinterpret_cast<uint32_t *>(w + L.order),
                      reinterpret_cast<uint32_t *>(counters + CNT_QUEUE), shape);
     if (st != SG_OK) return st;
     shape.importance = want_importance && !counting;
@@ -482,9 +473,8 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
                         "clear importance");
     if (shape.persistent) {
         StageTimer t(ST_RANGES, stream);
-        SG_CUDA(launch_tile_order(ranges, b.n_tiles, counters + CNT_TILES, reinterpret_cast<uint32_t *>(w + L.tok0),
-                                  reinterpret_cast<uint32_t *>(w + L.tov0), reinterpret_cast<uint32_t *>(w + L.tok1),
-                                  reinterpret_cast<uint32_t *>(w + L.tov1), hist, sums, stream),
+        SG_CUDA(launch_tile_order(ranges, b.n_tiles, reinterpret_cast<uint32_t *>(w + L.order),
+                                  reinterpret_cast<uint32_t *>(sums), stream),
                 "tile order");
     }
     {
@@ -539,7 +529,7 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
     unsigned long long *evals =
         counting ? reinterpret_cast<unsigned long long *>(counters + CNT_EVALS) : nullptr;
     BlendShape shape{};
-    st = blend_shape(true, reinterpret_cast<uint32_t *>(bw + BL.tov0),
+    st = blend_shape(true, reinterpret_cast<uint32_t *>(bw + BL.order),
                      reinterpret_cast<uint32_t *>(counters + CNT_QUEUE), shape);
     if (st != SG_OK) return st;
     {
@@ -552,10 +542,8 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
     }
     if (shape.persistent) {
         StageTimer t(ST_BWD_CLEAR, stream);
-        SG_CUDA(launch_tile_order(ranges, b.n_tiles, counters + CNT_TILES, reinterpret_cast<uint32_t *>(bw + BL.tok0),
-                                  reinterpret_cast<uint32_t *>(bw + BL.tov0), reinterpret_cast<uint32_t *>(bw + BL.tok1),
-                                  reinterpret_cast<uint32_t *>(bw + BL.tov1), reinterpret_cast<uint32_t *>(bw + BL.hist),
-                                  reinterpret_cast<uint64_t *>(bw + BL.sums), stream),
+        SG_CUDA(launch_tile_order(ranges, b.n_tiles, reinterpret_cast<uint32_t *>(bw + BL.order),
+                                  reinterpret_cast<uint32_t *>(bw + BL.sums), stream),
                 "tile order");
     }
     {

@@ -92,7 +92,7 @@ constexpr int SCAN_TILE = 4096;
 // forward and the backward of one call).
 struct WsLayout {
     size_t batch, counters, rec, tiles_touched, rect, clamp, dkey0, dval0, dkey1, dval1,
-        offsets, ranges, tok0, tov0, tok1, tov1, scan_sums, hist, aux_tile, fixed_end;
+        offsets, ranges, order, scan_sums, hist, aux_tile, fixed_end;
     size_t pval_final, pkey_final, pval_tmp, pkey_tmp, total;
     uint64_t M, n_tiles, cap;
     uint32_t hist_blocks;     // radix blocks of the larger sort
@@ -253,10 +253,10 @@ cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted
 // ranges must be zero on entry (the forward's setup kernel clears them).
 cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64_t cap,
                           uint2 *ranges, uint64_t n_tiles, cudaStream_t s);
-// Tiles sorted by descending list length into v0 (k0..v1: n_tiles each).
-cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, const uint64_t *n_tiles_dev,
-                              uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
-                              uint64_t *scan_sums, cudaStream_t s);
+// Tiles by descending list length (256 length buckets) into order[n_tiles];
+// scratch: 512 words.
+cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *scratch,
+                              cudaStream_t s);
 // counters[CNT_STATUS] = SG_ERR_CAPACITY when the pairs exceed cap.
 cudaError_t launch_capacity_status(uint64_t *counters, uint64_t cap, cudaStream_t s);
 

@@ -592,18 +592,16 @@ __global__ void __launch_bounds__(256) k_tile_bucket_scatter(const uint2 *__rest
     }
 }
 
-cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, const uint64_t *n_tiles_dev,
-                              uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
-                              uint64_t *scan_sums, cudaStream_t s) {
-    (void)n_tiles_dev; (void)k0; (void)k1; (void)v1; (void)hist;
+cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *scratch,
+                              cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
-    uint32_t *counts = reinterpret_cast<uint32_t *>(scan_sums), *cursor = counts + TB_BUCKETS;
+    uint32_t *counts = scratch, *cursor = scratch + TB_BUCKETS;
     cudaError_t e = cudaMemsetAsync(counts, 0, 2 * TB_BUCKETS * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const uint64_t want = div_up(n_tiles, 256);
     const unsigned grid = (unsigned)(want < 608u ? want : 608u);
     k_tile_bucket_count<<<grid, 256, 0, s>>>(ranges, n_tiles, counts);
-    k_tile_bucket_scatter<<<grid, 256, 0, s>>>(ranges, n_tiles, counts, cursor, v0);
+    k_tile_bucket_scatter<<<grid, 256, 0, s>>>(ranges, n_tiles, counts, cursor, order);
     count_launches(2);
     return cudaGetLastError();
 }
