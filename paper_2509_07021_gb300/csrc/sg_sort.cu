@@ -154,16 +154,17 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort, 8-bit digits, 4096 keys per block, one sweep per pass
+// stable LSD radix sort, 8-bit digits, RS_TILE keys per block, one sweep per pass
 // ---------------------------------------------------------------------------
-// One kernel histograms every digit position at once; a second turns them into
-// per-pass digit bases. Each pass is then a single kernel: blocks take key
+// One kernel histograms every digit position at once (and clears the look-back
+// flags of every pass). Each pass is then a single kernel: blocks take key
 // tiles in order from an atomic counter, rank their keys stably (warp
-// match_any + per-warp digit counters), publish their digit counts, and get
-// their global offsets by looking back over the tiles before them (decoupled
-// look-back). A look-back spin is bounded: past the bound the block records
-// SG_ERR_TIMEOUT in the status word and carries on with a wrong offset
-// instead of waiting forever.
+// match_any + per-warp digit counters), scan the pass's digit histogram for
+// the digit bases, publish their digit counts, and get their offsets among
+// the tiles before them by looking back (decoupled look-back). A look-back
+// spin is bounded: past the bound the block records SG_ERR_TIMEOUT in the
+// status word and carries on with a smaller offset (wrong order, still inside
+// the array) instead of waiting forever.
 
 // packed look-back word: 2 status bits, 30 count bits
 constexpr uint32_t LB_AGG = 1u << 30, LB_INC = 2u << 30, LB_VAL = (1u << 30) - 1u;
