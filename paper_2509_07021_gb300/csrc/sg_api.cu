@@ -182,7 +182,7 @@ int build_batch(const sg_scene *scenes, int n_scenes, const sg_camera *cams, con
         d.blk_off = (uint32_t)bwd_blk;
         bwd_blk += div_up((uint64_t)sc.n, PRE_THREADS);
     }
-    uint64_t tiles = 0, pix = 0, ent = 0, blk = 0;
+    uint64_t tiles = 0, pix = 0, ent = 0;
     for (int v = 0; v < n_views; ++v) {
         const sg_camera &c = cams[v];
         const int s = view_scene ? view_scene[v] : 0;
@@ -211,22 +211,25 @@ int build_batch(const sg_scene *scenes, int n_scenes, const sg_camera *cams, con
         d.scene = s;
         d.n = (int32_t)scenes[s].n;
         d.tile_off = (uint32_t)tiles;
-        d.blk_off = (uint32_t)blk;
         d.pix_off = pix;
         d.ent_off = ent;
         tiles += (uint64_t)d.tiles_x * d.tiles_y;
         pix += (uint64_t)c.width * c.height;
         ent += (uint64_t)scenes[s].n;
-        blk += div_up((uint64_t)scenes[s].n, PRE_THREADS);
     }
     if (tiles >= (1ull << 31)) return fail(SG_ERR_INVALID_ARG, "too many tiles (%llu)", (unsigned long long)tiles);
     if (ent >= (1ull << 32) - 1)
         return fail(SG_ERR_INVALID_ARG, "too many (view, Gaussian) entries (%llu)", (unsigned long long)ent);
-    if (blk >= (1ull << 31) || bwd_blk >= (1ull << 31)) return fail(SG_ERR_INVALID_ARG, "too many blocks");
+    if (bwd_blk >= (1ull << 31)) return fail(SG_ERR_INVALID_ARG, "too many blocks");
     b.n_tiles = (uint32_t)tiles;
     b.n_entries = ent;
-    b.pre_blocks = (uint32_t)blk;
-    b.bwd_blocks = (uint32_t)bwd_blk;
+    b.scene_blocks = (uint32_t)bwd_blk;
+    uint32_t per_scene[SG_MAX_SCENES] = {};
+    b.max_views_per_scene = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const uint32_t c = ++per_scene[b.view[v].scene];
+        b.max_views_per_scene = c > b.max_views_per_scene ? c : b.max_views_per_scene;
+    }
     return SG_OK;
 }
 

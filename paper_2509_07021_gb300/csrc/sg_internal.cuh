@@ -28,7 +28,7 @@ struct ViewDesc {
     int32_t scene;        // index into Batch::scene
     int32_t n;            // Gaussians of that scene
     uint32_t tile_off;    // first global tile id of the view
-    uint32_t blk_off;     // first preprocess block of the view
+    uint32_t pad1;
     uint32_t pad0;
     uint64_t pix_off;     // first pixel of the view in T_final / last (img: x3)
     uint64_t ent_off;     // first (view, Gaussian) entry of the view
@@ -45,14 +45,14 @@ struct SceneDesc {
     sg_grads grads;
     int64_t n, n_lobes;
     int32_t dtype_geom, dtype_lobe, dtype_sharp, color_model;
-    uint32_t blk_off;     // first preprocess-backward block of the scene
+    uint32_t blk_off;     // first block of the scene in the per-Gaussian preprocess grids
 };
 
 struct Batch {
     int32_t n_views, n_scenes;
     uint32_t n_tiles;
-    uint32_t pre_blocks;
-    uint32_t bwd_blocks;
+    uint32_t scene_blocks;   // blocks of 256 scene Gaussians over all scenes
+    uint32_t max_views_per_scene;
     uint32_t pad0;
     uint64_t n_entries;
     ViewDesc view[SG_MAX_VIEWS];

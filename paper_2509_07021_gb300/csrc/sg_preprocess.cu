@@ -177,15 +177,6 @@ __device__ __forceinline__ void load_geo(const SceneDesc &sc, int64_t g, float &
     o = ldp<DG>(sc.opac, g);
 }
 
-__device__ __forceinline__ int find_block_view(const Batch &b, uint32_t blk) {
-    int lo = 0, hi = b.n_views - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (b.view[mid].blk_off <= blk) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ int find_block_scene(const Batch &b, uint32_t blk) {
     int lo = 0, hi = b.n_scenes - 1;
     while (lo < hi) {
@@ -312,22 +303,15 @@ __device__ __forceinline__ void sh3_grad_acc(float x, float y, float z, const fl
 // ---------------------------------------------------------------------------
 // K1 preprocessSG
 // ---------------------------------------------------------------------------
-template <int DG, int DL, int DS, int CM>
-__global__ void __launch_bounds__(PRE_THREADS)
-k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__restrict__ tiles_touched,
-             uint2 *__restrict__ rect, uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
-             uint8_t *__restrict__ clamp) {
-    const Batch &b = *bp;
-    const int v = find_block_view(b, blockIdx.x);
-    const ViewDesc &vw = b.view[v];
-    const SceneDesc &sc = b.scene[vw.scene];
-    const int64_t g = (int64_t)(blockIdx.x - vw.blk_off) * PRE_THREADS + threadIdx.x;
-    if (g >= vw.n) return;
-    const uint64_t e = vw.ent_off + (uint64_t)g;
-
-    float px, py, pz, s0, s1, s2, q0, q1, q2, q3, o;
-    load_geo<DG>(sc, g, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o);
-    const float gm = __ldg(sc.gmask + g);
+// One (view, Gaussian) entry: projection (decision recipe), colour, record and
+// tile binning. The Gaussian's parameters were loaded once by the caller.
+template <int DL, int DS, int CM>
+__device__ __forceinline__ void preprocess_entry(const ViewDesc &vw, const SceneDesc &sc, int64_t g, float px,
+                                                 float py, float pz, float s0, float s1, float s2, float q0,
+                                                 float q1, float q2, float q3, float o, float gm, uint64_t e,
+                                                 Rec *__restrict__ rec, uint32_t *__restrict__ tiles_touched,
+                                                 uint2 *__restrict__ rect, uint32_t *__restrict__ dkey,
+                                                 uint32_t *__restrict__ dval, uint8_t *__restrict__ clamp) {
     Geo G;
     project_recipe(vw, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o, gm, G);
     if (!G.visible) {
@@ -393,11 +377,42 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
     dval[e] = (uint32_t)e;
 }
 
+// One thread per scene Gaussian: its parameters are read once and projected
+// into every view of the call that shows its scene. ONE_VIEW: no scene has
+// more than one view, so the walk stops at the first (the parameters need not
+// stay live across views).
+template <int DG, int DL, int DS, int CM, bool ONE_VIEW>
+__global__ void __launch_bounds__(PRE_THREADS)
+k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__restrict__ tiles_touched,
+             uint2 *__restrict__ rect, uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
+             uint8_t *__restrict__ clamp) {
+    const Batch &b = *bp;
+    const int si = find_block_scene(b, blockIdx.x);
+    const SceneDesc &sc = b.scene[si];
+    const int64_t g = (int64_t)(blockIdx.x - sc.blk_off) * PRE_THREADS + threadIdx.x;
+    if (g >= sc.n) return;
+    float px, py, pz, s0, s1, s2, q0, q1, q2, q3, o;
+    load_geo<DG>(sc, g, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o);
+    const float gm = __ldg(sc.gmask + g);
+    for (int v = 0; v < b.n_views; ++v) {
+        const ViewDesc &vw = b.view[v];
+        if (vw.scene != si) continue;
+        preprocess_entry<DL, DS, CM>(vw, sc, g, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o, gm,
+                                     vw.ent_off + (uint64_t)g, rec, tiles_touched, rect, dkey, dval, clamp);
+        if (ONE_VIEW) break;
+    }
+}
+
 template <int DG, int DL, int DS, int CM = SG_COLOR_SG>
 static cudaError_t launch_pre_t(const Batch &hb, const Batch *db, Rec *rec, uint32_t *tt, uint2 *rect,
                                 uint32_t *dkey, uint32_t *dval, uint8_t *clamp, cudaStream_t s) {
-    if (hb.pre_blocks == 0) return cudaSuccess;
-    k_preprocess<DG, DL, DS, CM><<<hb.pre_blocks, PRE_THREADS, 0, s>>>(db, rec, tt, rect, dkey, dval, clamp);
+    if (hb.scene_blocks == 0) return cudaSuccess;   // one block per 256 scene Gaussians
+    if (hb.max_views_per_scene <= 1)
+        k_preprocess<DG, DL, DS, CM, true><<<hb.scene_blocks, PRE_THREADS, 0, s>>>(db, rec, tt, rect, dkey, dval,
+                                                                                   clamp);
+    else
+        k_preprocess<DG, DL, DS, CM, false><<<hb.scene_blocks, PRE_THREADS, 0, s>>>(db, rec, tt, rect, dkey, dval,
+                                                                                    clamp);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -454,13 +469,17 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
     float d_mean[3] = {0.f, 0.f, 0.f}, d_scale[3] = {0.f, 0.f, 0.f}, d_q[4] = {0.f, 0.f, 0.f, 0.f};
     float d_opac = 0.f, d_gmask = 0.f, d_c0[3] = {0.f, 0.f, 0.f};
     bool first = true;   // first visible view writes lobe gradients, later views add
+    const bool multi_view = b.n_views > 1;
 
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vw = b.view[v];
         if (vw.scene != si) continue;
         const uint64_t e = vw.ent_off + (uint64_t)g;
-        // every load of this view is issued before the visibility test
+        // With one view, every load is issued before the visibility test (the
+        // latency of the test is hidden); with several, most entries reach no
+        // tile and their gradient loads are skipped.
         const uint32_t tte = tiles_touched[e];
+        if (multi_view && tte == 0u) continue;
         const float gx = dg[e], gy = dg[M + e], gA = dg[2 * M + e], gB = dg[3 * M + e],
                     gC = dg[4 * M + e], gop = dg[5 * M + e];
         const float grgb[3] = {dg[6 * M + e], dg[7 * M + e], dg[8 * M + e]};
@@ -672,8 +691,8 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
 template <int DG, int DL, int DS, int CM = SG_COLOR_SG>
 static cudaError_t launch_bwd_t(const Batch &hb, const Batch *db, const uint32_t *tt, const uint8_t *clamp,
                                 const float *dg, uint64_t M, cudaStream_t s) {
-    if (hb.bwd_blocks == 0) return cudaSuccess;
-    k_preprocess_bwd<DG, DL, DS, CM><<<hb.bwd_blocks, PRE_THREADS, 0, s>>>(db, tt, clamp, dg, M);
+    if (hb.scene_blocks == 0) return cudaSuccess;
+    k_preprocess_bwd<DG, DL, DS, CM><<<hb.scene_blocks, PRE_THREADS, 0, s>>>(db, tt, clamp, dg, M);
     count_launches(1);
     return cudaGetLastError();
 }
