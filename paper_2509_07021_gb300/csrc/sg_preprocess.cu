@@ -71,17 +71,15 @@ struct Geo {
     bool visible;
 };
 
-// The binary32 decision recipe. Fills every field of g.
-__device__ __forceinline__ void project_recipe(const ViewDesc &vw, float px, float py, float pz,
-                                               float s0, float s1, float s2, float q0, float q1,
-                                               float q2, float q3, float opac, float gmask,
-                                               Geo &g) {
-    const float *V = vw.V;
-    g.tx = fa(fa(fa(fm(V[0], px), fm(V[1], py)), fm(V[2], pz)), V[3]);
-    g.ty = fa(fa(fa(fm(V[4], px), fm(V[5], py)), fm(V[6], pz)), V[7]);
-    g.tz = fa(fa(fa(fm(V[8], px), fm(V[9], py)), fm(V[10], pz)), V[11]);
-    const bool near_ok = g.tz > vw.near_plane;
+// The view-independent part of the recipe: unit quaternion, rotation R,
+// M = R diag(s) and Sigma_3D = M M^T (computed once per Gaussian for all views).
+struct Geo3 {
+    float qw, qx, qy, qz, invq;
+    float R[3][3], M[3][3], S[3][3];
+};
 
+__device__ __forceinline__ void geo3_recipe(float s0, float s1, float s2, float q0, float q1, float q2,
+                                            float q3, Geo3 &g) {
     const float n2 = fa(fa(fa(fm(q0, q0), fm(q1, q1)), fm(q2, q2)), fm(q3, q3));
     g.invq = fdv(1.f, fsq(n2));
     const float w = fm(q0, g.invq), x = fm(q1, g.invq), y = fm(q2, g.invq), z = fm(q3, g.invq);
@@ -107,6 +105,26 @@ __device__ __forceinline__ void project_recipe(const ViewDesc &vw, float px, flo
             g.S[i][j] = fa(fa(fm(g.M[i][0], g.M[j][0]), fm(g.M[i][1], g.M[j][1])),
                            fm(g.M[i][2], g.M[j][2]));
             g.S[j][i] = g.S[i][j];
+        }
+}
+
+// The binary32 decision recipe for one view, given the Gaussian's Geo3.
+// Fills every field of g.
+__device__ __forceinline__ void project_view(const ViewDesc &vw, float px, float py, float pz, const Geo3 &g3,
+                                             float opac, float gmask, Geo &g) {
+    const float *V = vw.V;
+    g.tx = fa(fa(fa(fm(V[0], px), fm(V[1], py)), fm(V[2], pz)), V[3]);
+    g.ty = fa(fa(fa(fm(V[4], px), fm(V[5], py)), fm(V[6], pz)), V[7]);
+    g.tz = fa(fa(fa(fm(V[8], px), fm(V[9], py)), fm(V[10], pz)), V[11]);
+    const bool near_ok = g.tz > vw.near_plane;
+    g.qw = g3.qw; g.qx = g3.qx; g.qy = g3.qy; g.qz = g3.qz; g.invq = g3.invq;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            g.R[i][j] = g3.R[i][j];
+            g.M[i][j] = g3.M[i][j];
+            g.S[i][j] = g3.S[i][j];
         }
 
     const float fx = vw.fx, fy = vw.fy;
@@ -157,6 +175,16 @@ __device__ __forceinline__ void project_recipe(const ViewDesc &vw, float px, flo
     const bool finite = isfinite(g.x) && isfinite(g.y) && isfinite(g.rf) && isfinite(g.conA) &&
                         isfinite(g.conB) && isfinite(g.conC);
     g.visible = near_ok && det_ok && area_ok && op_ok && finite;
+}
+
+// The whole recipe for one view.
+__device__ __forceinline__ void project_recipe(const ViewDesc &vw, float px, float py, float pz,
+                                               float s0, float s1, float s2, float q0, float q1,
+                                               float q2, float q3, float opac, float gmask,
+                                               Geo &g) {
+    Geo3 g3;
+    geo3_recipe(s0, s1, s2, q0, q1, q2, q3, g3);
+    project_view(vw, px, py, pz, g3, opac, gmask, g);
 }
 
 template <int DG>
@@ -307,13 +335,12 @@ __device__ __forceinline__ void sh3_grad_acc(float x, float y, float z, const fl
 // tile binning. The Gaussian's parameters were loaded once by the caller.
 template <int DL, int DS, int CM>
 __device__ __forceinline__ void preprocess_entry(const ViewDesc &vw, const SceneDesc &sc, int64_t g, float px,
-                                                 float py, float pz, float s0, float s1, float s2, float q0,
-                                                 float q1, float q2, float q3, float o, float gm, uint64_t e,
+                                                 float py, float pz, const Geo3 &g3, float o, float gm, uint64_t e,
                                                  Rec *__restrict__ rec, uint32_t *__restrict__ tiles_touched,
                                                  uint2 *__restrict__ rect, uint32_t *__restrict__ dkey,
                                                  uint32_t *__restrict__ dval, uint8_t *__restrict__ clamp) {
     Geo G;
-    project_recipe(vw, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o, gm, G);
+    project_view(vw, px, py, pz, g3, o, gm, G);
     if (!G.visible) {
         tiles_touched[e] = 0u;
         rect[e] = make_uint2(0u, 0u);
@@ -394,11 +421,13 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
     float px, py, pz, s0, s1, s2, q0, q1, q2, q3, o;
     load_geo<DG>(sc, g, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o);
     const float gm = __ldg(sc.gmask + g);
+    Geo3 g3;
+    geo3_recipe(s0, s1, s2, q0, q1, q2, q3, g3);
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vw = b.view[v];
         if (vw.scene != si) continue;
-        preprocess_entry<DL, DS, CM>(vw, sc, g, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o, gm,
-                                     vw.ent_off + (uint64_t)g, rec, tiles_touched, rect, dkey, dval, clamp);
+        preprocess_entry<DL, DS, CM>(vw, sc, g, px, py, pz, g3, o, gm, vw.ent_off + (uint64_t)g, rec,
+                                     tiles_touched, rect, dkey, dval, clamp);
         if (ONE_VIEW) break;
     }
 }
@@ -470,6 +499,9 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
     float d_opac = 0.f, d_gmask = 0.f, d_c0[3] = {0.f, 0.f, 0.f};
     bool first = true;   // first visible view writes lobe gradients, later views add
     const bool multi_view = b.n_views > 1;
+    Geo3 g3;
+    geo3_recipe(s0, s1, s2, q0, q1, q2, q3, g3);
+    float dS[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vw = b.view[v];
@@ -572,7 +604,7 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
         // ---- geometry: recompute the projection (after the colour part, so that
         // its intermediates are not live across the lobe loop) ----
         Geo G;
-        project_recipe(vw, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o, gm, G);
+        project_view(vw, px, py, pz, g3, o, gm, G);
 
         // ---- projected centre: x = fx t_x / t_z + cx - 0.5 ----
         const float itz = 1.0f / G.tz;
@@ -609,37 +641,11 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
                 Gs[i][j] = 2.f * da * G.A[0][i] * G.A[0][j] +
                            db * (G.A[0][i] * G.A[1][j] + G.A[1][i] * G.A[0][j]) +
                            2.f * dc * G.A[1][i] * G.A[1][j];
-        float dM[3][3];
+        // dL/dSigma_3D summed over the views; chained to scale and rotation once
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-                dM[i][k] = Gs[i][0] * G.M[0][k] + Gs[i][1] * G.M[1][k] + Gs[i][2] * G.M[2][k];
-        const float sv[3] = {s0, s1, s2};
-        float dR[3][3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            d_scale[k] += dM[0][k] * G.R[0][k] + dM[1][k] * G.R[1][k] + dM[2][k] * G.R[2][k];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) dR[i][k] = dM[i][k] * sv[k];
-        }
-        // rotation of the unit quaternion (w, x, y, z)
-        {
-            const float w = G.qw, x = G.qx, y = G.qy, z = G.qz;
-            const float gw = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] -
-                                    y * dR[2][0] + x * dR[2][1]);
-            const float gxq = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] -
-                                     w * dR[1][2] + z * dR[2][0] + w * dR[2][1] - 2.f * x * dR[2][2]);
-            const float gyq = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] +
-                                     z * dR[1][2] - w * dR[2][0] + z * dR[2][1] - 2.f * y * dR[2][2]);
-            const float gzq = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] -
-                                     2.f * z * dR[1][1] + y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
-            const float pr = w * gw + x * gxq + y * gyq + z * gzq;
-            d_q[0] += (gw - w * pr) * G.invq;
-            d_q[1] += (gxq - x * pr) * G.invq;
-            d_q[2] += (gyq - y * pr) * G.invq;
-            d_q[3] += (gzq - z * pr) * G.invq;
-        }
+            for (int j = 0; j < 3; ++j) dS[i][j] += Gs[i][j];
         // J entries
         const float *V = vw.V;
         const float dJ00 = dA0[0] * V[0] + dA0[1] * V[1] + dA0[2] * V[2];
@@ -667,6 +673,37 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
     }
 
     const sg_grads &gr = sc.grads;
+    // Sigma_3D = M M^T, M = R diag(s): scale and (unit, then raw) quaternion
+    if (!first) {
+        float dM[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                dM[i][k] = dS[i][0] * g3.M[0][k] + dS[i][1] * g3.M[1][k] + dS[i][2] * g3.M[2][k];
+        const float sv[3] = {s0, s1, s2};
+        float dR[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            d_scale[k] = dM[0][k] * g3.R[0][k] + dM[1][k] * g3.R[1][k] + dM[2][k] * g3.R[2][k];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) dR[i][k] = dM[i][k] * sv[k];
+        }
+        const float w = g3.qw, x = g3.qx, y = g3.qy, z = g3.qz;
+        const float gw = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] -
+                                y * dR[2][0] + x * dR[2][1]);
+        const float gxq = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] -
+                                 w * dR[1][2] + z * dR[2][0] + w * dR[2][1] - 2.f * x * dR[2][2]);
+        const float gyq = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] +
+                                 z * dR[1][2] - w * dR[2][0] + z * dR[2][1] - 2.f * y * dR[2][2]);
+        const float gzq = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] -
+                                 2.f * z * dR[1][1] + y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+        const float pr = w * gw + x * gxq + y * gyq + z * gzq;
+        d_q[0] = (gw - w * pr) * g3.invq;
+        d_q[1] = (gxq - x * pr) * g3.invq;
+        d_q[2] = (gyq - y * pr) * g3.invq;
+        d_q[3] = (gzq - z * pr) * g3.invq;
+    }
     if (first && sh_mode && gr.sh) {   // not visible in any view: SH gradients are zero
         for (int k = 0; k < 48; ++k) gr.sh[(int64_t)k * n + g] = 0.f;
     }
