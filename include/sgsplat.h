@@ -162,7 +162,7 @@ typedef struct sg_sizes {
  * e = ent_off(view) + Gaussian id, views in call order). Read-only views for
  * inspection, e.g. visibility and screen radius per Gaussian.
  *   rec           [M] 48-byte records, binary32:
- *                     x, y, conic A, conic B | conic C, o', r, g | b, radius, depth, t
+ *                     x, y, conic A, conic B | conic C, t, o', r | g, b, radius, depth
  *                 (t: the enlarged bound on q = d^T conic d where alpha can
  *                 reach 1/255, 2 ln(255 o') 1.01 + 0.01, negative if o' < 1/255)
  *                 (x, y: projected centre in pixel-index coordinates; conic

@@ -90,7 +90,7 @@ constexpr int SUB_W = 8, SUB_H = 4;
 // out are ones the alpha test would skip anyway: skipping them changes no
 // result.
 __device__ __forceinline__ uint32_t reach_mask(const Rec &rc, float x0, float y0) {
-    const float A = rc.a.z, B = rc.a.w, C = rc.b.x, op = rc.b.y;
+    const float A = rc.a.z, B = rc.a.w, C = rc.b.x, op = rc.b.z;
     const float detc = A * C - B * B;
     const float k2 = 2.f * __logf(255.f * op);
     if (!(detc > 0.f) || !(k2 >= 0.f)) return 0xFFu;
@@ -116,8 +116,8 @@ __device__ __forceinline__ uint32_t reach_mask(const Rec &rc, float x0, float y0
 template <bool CULL, int NB>
 __device__ __forceinline__ void stage(StagedN<NB> &sm, int slot, const Rec &rc, uint32_t e, float x0, float y0) {
     sm.q[slot] = make_float4(rc.a.x, rc.a.y, -0.5f * LOG2E * rc.a.z, -LOG2E * rc.a.w);
-    sm.r[slot] = make_float4(-0.5f * LOG2E * rc.b.x, rc.b.y, rc.b.z, rc.b.w);
-    sm.s[slot] = rc.c.x;
+    sm.r[slot] = make_float4(-0.5f * LOG2E * rc.b.x, rc.b.z, rc.b.w, rc.c.x);
+    sm.s[slot] = rc.c.y;
     sm.id[slot] = e;
     sm.mask[slot] = CULL ? reach_mask(rc, x0, y0) : 0xFFu;
 }

@@ -59,11 +59,12 @@ struct Batch {
     SceneDesc scene[SG_MAX_SCENES];
 };
 
-// One projected Gaussian as the blend reads it: 48 bytes, two 32-byte sectors.
+// One projected Gaussian: 48 bytes. The tile binning reads the first 24 bytes
+// (one 32-byte sector), the blend the first 40.
 struct __align__(16) Rec {
     float4 a;   // x, y, conic A, conic B
-    float4 b;   // conic C, o' = m_g * o, r, g
-    float4 c;   // b, radius, depth, tile-binning threshold (tile_reach_threshold)
+    float4 b;   // conic C, tile-binning bound t (tile_reach_threshold), o' = m_g * o, r
+    float4 c;   // g, b, radius, depth
 };
 
 // Device counters kept in the workspace.

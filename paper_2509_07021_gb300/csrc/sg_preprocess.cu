@@ -381,13 +381,13 @@ __device__ __forceinline__ void preprocess_entry(const ViewDesc &vw, const Scene
             cbl += wgt * ldp<DL>(sc.amp, 2 * L + k);
         }
     }
-    Rec r;
-    r.a = make_float4(G.x, G.y, G.conA, G.conB);
-    r.b = make_float4(G.conC, G.op, fmaxf(cr, 0.f), fmaxf(cg, 0.f));
     // channels clamped by max(c, 0) (not c >= 0, NaN included): the backward reads these bits
     clamp[e] = (uint8_t)((cr >= 0.f ? 0u : 1u) | (cg >= 0.f ? 0u : 2u) | (cbl >= 0.f ? 0u : 4u));
     const float reach_t = tile_reach_threshold(G.op);
-    r.c = make_float4(fmaxf(cbl, 0.f), G.rf, G.tz, reach_t);
+    Rec r;
+    r.a = make_float4(G.x, G.y, G.conA, G.conB);
+    r.b = make_float4(G.conC, reach_t, G.op, fmaxf(cr, 0.f));
+    r.c = make_float4(fmaxf(cg, 0.f), fmaxf(cbl, 0.f), G.rf, G.tz);
     rec[e] = r;
     // tiles of the rectangle that the alpha >= 1/255 ellipse reaches
     TileReach R;

@@ -462,8 +462,10 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
             rows = (ry >> 16) - (ry & 0xFFFFu);
             tbase = vw.tile_off;
             tx = (uint32_t)vw.tiles_x;
-            const Rec r = rec[e];
-            tile_reach_init(r.a.x, r.a.y, r.a.z, r.a.w, r.b.x, r.c.w, s_R[threadIdx.x]);
+            // the binning reads the record's first 24 bytes: x, y, conic, bound (one sector)
+            const float4 ra = rec[e].a;
+            const float2 rb = *reinterpret_cast<const float2 *>(&rec[e].b);
+            tile_reach_init(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, s_R[threadIdx.x]);
         }
     }
     uint32_t total, total_rows;

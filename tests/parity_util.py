@@ -66,15 +66,15 @@ def check_decisions(gv: GpuView, scene, cams, results):
         np.testing.assert_array_equal(vis, dec.visible, err_msg=f"view {v}: visibility")
         rec = gv.rec[sl][vis]
         np.testing.assert_array_equal(rect[vis], dec.rect[vis], err_msg=f"view {v}: rect")
-        np.testing.assert_array_equal(rec[:, 9].astype(np.int64), dec.radius[vis], err_msg="radius")
-        np.testing.assert_array_equal(rec[:, 10].view(np.uint32), dec.depth_bits[vis], err_msg="depth")
+        np.testing.assert_array_equal(rec[:, 10].astype(np.int64), dec.radius[vis], err_msg="radius")
+        np.testing.assert_array_equal(rec[:, 11].view(np.uint32), dec.depth_bits[vis], err_msg="depth")
         np.testing.assert_array_equal(rec[:, 0:2].view(np.uint32),
                                       dec.xy32[vis].astype(np.float32).view(np.uint32), err_msg="xy")
         np.testing.assert_array_equal(rec[:, [2, 3, 4]].view(np.uint32),
                                       dec.conic32[vis].astype(np.float32).view(np.uint32), err_msg="conic")
         opd = (scene.gmask.astype(np.float32) * scene.opac.astype(np.float32))[vis]
-        np.testing.assert_array_equal(rec[:, 5], opd)
-        np.testing.assert_array_equal(rec[:, 11].view(np.uint32), dec.reach_t[vis].view(np.uint32),
+        np.testing.assert_array_equal(rec[:, 6], opd)
+        np.testing.assert_array_equal(rec[:, 5].view(np.uint32), dec.reach_t[vis].view(np.uint32),
                                       err_msg="tile-binning bound")
         np.testing.assert_array_equal(gv.tt[sl], dec.touched, err_msg=f"view {v}: tiles_touched")
         # tile lists
