@@ -247,18 +247,26 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
             constexpr int RS = row_slots<P>();
 #pragma unroll
             for (int j0 = 0; j0 < P; j0 += RS) {
-                if (!((msk >> j0) & ((1u << RS) - 1u))) continue;   // warp-uniform
+                const uint32_t bits = (msk >> j0) & ((1u << RS) - 1u);
+                if (!bits) continue;                           // warp-uniform
                 RowEval row;
                 eval_row(fpy[j0], q, r, row);
+                // both pixels of the row first, with no branch between them
+                PairEval pe[RS];
+                bool ok[RS];
 #pragma unroll
                 for (int h = 0; h < RS; ++h) {
                     const int j = j0 + h;
-                    if (!((msk >> j) & 1u)) continue;        // warp-uniform
-                    if (done[j]) continue;
-                    PairEval p;
-                    eval_pixel(fpx[j], q, r, row, p);
-                    if (COUNT) ++ne;
-                    if (p.p2 > 0.f || p.alpha < ALPHA_MIN) continue;
+                    eval_pixel(fpx[j], q, r, row, pe[h]);
+                    const bool live = ((bits >> h) & 1u) && !done[j];
+                    if (COUNT) ne += live ? 1u : 0u;
+                    ok[h] = live && !(pe[h].p2 > 0.f || pe[h].alpha < ALPHA_MIN);
+                }
+#pragma unroll
+                for (int h = 0; h < RS; ++h) {
+                    const int j = j0 + h;
+                    if (!ok[h]) continue;
+                    const PairEval &p = pe[h];
                     const float tt = __fmul_rn(T[j], __fsub_rn(1.f, p.alpha));
                     if (tt < T_STOP) { done[j] = true; continue; }
                     const float w = p.alpha * T[j];
@@ -404,6 +412,33 @@ __device__ __forceinline__ void warp_sum9_atomic(const float v[9], float *dg, ui
     if (lane == 1) atomicAdd(dg + 8 * M + e, d);
 }
 
+// Adds one pixel's share of one blended pair to v (in dg order) and steps the
+// pixel's T and Sg back over the pair.
+__device__ __forceinline__ void bwd_adjoint(const PairEval &p, float dy, const float4 &r, float bl,
+                                            float &T, float &Sg, float g0, float g1, float g2, float v[9]) {
+    const float oma = __fsub_rn(1.f, p.alpha);
+    const float ro = rcp_approx(oma);
+    const float Ti = T * ro;
+    const float w = p.alpha * Ti;
+    const float cg = fmaf(r.z, g0, fmaf(r.w, g1, bl * g2));
+    const float dal = Ti * cg - Sg * ro;
+    Sg = fmaf(cg, w, Sg);
+    T = Ti;
+    v[6] = fmaf(w, g0, v[6]);
+    v[7] = fmaf(w, g1, v[7]);
+    v[8] = fmaf(w, g2, v[8]);
+    // dL/do' share of this pixel; none where the 0.99 clamp is active.
+    // dL/dpower = o' dG: the factor o' is applied once per Gaussian.
+    const float dG = p.ag > ALPHA_MAX ? 0.f : dal * p.G;
+    v[5] += dG;
+    const float hx = dG * p.dx, hy = dG * dy;
+    v[0] += hx;                          // sum dG dx
+    v[1] += hy;                          // sum dG dy
+    v[2] = fmaf(hx, p.dx, v[2]);         // sum dG dx^2
+    v[3] = fmaf(hx, dy, v[3]);           // sum dG dx dy
+    v[4] = fmaf(hy, dy, v[4]);           // sum dG dy^2
+}
+
 // Per pixel the walk runs back from the pixel's last blended pair, recovering
 // the transmittance before each pair as T_i = T_{i+1} / (1 - alpha_i) and
 // keeping Sg = sum over later pairs of (c . g) alpha T, so that
@@ -485,40 +520,27 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
             constexpr int RS = row_slots<P>();
 #pragma unroll
             for (int j0 = 0; j0 < P; j0 += RS) {
-                if (!((msk >> j0) & ((1u << RS) - 1u))) continue;   // warp-uniform
+                const uint32_t bits = (msk >> j0) & ((1u << RS) - 1u);
+                if (!bits) continue;                           // warp-uniform
                 RowEval row;
                 eval_row(fpy[j0], q, r, row);
+                // both pixels of the row first, with no branch between them
+                PairEval pe[RS];
+                bool ok[RS];
 #pragma unroll
                 for (int hh = 0; hh < RS; ++hh) {
                     const int j = j0 + hh;
-                    if (!((msk >> j) & 1u)) continue;        // warp-uniform
-                    if (pos >= mylast[j]) continue;
-                    PairEval p;
-                    eval_pixel(fpx[j], q, r, row, p);
-                    if (COUNT) ++ne;
-                    if (p.p2 > 0.f || p.alpha < ALPHA_MIN) continue;
+                    eval_pixel(fpx[j], q, r, row, pe[hh]);
+                    const bool live = ((bits >> hh) & 1u) && pos < mylast[j];
+                    if (COUNT) ne += live ? 1u : 0u;
+                    ok[hh] = live && !(pe[hh].p2 > 0.f || pe[hh].alpha < ALPHA_MIN);
+                }
+#pragma unroll
+                for (int hh = 0; hh < RS; ++hh) {
+                    const int j = j0 + hh;
+                    if (!ok[hh]) continue;
                     any = true;
-                    const float oma = __fsub_rn(1.f, p.alpha);
-                    const float ro = rcp_approx(oma);
-                    const float Ti = T[j] * ro;
-                    const float w = p.alpha * Ti;
-                    const float cg = fmaf(r.z, g0[j], fmaf(r.w, g1[j], bl * g2[j]));
-                    const float dal = Ti * cg - Sg[j] * ro;
-                    Sg[j] = fmaf(cg, w, Sg[j]);
-                    T[j] = Ti;
-                    v[6] = fmaf(w, g0[j], v[6]);
-                    v[7] = fmaf(w, g1[j], v[7]);
-                    v[8] = fmaf(w, g2[j], v[8]);
-                    // dL/do' share of this pixel; none where the 0.99 clamp is active.
-                    // dL/dpower = o' dG: the factor o' is applied once per Gaussian.
-                    const float dG = p.ag > ALPHA_MAX ? 0.f : dal * p.G;
-                    v[5] += dG;
-                    const float hx = dG * p.dx, hy = dG * row.dy;
-                    v[0] += hx;                               // sum dG dx
-                    v[1] += hy;                               // sum dG dy
-                    v[2] = fmaf(hx, p.dx, v[2]);              // sum dG dx^2
-                    v[3] = fmaf(hx, row.dy, v[3]);            // sum dG dx dy
-                    v[4] = fmaf(hy, row.dy, v[4]);            // sum dG dy^2
+                    bwd_adjoint(pe[hh], row.dy, r, bl, T[j], Sg[j], g0[j], g1[j], g2[j], v);
                 }
             }
             if (__any_sync(0xffffffffu, any)) {

@@ -333,9 +333,28 @@ __device__ __forceinline__ void sh3_grad_acc(float x, float y, float z, const fl
 // ---------------------------------------------------------------------------
 // One (view, Gaussian) entry: projection (decision recipe), colour, record and
 // tile binning. The Gaussian's parameters were loaded once by the caller.
+// The view-independent part of a Gaussian's SG colour: c0 and its lobe range
+// (CSR bounds clamped to [0, L] so a malformed lobe_off cannot read out of range).
+struct ColourBase {
+    float c0[3];
+    int lo, hi;
+};
+
+template <int CM>
+__device__ __forceinline__ void load_colour_base(const SceneDesc &sc, int64_t g, ColourBase &cb) {
+    cb.c0[0] = cb.c0[1] = cb.c0[2] = 0.f;
+    cb.lo = cb.hi = 0;
+    if (CM == SG_COLOR_SH3) return;
+    const int64_t n = sc.n;
+    cb.c0[0] = __ldg(sc.c0 + g); cb.c0[1] = __ldg(sc.c0 + n + g); cb.c0[2] = __ldg(sc.c0 + 2 * n + g);
+    cb.hi = min(__ldg(sc.lobe_off + g + 1), (int)sc.n_lobes);
+    cb.lo = max(0, min(__ldg(sc.lobe_off + g), cb.hi));
+}
+
 template <int DL, int DS, int CM>
 __device__ __forceinline__ void preprocess_entry(const ViewDesc &vw, const SceneDesc &sc, int64_t g, float px,
-                                                 float py, float pz, const Geo3 &g3, float o, float gm, uint64_t e,
+                                                 float py, float pz, const Geo3 &g3, float o, float gm,
+                                                 const ColourBase &cb, uint64_t e,
                                                  Rec *__restrict__ rec, uint32_t *__restrict__ tiles_touched,
                                                  uint2 *__restrict__ rect, uint32_t *__restrict__ dkey,
                                                  uint32_t *__restrict__ dval, uint8_t *__restrict__ clamp) {
@@ -365,11 +384,8 @@ __device__ __forceinline__ void preprocess_entry(const ViewDesc &vw, const Scene
             for (int k = 0; k < 16; ++k) c[ch] = fmaf(Y[k], __ldg(sc.sh + (int64_t)(ch * 16 + k) * n + g), c[ch]);
         cr = c[0]; cg = c[1]; cbl = c[2];
     } else {
-        cr = __ldg(sc.c0 + g); cg = __ldg(sc.c0 + n + g); cbl = __ldg(sc.c0 + 2 * n + g);
-        // CSR bounds clamped to [0, L] so a malformed lobe_off cannot read out of range
-        const int hi = min(__ldg(sc.lobe_off + g + 1), (int)L);
-        const int lo = max(0, min(__ldg(sc.lobe_off + g), hi));
-        for (int k = lo; k < hi; ++k) {
+        cr = cb.c0[0]; cg = cb.c0[1]; cbl = cb.c0[2];
+        for (int k = cb.lo; k < cb.hi; ++k) {
             const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
                         az = ldp<DL>(sc.axis, 2 * L + k);
             const float ia = 1.0f / sqrtf(ax * ax + ay * ay + az * az);
@@ -408,8 +424,11 @@ __device__ __forceinline__ void preprocess_entry(const ViewDesc &vw, const Scene
 // into every view of the call that shows its scene. ONE_VIEW: no scene has
 // more than one view, so the walk stops at the first (the parameters need not
 // stay live across views).
+#ifndef SG_PRE_MIN_BLOCKS
+#define SG_PRE_MIN_BLOCKS 1
+#endif
 template <int DG, int DL, int DS, int CM, bool ONE_VIEW>
-__global__ void __launch_bounds__(PRE_THREADS)
+__global__ void __launch_bounds__(PRE_THREADS, SG_PRE_MIN_BLOCKS)
 k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__restrict__ tiles_touched,
              uint2 *__restrict__ rect, uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
              uint8_t *__restrict__ clamp) {
@@ -421,12 +440,14 @@ k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__re
     float px, py, pz, s0, s1, s2, q0, q1, q2, q3, o;
     load_geo<DG>(sc, g, px, py, pz, s0, s1, s2, q0, q1, q2, q3, o);
     const float gm = __ldg(sc.gmask + g);
+    ColourBase cb;   // issued with the geometry loads: one memory round trip fewer
+    load_colour_base<CM>(sc, g, cb);
     Geo3 g3;
     geo3_recipe(s0, s1, s2, q0, q1, q2, q3, g3);
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vw = b.view[v];
         if (vw.scene != si) continue;
-        preprocess_entry<DL, DS, CM>(vw, sc, g, px, py, pz, g3, o, gm, vw.ent_off + (uint64_t)g, rec,
+        preprocess_entry<DL, DS, CM>(vw, sc, g, px, py, pz, g3, o, gm, cb, vw.ent_off + (uint64_t)g, rec,
                                      tiles_touched, rect, dkey, dval, clamp);
         if (ONE_VIEW) break;
     }
