@@ -328,6 +328,30 @@ __device__ __forceinline__ void sh3_grad_acc(float x, float y, float z, const fl
     gx += -SH_C3A * (3.f * xx - 3.f * yy) * w[15]; gy += 6.f * SH_C3A * x * y * w[15];
 }
 
+// Parameters of the lobes k0 .. k0 + LOBE_CHUNK - 1 of one Gaussian, loaded
+// together (two lobes per round trip measured fastest: four cost registers).
+// Indices past hi - 1 repeat lobe hi - 1 (in range; those values are unused).
+#ifndef SG_LOBE_CHUNK
+#define SG_LOBE_CHUNK 2
+#endif
+constexpr int LOBE_CHUNK = SG_LOBE_CHUNK;
+template <int DL, int DS>
+struct LobeChunk {
+    float ax[LOBE_CHUNK], ay[LOBE_CHUNK], az[LOBE_CHUNK], sh[LOBE_CHUNK], m[LOBE_CHUNK];
+    float a0[LOBE_CHUNK], a1[LOBE_CHUNK], a2[LOBE_CHUNK];
+    __device__ __forceinline__ void load(const SceneDesc &sc, int k0, int hi) {
+        const int64_t L = sc.n_lobes;
+#pragma unroll
+        for (int u = 0; u < LOBE_CHUNK; ++u) {
+            const int k = min(k0 + u, hi - 1);
+            ax[u] = ldp<DL>(sc.axis, k); ay[u] = ldp<DL>(sc.axis, L + k); az[u] = ldp<DL>(sc.axis, 2 * L + k);
+            sh[u] = ldp<DS>(sc.sharp, k);
+            m[u] = __ldg(sc.lmask + k);
+            a0[u] = ldp<DL>(sc.amp, k); a1[u] = ldp<DL>(sc.amp, L + k); a2[u] = ldp<DL>(sc.amp, 2 * L + k);
+        }
+    }
+};
+
 // ---------------------------------------------------------------------------
 // K1 preprocessSG
 // ---------------------------------------------------------------------------
@@ -385,16 +409,20 @@ __device__ __forceinline__ void preprocess_entry(const ViewDesc &vw, const Scene
         cr = c[0]; cg = c[1]; cbl = c[2];
     } else {
         cr = cb.c0[0]; cg = cb.c0[1]; cbl = cb.c0[2];
-        for (int k = cb.lo; k < cb.hi; ++k) {
-            const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
-                        az = ldp<DL>(sc.axis, 2 * L + k);
-            const float ia = 1.0f / sqrtf(ax * ax + ay * ay + az * az);
-            const float dot = (ax * dx + ay * dy + az * dz) * ia;
-            const float sh = ldp<DS>(sc.sharp, k);
-            const float wgt = __ldg(sc.lmask + k) * expf(sh * (dot - 1.0f));
-            cr += wgt * ldp<DL>(sc.amp, k);
-            cg += wgt * ldp<DL>(sc.amp, L + k);
-            cbl += wgt * ldp<DL>(sc.amp, 2 * L + k);
+        for (int k0 = cb.lo; k0 < cb.hi; k0 += LOBE_CHUNK) {
+            LobeChunk<DL, DS> lc;
+            lc.load(sc, k0, cb.hi);
+#pragma unroll
+            for (int u = 0; u < LOBE_CHUNK; ++u) {
+                if (k0 + u >= cb.hi) break;
+                const float ax = lc.ax[u], ay = lc.ay[u], az = lc.az[u];
+                const float ia = 1.0f / sqrtf(ax * ax + ay * ay + az * az);
+                const float dot = (ax * dx + ay * dy + az * dz) * ia;
+                const float wgt = lc.m[u] * expf(lc.sh[u] * (dot - 1.0f));
+                cr += wgt * lc.a0[u];
+                cg += wgt * lc.a1[u];
+                cbl += wgt * lc.a2[u];
+            }
         }
     }
     // channels clamped by max(c, 0) (not c >= 0, NaN included): the backward reads these bits
@@ -579,38 +607,44 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
             d_c0[1] += gc[1];
             d_c0[2] += gc[2];
         }
-        for (int k = lo; k < hi; ++k) {
-            const float ax = ldp<DL>(sc.axis, k), ay = ldp<DL>(sc.axis, L + k),
-                        az = ldp<DL>(sc.axis, 2 * L + k);
-            const float na = sqrtf(ax * ax + ay * ay + az * az);
-            const float ia = 1.0f / na;
-            const float mx = ax * ia, my = ay * ia, mz = az * ia;
-            const float dot = mx * vx + my * vy + mz * vz;
-            const float sh = ldp<DS>(sc.sharp, k);
-            const float ex = expf(sh * (dot - 1.0f));
-            const float m = __ldg(sc.lmask + k);
-            const float a0 = ldp<DL>(sc.amp, k), a1 = ldp<DL>(sc.amp, L + k), a2 = ldp<DL>(sc.amp, 2 * L + k);
-            const float ga = a0 * gc[0] + a1 * gc[1] + a2 * gc[2];
-            const float de = m * ga;
-            const float dd = de * ex * sh;                 // dL/d(mu_hat . v)
-            const float gmx = dd * vx, gmy = dd * vy, gmz = dd * vz;   // dL/dmu_hat
-            const float pr = mx * gmx + my * gmy + mz * gmz;
-            dvx += dd * mx; dvy += dd * my; dvz += dd * mz;
-            float ga_out[3] = {m * ex * gc[0], m * ex * gc[1], m * ex * gc[2]};
-            float gax[3] = {(gmx - mx * pr) * ia, (gmy - my * pr) * ia, (gmz - mz * pr) * ia};
-            const float gs = de * ex * (dot - 1.0f);
-            const float gml = ex * ga;
-            const sg_grads &gr = sc.grads;
-            if (first) {
-                if (gr.amp) { gr.amp[k] = ga_out[0]; gr.amp[L + k] = ga_out[1]; gr.amp[2 * L + k] = ga_out[2]; }
-                if (gr.axis) { gr.axis[k] = gax[0]; gr.axis[L + k] = gax[1]; gr.axis[2 * L + k] = gax[2]; }
-                if (gr.sharp) gr.sharp[k] = gs;
-                if (gr.lmask) gr.lmask[k] = gml;
-            } else {
-                if (gr.amp) { gr.amp[k] += ga_out[0]; gr.amp[L + k] += ga_out[1]; gr.amp[2 * L + k] += ga_out[2]; }
-                if (gr.axis) { gr.axis[k] += gax[0]; gr.axis[L + k] += gax[1]; gr.axis[2 * L + k] += gax[2]; }
-                if (gr.sharp) gr.sharp[k] += gs;
-                if (gr.lmask) gr.lmask[k] += gml;
+        for (int k0 = lo; k0 < hi; k0 += LOBE_CHUNK) {
+            LobeChunk<DL, DS> lc;
+            lc.load(sc, k0, hi);
+#pragma unroll
+            for (int u = 0; u < LOBE_CHUNK; ++u) {
+                const int k = k0 + u;
+                if (k >= hi) break;
+                const float ax = lc.ax[u], ay = lc.ay[u], az = lc.az[u];
+                const float na = sqrtf(ax * ax + ay * ay + az * az);
+                const float ia = 1.0f / na;
+                const float mx = ax * ia, my = ay * ia, mz = az * ia;
+                const float dot = mx * vx + my * vy + mz * vz;
+                const float sh = lc.sh[u];
+                const float ex = expf(sh * (dot - 1.0f));
+                const float m = lc.m[u];
+                const float a0 = lc.a0[u], a1 = lc.a1[u], a2 = lc.a2[u];
+                const float ga = a0 * gc[0] + a1 * gc[1] + a2 * gc[2];
+                const float de = m * ga;
+                const float dd = de * ex * sh;                 // dL/d(mu_hat . v)
+                const float gmx = dd * vx, gmy = dd * vy, gmz = dd * vz;   // dL/dmu_hat
+                const float pr = mx * gmx + my * gmy + mz * gmz;
+                dvx += dd * mx; dvy += dd * my; dvz += dd * mz;
+                float ga_out[3] = {m * ex * gc[0], m * ex * gc[1], m * ex * gc[2]};
+                float gax[3] = {(gmx - mx * pr) * ia, (gmy - my * pr) * ia, (gmz - mz * pr) * ia};
+                const float gs = de * ex * (dot - 1.0f);
+                const float gml = ex * ga;
+                const sg_grads &gr = sc.grads;
+                if (first) {
+                    if (gr.amp) { gr.amp[k] = ga_out[0]; gr.amp[L + k] = ga_out[1]; gr.amp[2 * L + k] = ga_out[2]; }
+                    if (gr.axis) { gr.axis[k] = gax[0]; gr.axis[L + k] = gax[1]; gr.axis[2 * L + k] = gax[2]; }
+                    if (gr.sharp) gr.sharp[k] = gs;
+                    if (gr.lmask) gr.lmask[k] = gml;
+                } else {
+                    if (gr.amp) { gr.amp[k] += ga_out[0]; gr.amp[L + k] += ga_out[1]; gr.amp[2 * L + k] += ga_out[2]; }
+                    if (gr.axis) { gr.axis[k] += gax[0]; gr.axis[L + k] += gax[1]; gr.axis[2 * L + k] += gax[2]; }
+                    if (gr.sharp) gr.sharp[k] += gs;
+                    if (gr.lmask) gr.lmask[k] += gml;
+                }
             }
         }
         first = false;
