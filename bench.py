@@ -324,8 +324,8 @@ def stage_rooflines(stages_ms, counts, evals, hbm_gbs):
         "depth_sort": 4 * M + 8 * M + 8 * V + 3 * 16 * V,       # histogram, pass 0 (drops), passes 1-3
         "pair_offsets": 12 * V,                                 # sorted id + tt in, offset out
         "duplicate": 64 * V + 8 * K,                            # id, tt, rect, record in; pairs out
-        "tile_sort": 4 * K + 2 * 16 * K,                        # histogram, two passes
-        "tile_ranges": 4 * K + 8 * T,
+        "tile_sort": 4 * K + 2 * 16 * K + 8 * T,                # histogram, two passes, tile ranges
+        "tile_ranges": 12 * T,                                  # persistent tile order: ranges in, order out
         "bwd_clear": 36 * M,
         "preprocess_bwd": 64 * N + 32 * L + 41 * M + 60 * N + 32 * L,
     }

@@ -177,6 +177,7 @@ typedef struct sg_sizes {
  *   depth_order   [M] uint32: the entries with tiles_touched > 0 sorted by
  *                 (depth bits, entry), first; the rest of the array is scratch
  *   ranges        [n_tiles] 2 x uint32 [start, end) into the pair arrays
+ *                 ((0, 0) for a tile with no pair)
  *   pair_tile     [n_pairs] uint32 global tile id (view tile offset + ty * tiles_x + tx)
  *   pair_entry    [n_pairs] uint32 entry of each pair, sorted by (tile, depth bits, entry)
  */

@@ -387,10 +387,11 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     const bool counting = (prof().flags & SG_PROFILE_COUNT) != 0;
     uint64_t *aux_tile = reinterpret_cast<uint64_t *>(w + L.aux_tile);
     {
-        // the setup kernel also clears the tile ranges and both sorts' scratch
+        // the setup kernel also marks every tile range empty and clears both sorts' scratch
         ZeroRegions z;
         z.ptr[0] = reinterpret_cast<uint32_t *>(ranges);
         z.words[0] = 2 * L.n_tiles;
+        z.even[0] = RANGE_EMPTY;
         z.ptr[1] = reinterpret_cast<uint32_t *>(sums);
         z.words[1] = SORT_AUX_BYTES / 4;
         z.ptr[2] = reinterpret_cast<uint32_t *>(aux_tile);
@@ -448,18 +449,17 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     uint32_t *k1 = even ? pk_tmp : pk_final, *v1 = even ? pv_tmp : pv_final;
     {
         StageTimer t(ST_DUPLICATE, stream);
-        SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, rec, offs, counters, cap, k0, v0, n_views, stream),
+        // also the tile sort's digit histograms and cleared look-back flags
+        SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, rec, offs, counters, cap, k0, v0, n_views, stream,
+                                 L.tile_passes, aux_tile, hist, sort_flag_words(K, L.tile_bits)),
                 "duplicateWithKeys");
     }
     {
         StageTimer t(ST_TILE_SORT, stream);
+        // the last pass also bounds every tile's range in the sorted pairs
         SG_CUDA(launch_radix_sort(k0, v0, k1, v1, counters + CNT_PAIRS, K, L.tile_bits, hist, aux_tile, stream,
-                                  counters + CNT_STATUS, nullptr, true),
+                                  counters + CNT_STATUS, nullptr, true, ranges, L.n_tiles, true),
                 "tile sort");
-    }
-    {
-        StageTimer t(ST_RANGES, stream);
-        SG_CUDA(launch_ranges(pk_final, counters, K, ranges, L.n_tiles, stream), "tile ranges");
     }
     unsigned long long *evals =
         counting ? reinterpret_cast<unsigned long long *>(counters + CNT_EVALS) : nullptr;

@@ -208,10 +208,13 @@ void count_launches(int n);
 
 // ---- launchers (host side, defined in the .cu files) ----
 // Up to N device regions of 32-bit words that the setup kernel zeroes.
+// Regions the setup kernel fills: word i of region r gets even[r] if i is
+// even, else 0 (even[r] = 0: plain zeroing).
 struct ZeroRegions {
     static constexpr int N = 3;
     uint32_t *ptr[N] = {nullptr, nullptr, nullptr};
     uint64_t words[N] = {0, 0, 0};
+    uint32_t even[N] = {0, 0, 0};
 };
 cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStream_t s,
                          const ZeroRegions &z = ZeroRegions());
@@ -241,19 +244,26 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 constexpr size_t SORT_AUX_BYTES = 16384;
 constexpr uint32_t SORT_DROP_KEY = 0xFFFFFFFFu;
 // aux_zeroed: the caller has already zeroed the aux region in this stream.
+// hist_ready: the caller has also written every pass's digit histogram into
+// aux and zeroed the sort_flag_words(max_n, bits) look-back words of hist.
+// ranges (nullable): keys are ids below n_ranges; the sort also writes each
+// id's [first, last + 1) position range in the sorted output, (0, 0) for an id
+// with no key. On entry every range must hold (RANGE_EMPTY, 0).
+constexpr uint32_t RANGE_EMPTY = 0xFFFFFFFFu;
 cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
                               uint64_t *aux, cudaStream_t s, uint64_t *status = nullptr,
-                              uint64_t *kept_out = nullptr, bool aux_zeroed = false);
+                              uint64_t *kept_out = nullptr, bool aux_zeroed = false, uint2 *ranges = nullptr,
+                              uint64_t n_ranges = 0, bool hist_ready = false);
 int radix_passes(int bits);
+// Look-back flag words a sort of up to max_n keys of `bits` bits uses.
+uint64_t sort_flag_words(uint64_t max_n, int bits);
 
 cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,
                              const uint32_t *tiles_touched, const uint2 *rect, const Rec *rec,
                              const uint32_t *offsets, const uint64_t *counters, uint64_t cap,
-                             uint32_t *pkey, uint32_t *pval, int n_views, cudaStream_t s);
-// ranges must be zero on entry (the forward's setup kernel clears them).
-cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64_t cap,
-                          uint2 *ranges, uint64_t n_tiles, cudaStream_t s);
+                             uint32_t *pkey, uint32_t *pval, int n_views, cudaStream_t s, int hist_passes = 0,
+                             uint64_t *sort_aux = nullptr, uint32_t *flags = nullptr, uint64_t flag_words = 0);
 // Tiles by descending list length (256 length buckets) into order[n_tiles];
 // scratch: 512 words.
 cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *scratch,

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(256) k_setup(const BatchParam<NV, NS> p, Batch
     uint32_t *ds = reinterpret_cast<uint32_t *>(&dst->scene[0]);
     for (int i = threadIdx.x; i < (int)(n_scenes * sizeof(SceneDesc) / 4); i += blockDim.x) ds[i] = ps[i];
     for (int r = 0; r < ZeroRegions::N; ++r)
-        for (uint64_t i = threadIdx.x; i < z.words[r]; i += blockDim.x) z.ptr[r][i] = 0u;
+        for (uint64_t i = threadIdx.x; i < z.words[r]; i += blockDim.x) z.ptr[r][i] = (i & 1) ? 0u : z.even[r];
     if (threadIdx.x < CNT_N) counters[threadIdx.x] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {

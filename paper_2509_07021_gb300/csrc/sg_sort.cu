@@ -243,10 +243,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint32_t *__restri
     }
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_os_pass(
+// three resident blocks per SM (80 registers a thread)
+__global__ void __launch_bounds__(RS_THREADS, 3) k_os_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint64_t *__restrict__ n_dev, uint64_t max_n, int pass, int shift,
-    uint32_t mask, bool drop, uint32_t *__restrict__ flags, SortAux *aux) {
+    uint32_t mask, bool drop, uint32_t *__restrict__ flags, SortAux *aux, uint2 *__restrict__ ranges,
+    uint64_t n_ranges) {
     constexpr int NW = RS_THREADS / 32;
     constexpr int PER_WARP = RS_TILE / NW;   // 512 consecutive keys per warp
     __shared__ uint32_t cnt[NW][RS_RADIX];
@@ -359,40 +361,78 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_pass(
     }
     __syncthreads();
     const int items = (int)tot;   // the block's kept keys
+    // Last pass with ranges: the block's keys are now in full key order (its
+    // input is sorted by the lower digits, its local sort by this one is
+    // stable), so each run of one key is contiguous in the output; its ends
+    // bound that key's range. Skipped when the count exceeded the capacity.
+    const bool want_ranges = ranges != nullptr && *n_dev <= max_n;
     for (int p = threadIdx.x; p < items; p += RS_THREADS) {
         const uint32_t key = sk[p];
         const uint32_t dd = (key >> shift) & mask;
         const uint32_t o = gstart[dd] + (uint32_t)p - dstart[dd];
         kout[o] = key;
         vout[o] = sv[p];
+        if (want_ranges && key < n_ranges) {
+            if (p == 0 || sk[p - 1] != key) atomicMin(&ranges[key].x, o);
+            if (p == items - 1 || sk[p + 1] != key) atomicMax(&ranges[key].y, o + 1u);
+        }
     }
 }
 
 int radix_passes(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
 
-__global__ void k_os_finish(const SortAux *aux, uint64_t *status, uint64_t *kept_out) {
-    if (status && aux->status) *status = aux->status;
-    if (kept_out) *kept_out = aux->kept;
+uint64_t sort_flag_words(uint64_t max_n, int bits) {
+    return div_up(max_n, RS_TILE) * RS_RADIX * (uint64_t)radix_passes(bits);
+}
+
+// Status and kept count (one thread); ids that got no key get the range (0, 0).
+// no_pass: the keys had no bits, so no pass ran and every key is id 0.
+__global__ void k_os_finish(const SortAux *aux, uint64_t *status, uint64_t *kept_out, uint2 *ranges,
+                            uint64_t n_ranges, bool no_pass, const uint64_t *n_dev, uint64_t max_n) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && !no_pass) {
+        if (status && aux->status) *status = aux->status;
+        if (kept_out) *kept_out = aux->kept;
+    }
+    if (!ranges || i >= n_ranges) return;
+    if (no_pass) {
+        const uint64_t nd = *n_dev, n = nd <= max_n ? nd : 0;   // none when over capacity
+        ranges[i] = (i == 0 && n > 0) ? make_uint2(0u, (uint32_t)n) : make_uint2(0u, 0u);
+    } else if (ranges[i].x == RANGE_EMPTY) {
+        ranges[i] = make_uint2(0u, 0u);
+    }
 }
 
 cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
                               uint64_t *scan_sums, cudaStream_t s, uint64_t *status, uint64_t *kept_out,
-                              bool aux_zeroed) {
+                              bool aux_zeroed, uint2 *ranges, uint64_t n_ranges, bool hist_ready) {
     const uint32_t nblocks = (uint32_t)div_up(max_n, RS_TILE);
     const int passes = radix_passes(bits);
-    if (nblocks == 0 || passes == 0) return cudaSuccess;
+    const uint64_t fgrid = ranges ? std::max<uint64_t>(div_up(n_ranges, 256), 1) : 1;
+    if (nblocks == 0 || passes == 0) {
+        // nothing to sort; ranges still get their final values
+        if (ranges) {
+            k_os_finish<<<(unsigned)fgrid, 256, 0, s>>>(reinterpret_cast<SortAux *>(scan_sums), nullptr, nullptr,
+                                                       ranges, n_ranges, passes == 0, n_dev, max_n);
+            count_launches(1);
+            return cudaGetLastError();
+        }
+        return cudaSuccess;
+    }
     if (max_n > (uint64_t)LB_VAL) return cudaErrorInvalidValue;   // counts must fit the look-back word
     SortAux *aux = reinterpret_cast<SortAux *>(scan_sums);
-    if (!aux_zeroed) {
-        const cudaError_t e = cudaMemsetAsync(aux, 0, sizeof(SortAux), s);
-        if (e != cudaSuccess) return e;
-    }
-    const unsigned hgrid = nblocks < 4u * 152u ? nblocks : 4u * 152u;
     const bool drop = kept_out != nullptr;
     const uint64_t pass_words = (uint64_t)nblocks * RS_RADIX;
-    k_os_hist<<<hgrid, RS_THREADS, 0, s>>>(k0, n_dev, max_n, bits, drop, aux, hist, pass_words * passes);
-    count_launches(1);
+    if (!hist_ready) {
+        if (!aux_zeroed) {
+            const cudaError_t e = cudaMemsetAsync(aux, 0, sizeof(SortAux), s);
+            if (e != cudaSuccess) return e;
+        }
+        const unsigned hgrid = nblocks < 4u * 152u ? nblocks : 4u * 152u;
+        k_os_hist<<<hgrid, RS_THREADS, 0, s>>>(k0, n_dev, max_n, bits, drop, aux, hist, pass_words * passes);
+        count_launches(1);
+    }
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
@@ -400,15 +440,17 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
         const uint32_t mask = (1u << nb) - 1u;
         // with drop, pass 0 leaves SORT_DROP_KEY out and later passes see only the kept keys
         const uint64_t *np = (drop && p > 0) ? &aux->kept : n_dev;
+        uint2 *rg = p == passes - 1 ? ranges : nullptr;
         k_os_pass<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, np, max_n, p, shift, mask, drop && p == 0,
-                                                 hist + pass_words * p, aux);
+                                                 hist + pass_words * p, aux, rg, n_ranges);
         count_launches(1);
         uint32_t *t;
         t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
     }
-    if (status || kept_out) {
-        k_os_finish<<<1, 1, 0, s>>>(aux, status, kept_out);
+    if (status || kept_out || ranges) {
+        k_os_finish<<<(unsigned)fgrid, ranges ? 256 : 1, 0, s>>>(aux, status, kept_out, ranges, n_ranges, false,
+                                                                 n_dev, max_n);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -426,14 +468,28 @@ __device__ __forceinline__ int find_entry_view(const Batch &b, uint64_t e) {
     return lo;
 }
 
-// One block per 256 consecutive entries (depth order). The block's pairs are
-// contiguous in the output; its threads write them in order, each finding the
-// owning entry by binary search over the block's prefix sums, so stores are
-// coalesced and a large rectangle is spread over the whole block. Inside an
-// entry the tiles follow row-major order.
+// Adds the keys a, a + 1, .., b - 1 to a block's digit histograms: one count
+// per key for the lowest digit, one per run of equal digit above it.
+__device__ __forceinline__ void hist_key_run(uint32_t (*h)[RS_RADIX], int passes, uint32_t a, uint32_t b) {
+    for (uint32_t t = a; t < b; ++t) atomicAdd(&h[0][t & (RS_RADIX - 1)], 1u);
+    for (int p = 1; p < passes; ++p) {
+        const int sh = 8 * p;
+        for (uint32_t t = a; t < b;) {
+            const uint64_t next = ((uint64_t)(t >> sh) + 1u) << sh;   // first key of the next digit
+            const uint32_t seg = next < (uint64_t)b ? (uint32_t)next : b;
+            atomicAdd(&h[p][(t >> sh) & (RS_RADIX - 1)], seg - t);
+            t = seg;
+        }
+    }
+}
+
 // One block per 256 depth-sorted entries. The block's pairs go, entry by entry
 // and row by row, to [offsets[first entry], + the block's total): work items are
-// (entry, tile row); each finds its reached columns once and writes that run.
+// (entry, tile row); each finds its reached columns once and writes that run
+// (row-major inside an entry), so a large rectangle is spread over the whole
+// block and the stores stay coalesced. With hist_passes > 0 the kernel also
+// prepares the tile sort: it clears its look-back flags and adds exactly the
+// keys it writes to the digit histograms of its hist_passes passes.
 __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp, uint64_t M,
                                                    const uint32_t *__restrict__ sorted_ent,
                                                    const uint32_t *__restrict__ tiles_touched,
@@ -441,10 +497,17 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
                                                    const uint32_t *__restrict__ offsets,
                                                    const uint64_t *__restrict__ counters, uint64_t cap,
                                                    uint32_t *__restrict__ pkey,
-                                                   uint32_t *__restrict__ pval) {
+                                                   uint32_t *__restrict__ pval, int hist_passes,
+                                                   SortAux *__restrict__ aux, uint32_t *__restrict__ flags,
+                                                   uint64_t flag_words) {
     __shared__ uint32_t s_rinc[256], s_e[256], s_rx[256], s_ry[256], s_base[256], s_tx[256];
     __shared__ TileReach s_R[256];
     __shared__ uint32_t shs[33];
+    __shared__ uint32_t h[4][RS_RADIX];
+    // the tile sort's look-back flags start at zero (its passes run after this kernel)
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < flag_words; i += (uint64_t)gridDim.x * 256)
+        flags[i] = 0u;
+    for (int i = threadIdx.x; i < 4 * RS_RADIX; i += 256) h[i / RS_RADIX][i % RS_RADIX] = 0u;
     if (counters[CNT_PAIRS] > cap) return;   // capacity exceeded: the host reports it (uniform)
     const uint64_t j0 = (uint64_t)blockIdx.x * 256;
     const uint64_t j = j0 + threadIdx.x;
@@ -506,6 +569,9 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
                 pval[out0 + q] = s_e[o];
             }
         }
+        if (hist_passes > 0 && at < total)   // the keys written above, no more
+            hist_key_run(h, hist_passes, key0 + (uint32_t)c0,
+                         key0 + (uint32_t)c0 + min((uint32_t)(c1 - c0), total - at));
         done += chunk;
     }
     // Rows add up to tiles_touched by construction. Should they ever fall short,
@@ -513,6 +579,14 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
     for (uint32_t q = done + threadIdx.x; q < total; q += 256) {
         pkey[out0 + q] = s_base[0];
         pval[out0 + q] = (uint32_t)j0;
+        if (hist_passes > 0) hist_key_run(h, hist_passes, s_base[0], s_base[0] + 1u);
+    }
+    if (hist_passes > 0) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < hist_passes * RS_RADIX; i += 256) {
+            const uint32_t c = h[i / RS_RADIX][i % RS_RADIX];
+            if (c) atomicAdd(&aux->hist[i / RS_RADIX][i % RS_RADIX], c);
+        }
     }
 }
 
@@ -520,35 +594,14 @@ cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted
                              const uint32_t *tiles_touched, const uint2 *rect, const Rec *rec,
                              const uint32_t *offsets,
                              const uint64_t *counters, uint64_t cap, uint32_t *pkey, uint32_t *pval,
-                             int n_views, cudaStream_t s) {
+                             int n_views, cudaStream_t s, int hist_passes, uint64_t *sort_aux,
+                             uint32_t *flags, uint64_t flag_words) {
     (void)n_views;
-    if (M == 0) return cudaSuccess;
-    k_duplicate<<<(unsigned)div_up(M, 256), 256, 0, s>>>(db, M, sorted_ent, tiles_touched, rect, rec, offsets,
-                                                         counters, cap, pkey, pval);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// tile ranges from the sorted tile keys
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ pkey,
-                                                const uint64_t *__restrict__ counters, uint64_t cap,
-                                                uint2 *__restrict__ ranges, uint64_t n_tiles) {
-    const uint64_t K = counters[CNT_PAIRS];
-    if (K > cap) return;
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= K) return;
-    const uint32_t t = pkey[i];
-    if (t >= n_tiles) return;
-    if (i == 0 || pkey[i - 1] != t) ranges[t].x = (uint32_t)i;
-    if (i == K - 1 || pkey[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
-}
-
-cudaError_t launch_ranges(const uint32_t *pkey, const uint64_t *counters, uint64_t cap, uint2 *ranges,
-                          uint64_t n_tiles, cudaStream_t s) {
-    if (cap == 0) return cudaSuccess;
-    k_ranges<<<(unsigned)div_up(cap, 256), 256, 0, s>>>(pkey, counters, cap, ranges, n_tiles);
+    if (M == 0 && flag_words == 0) return cudaSuccess;
+    const uint64_t grid = std::max<uint64_t>(div_up(M, 256), 1);
+    k_duplicate<<<(unsigned)grid, 256, 0, s>>>(db, M, sorted_ent, tiles_touched, rect, rec, offsets, counters, cap,
+                                               pkey, pval, hist_passes, reinterpret_cast<SortAux *>(sort_aux),
+                                               flags, flag_words);
     count_launches(1);
     return cudaGetLastError();
 }

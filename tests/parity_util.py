@@ -89,6 +89,11 @@ def check_decisions(gv: GpuView, scene, cams, results):
     # pairs of all views are contiguous and ordered by global tile
     assert gv.K == sum(len(r.ids) for r in results)
     assert np.all(np.diff(gv.pair_tile) >= 0)
+    # every range starts where the tiles before it end; a tile with no pair holds (0, 0)
+    lens = gv.ranges[:, 1] - gv.ranges[:, 0]
+    ne = lens > 0
+    np.testing.assert_array_equal(gv.ranges[ne, 0], (np.cumsum(lens) - lens)[ne], err_msg="range starts")
+    np.testing.assert_array_equal(gv.ranges[~ne], 0, err_msg="tiles with no pair")
 
 
 def last_ids(last, ranges, ids, cam):
