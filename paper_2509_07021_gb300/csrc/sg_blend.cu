@@ -82,35 +82,39 @@ using StagedB = StagedN<BWD_BATCH>;
 // is sub-block w * P + j, lane l its pixel (l & 7, l >> 3).
 constexpr int SUB_W = 8, SUB_H = 4;
 
-// Bit s set unless no pixel of sub-block s can reach alpha >= 1/255. The
-// region o' exp(-d^T Sigma^-1 d / 2) >= 1/255 is the ellipse
-// d^T Sigma^-1 d <= 2 ln(255 o'), whose bounding box has half extents
-// sqrt(2 ln(255 o') Sigma_xx) and sqrt(2 ln(255 o') Sigma_yy) with
-// Sigma = conic^-1. The box is padded (0.1 % + 0.05 px) so that pixels left
-// out are ones the alpha test would skip anyway: skipping them changes no
-// result.
+// Bit s set unless no pixel centre of sub-block s lies in the enlarged ellipse
+// q = d^T conic d <= t, t being the record's tile-binning bound (2 ln(255 o')
+// grown by 1 % + 0.01, so every pixel where alpha can reach 1/255 lies inside;
+// pixels left out are ones the alpha test would skip anyway: skipping them
+// changes no result). Per band of 4 pixel rows, the ellipse's x-extent over the
+// band is taken where its edges are extreme (the right edge at dy = -m, the
+// left at dy = +m, m = B xmax / C, both clamped into the band) and compared
+// with the tile's two 8-column halves. Padded by 0.05 px for rounding.
 __device__ __forceinline__ uint32_t reach_mask(const Rec &rc, float x0, float y0) {
-    const float A = rc.a.z, B = rc.a.w, C = rc.b.x, op = rc.b.z;
-    const float detc = A * C - B * B;
-    const float k2 = 2.f * __logf(255.f * op);
-    if (!(detc > 0.f) || !(k2 >= 0.f)) return 0xFFu;
-    const float ex = sqrtf(k2 * C / detc) * 1.001f + 0.05f;
-    const float ey = sqrtf(k2 * A / detc) * 1.001f + 0.05f;
-    if (!isfinite(ex) || !isfinite(ey)) return 0xFFu;
-    const float xlo = rc.a.x - ex - x0, xhi = rc.a.x + ex - x0;
-    const float ylo = rc.a.y - ey - y0, yhi = rc.a.y + ey - y0;
-    uint32_t cols = 0u, rows = 0u;
+    const float x = rc.a.x, y = rc.a.y, A = rc.a.z, B = rc.a.w, C = rc.b.x, t = rc.b.y;
+    if (!(t >= 0.f)) return 0u;                      // o' < 1/255: alpha < 1/255 everywhere
+    const float det = A * C - B * B;
+    if (!(A > 0.f) || !(C > 0.f) || !(det > 0.f)) return 0xFFu;
+    const float At = A * t, invdet = 1.f / det, invA = 1.f / A;
+    const float ymax = sqrtf(At * invdet);
+    const float m = B * sqrtf(C * t * invdet) / C;
+    if (!isfinite(ymax) || !isfinite(m) || !isfinite(invA)) return 0xFFu;
+    constexpr float pad = 0.05f;
+    uint32_t mask = 0u;
 #pragma unroll
-    for (int sx = 0; sx < TILE / SUB_W; ++sx)
-        if (xhi >= (float)(sx * SUB_W) && xlo <= (float)(sx * SUB_W + SUB_W - 1)) cols |= 1u << sx;
+    for (int sy = 0; sy < TILE / SUB_H; ++sy) {
+        const float lo = fmaxf(y0 + (float)(SUB_H * sy) - y - pad, -ymax);
+        const float hi = fminf(y0 + (float)(SUB_H * sy + SUB_H - 1) - y + pad, ymax);
+        if (!(lo <= hi)) continue;
+        const float dr = fminf(fmaxf(-m, lo), hi), dl = fminf(fmaxf(m, lo), hi);
+        const float sr = sqrtf(fmaxf(0.f, At - det * dr * dr)), sl = sqrtf(fmaxf(0.f, At - det * dl * dl));
+        const float xr = x + (sr - B * dr) * invA + pad - x0, xl = x - (sl + B * dl) * invA - pad - x0;
 #pragma unroll
-    for (int sy = 0; sy < TILE / SUB_H; ++sy)
-        if (yhi >= (float)(sy * SUB_H) && ylo <= (float)(sy * SUB_H + SUB_H - 1)) rows |= 1u << sy;
-    uint32_t m = 0u;
-#pragma unroll
-    for (int sy = 0; sy < TILE / SUB_H; ++sy)
-        if (rows & (1u << sy)) m |= cols << (sy * (TILE / SUB_W));
-    return m;
+        for (int sx = 0; sx < TILE / SUB_W; ++sx)
+            if (xr >= (float)(sx * SUB_W) && xl <= (float)(sx * SUB_W + SUB_W - 1))
+                mask |= 1u << (sy * (TILE / SUB_W) + sx);
+    }
+    return mask;
 }
 
 template <bool CULL, int NB>
