@@ -146,3 +146,18 @@ def test_batched_importance_per_scene():
         expect = sum(r.importance for r in results)
         got = imps[s].cpu().numpy().astype(np.float64)
         assert np.linalg.norm(got - expect) <= 1e-3 * np.linalg.norm(expect)
+
+
+@pytest.mark.parametrize("sizes", [[(16, 16)], [(20, 12)]])
+def test_batched_one_or_two_tiles(sizes):
+    """A frame of one tile (the tile sort has no pass: its ranges come from the
+    pair count alone) and of two tiles (one pass) through the batched form."""
+    rng = np.random.default_rng(720 + len(sizes))
+    scene = synth.make_scene(rng, 600, lobes=synth.LOBE_MIX, means="cube", cube_side=1.3, masks="uniform")
+    cams = [synth.make_camera(w, h, 20.0) for w, h in sizes]
+    ds = [DeviceScene.from_host(scene)]
+    br = render.BatchedRenderer(ds, cams, [0] * len(cams))
+    br.forward()
+    n, st = br.status()
+    assert st == sgsplat.SG_OK and 0 < n <= br.capacity
+    _check_batched(br, [scene], cams, [0] * len(cams), seed=7)
