@@ -21,8 +21,9 @@
  *    the call only. The library allocates NO device memory: inputs, outputs,
  *    gradients and the workspaces are owned by the caller.
  *  - Work is issued on `stream` (a cudaStream_t; NULL = legacy default
- *    stream) and is stream ordered. sg_render_forward synchronises the stream
- *    once (a 4-byte read of the pair count); every other call is asynchronous.
+ *    stream) and is stream ordered. sg_render_forward waits once for a copy of
+ *    the pair count, queued right after the count is known (the rest of the
+ *    forward is already queued behind it); every other call is asynchronous.
  *  - Float arrays are planar structure of arrays: a "[3][N]" array holds N x
  *    values, then N y values, then N z values. Base addresses must be 16-byte
  *    aligned.
@@ -282,11 +283,14 @@ int sg_workspace_query(const sg_scene *scene, const sg_camera *cams, int n_views
  *
  * ws: device workspace of ws_bytes, 256-byte aligned. It must hold at least
  *   sg_sizes.ws_fixed_bytes; the pairs the call needs are counted on the
- *   device and read back once (the call synchronises `stream` here). If they
- *   exceed the capacity, the call returns SG_ERR_CAPACITY with out->n_pairs
- *   and out->ws_bytes set to what is needed and leaves the outputs
- *   unspecified; call again with a larger workspace. After success the
- *   workspace holds what sg_render_backward reads: keep it unmodified.
+ *   device and copied back once (the call returns when that copy is done,
+ *   with the rest of the forward queued on `stream`). If they exceed the
+ *   capacity, the call returns SG_ERR_CAPACITY with out->n_pairs and
+ *   out->ws_bytes set to what is needed and leaves the outputs unspecified
+ *   (the queued kernels bin no pair); call again with a larger workspace.
+ *   After success the workspace holds what sg_render_backward reads: keep it
+ *   unmodified. The copy goes to 64 bytes of pinned host memory that each
+ *   calling thread allocates once.
  * img: device [n_views] x [3][H][W] binary32, views packed one after another.
  * T_final: device [n_views] x [H][W] binary32, transmittance after the walk.
  * last: device [n_views] x [H][W] int32, 1 + position (inside the pixel's

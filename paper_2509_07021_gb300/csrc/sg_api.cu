@@ -337,9 +337,49 @@ void fill_sizes(const Batch &b, const WsLayout &L, uint64_t n_pairs, sg_sizes *o
     out->bwd_ws_bytes = bwd_bytes(b);
 }
 
-// sync = true: the plain form (one read of the pair count, SG_ERR_CAPACITY
-// returned to the caller). sync = false: the batched form (fixed grids sized by
-// the capacity, overflow recorded on the device, graph capturable).
+// Per-thread pinned host words, mapped into the device, and an event for the
+// plain form's read of the pair count: the scan's spine kernel stores the count
+// and the depth sort's status there, and the host waits on the event after it.
+struct CountReadback {
+    uint64_t *host = nullptr;     // [0] pairs, [1] status
+    uint64_t *dev_ptr = nullptr;  // the same words as the current device sees them
+    cudaEvent_t ev = nullptr;
+    int device = -1;
+};
+
+static cudaError_t count_readback(CountReadback *&out) {
+    thread_local CountReadback rb;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (!rb.host) {
+        void *p = nullptr;
+        e = cudaHostAlloc(&p, 64, cudaHostAllocPortable | cudaHostAllocMapped);
+        if (e != cudaSuccess) return e;
+        rb.host = static_cast<uint64_t *>(p);
+    }
+    if (!rb.ev || rb.device != dev) {
+        if (rb.ev) cudaEventDestroy(rb.ev);
+        rb.ev = nullptr;
+        e = cudaEventCreateWithFlags(&rb.ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        void *dp = nullptr;
+        e = cudaHostGetDevicePointer(&dp, rb.host, 0);
+        if (e != cudaSuccess) return e;
+        rb.dev_ptr = static_cast<uint64_t *>(dp);
+        rb.device = dev;
+    }
+    out = &rb;
+    return cudaSuccess;
+}
+
+// Both forms queue the whole forward at once with grids sized by the pair
+// capacity; the pair count stays on the device, which handles an overflow
+// (no pairs are written, every tile list is empty). sync = true: the plain
+// form also copies the count to the host behind an event and waits for that
+// copy alone after queueing everything, to return SG_ERR_CAPACITY (or the
+// depth sort's SG_ERR_TIMEOUT) and the count. sync = false: the batched form
+// (overflow recorded in the device status, graph capturable).
 int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, const int32_t *view_scene,
                  int n_views, void *ws, size_t ws_bytes, float *img, float *T_final, int32_t *last,
                  float *const *importance, sg_sizes *out, cudaStream_t stream, bool sync) {
@@ -413,31 +453,21 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
                                   stream, counters + CNT_STATUS, counters + CNT_VISIBLE, true),
                 "depth sort");
     }
+    CountReadback *rb = nullptr;   // plain form: where the scan leaves the pair count for the host
+    if (sync) SG_CUDA(count_readback(rb), "pair count readback");
     {
         StageTimer t(ST_OFFSETS, stream);
-        SG_CUDA(launch_scan(tt, dval0, offs, M, sums, counters + CNT_PAIRS, stream, counters + CNT_VISIBLE),
+        SG_CUDA(launch_scan(tt, dval0, offs, M, sums, counters + CNT_PAIRS, stream, counters + CNT_VISIBLE,
+                            rb ? rb->dev_ptr : nullptr, counters + CNT_STATUS),
                 "pair offsets");
     }
-    uint64_t K = cap;   // batched form: grids sized by the capacity, counts read on the device
+    // grids sized by the capacity (at most SORT_MAX_KEYS pairs); counts read on the device
+    const uint64_t cap_dev = std::min<uint64_t>(cap, SORT_MAX_KEYS);
+    uint64_t K = cap_dev;
     if (sync) {
-        uint64_t cnt_host[3] = {0, 0, 0};
-        {
-            StageTimer t(ST_READ_PAIRS, stream);
-            SG_CUDA(cudaMemcpyAsync(cnt_host, counters, sizeof(cnt_host), cudaMemcpyDeviceToHost, stream),
-                    "read pairs");
-        }
-        SG_CUDA(cudaStreamSynchronize(stream), "read pairs");
-        K = cnt_host[CNT_PAIRS];
-        if (cnt_host[CNT_STATUS] == SG_ERR_TIMEOUT)
-            return fail(SG_ERR_TIMEOUT, "depth sort: a bounded device wait expired");
-        if (K > cap || K >= (1ull << 32) - 1) {
-            const WsLayout need = make_layout(b, K);
-            fill_sizes(b, need, K, out);
-            return fail(SG_ERR_CAPACITY, "%llu pairs exceed the workspace capacity %llu (need %zu bytes)",
-                        (unsigned long long)K, (unsigned long long)cap, need.total);
-        }
+        SG_CUDA(cudaEventRecord(rb->ev, stream), "read pairs");
     } else {
-        SG_CUDA(launch_capacity_status(counters, cap, stream), "capacity status");
+        SG_CUDA(launch_capacity_status(counters, cap_dev, stream), "capacity status");
     }
     // duplicate into the buffer from which an even/odd number of tile passes ends in *_final
     uint32_t *pk_final = reinterpret_cast<uint32_t *>(w + L.pkey_final);
@@ -450,7 +480,7 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     {
         StageTimer t(ST_DUPLICATE, stream);
         // also the tile sort's digit histograms and cleared look-back flags
-        SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, rec, offs, counters, cap, k0, v0, n_views, stream,
+        SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, rec, offs, counters, cap_dev, k0, v0, n_views, stream,
                                  L.tile_passes, aux_tile, hist, sort_flag_words(K, L.tile_bits)),
                 "duplicateWithKeys");
     }
@@ -492,6 +522,23 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         SG_CUDA(cudaStreamSynchronize(stream), "read counter");
         std::lock_guard<std::mutex> g(prof().mu);
         prof().evals[0] += (int64_t)ne;
+    }
+    if (sync) {
+        SG_CUDA(cudaEventSynchronize(rb->ev), "read pairs");
+        const volatile uint64_t *mirror = rb->host;
+        const uint64_t n_pairs = mirror[0];
+        if (mirror[1] == SG_ERR_TIMEOUT)
+            return fail(SG_ERR_TIMEOUT, "depth sort: a bounded device wait expired");
+        if (n_pairs > cap_dev) {
+            const WsLayout need = make_layout(b, n_pairs);
+            fill_sizes(b, need, n_pairs, out);
+            if (n_pairs > SORT_MAX_KEYS)
+                return fail(SG_ERR_CAPACITY, "%llu pairs exceed the %llu one call can sort",
+                            (unsigned long long)n_pairs, (unsigned long long)SORT_MAX_KEYS);
+            return fail(SG_ERR_CAPACITY, "%llu pairs exceed the workspace capacity %llu (need %zu bytes)",
+                        (unsigned long long)n_pairs, (unsigned long long)cap, need.total);
+        }
+        K = n_pairs;
     }
     fill_sizes(b, L, K, out);
     return SG_OK;

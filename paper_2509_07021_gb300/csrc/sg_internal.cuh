@@ -227,10 +227,12 @@ cudaError_t launch_preprocess_backward(const Batch &hb, const Batch *db,
 
 // Exclusive scan of `in` (or of tiles_touched[idx[i]] when idx != null) into
 // `out`, total written to *total. n items (host known), or min(n, *n_dev) when
-// n_dev is given.
+// n_dev is given. mirror (nullable, host memory mapped into the device): also
+// receives the total and *status_src in its first two words.
 cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t *out,
                         uint64_t n, uint64_t *block_sums, uint64_t *total, cudaStream_t s,
-                        const uint64_t *n_dev = nullptr);
+                        const uint64_t *n_dev = nullptr, uint64_t *mirror = nullptr,
+                        const uint64_t *status_src = nullptr);
 
 // Stable LSD radix sort of (key, val) u32 pairs on bits [0, bits); item count read
 // from *n_dev and clamped to max_n (the capacity the launch is sized for, below
@@ -242,6 +244,8 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 // kept_out (nullable): drop mode — keys equal to SORT_DROP_KEY are left out, the
 // sorted kept keys fill positions [0, *kept_out) and *kept_out receives their count.
 constexpr size_t SORT_AUX_BYTES = 16384;
+// Most keys one sort takes (its look-back words carry 30-bit counts).
+constexpr uint64_t SORT_MAX_KEYS = (1ull << 30) - 1;
 constexpr uint32_t SORT_DROP_KEY = 0xFFFFFFFFu;
 // aux_zeroed: the caller has already zeroed the aux region in this stream.
 // hist_ready: the caller has also written every pass's digit histogram into

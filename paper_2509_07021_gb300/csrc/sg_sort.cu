@@ -78,8 +78,11 @@ __global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *__restrict_
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
+// mirror (nullable; host memory mapped into the device): receives the total
+// and *status_src, so the host can read both without a copy in the stream.
 __global__ void __launch_bounds__(1024) k_scan_spine(uint64_t *__restrict__ sums, uint64_t nb,
-                                                     uint64_t *__restrict__ total) {
+                                                     uint64_t *__restrict__ total, uint64_t *mirror,
+                                                     const uint64_t *status_src) {
     __shared__ uint64_t sh[33];
     const uint64_t per = div_up(nb, 1024);
     const uint64_t lo = threadIdx.x * per, hi = min(nb, lo + per);
@@ -93,6 +96,10 @@ __global__ void __launch_bounds__(1024) k_scan_spine(uint64_t *__restrict__ sums
         run += v;
     }
     if (threadIdx.x == 0 && total) *total = tot;
+    if (threadIdx.x == 0 && mirror) {
+        mirror[0] = tot;
+        mirror[1] = status_src ? *status_src : 0;
+    }
 }
 
 __global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ in,
@@ -138,15 +145,21 @@ __global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ 
 }
 
 cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t *out, uint64_t n,
-                        uint64_t *block_sums, uint64_t *total, cudaStream_t s, const uint64_t *n_dev) {
+                        uint64_t *block_sums, uint64_t *total, cudaStream_t s, const uint64_t *n_dev,
+                        uint64_t *mirror, const uint64_t *status_src) {
     const uint64_t nb = div_up(n, SCAN_TILE);
     if (nb == 0) {
+        if (mirror) {   // the spine alone writes the zero total
+            k_scan_spine<<<1, 1024, 0, s>>>(block_sums, 0, total, mirror, status_src);
+            count_launches(1);
+            return cudaGetLastError();
+        }
         if (total) return cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
         return cudaSuccess;
     }
     k_scan_reduce<<<(unsigned)nb, 256, 0, s>>>(in, gather_idx, n, n_dev, block_sums);
     count_launches(1);
-    k_scan_spine<<<1, 1024, 0, s>>>(block_sums, nb, total);
+    k_scan_spine<<<1, 1024, 0, s>>>(block_sums, nb, total, mirror, status_src);
     count_launches(1);
     k_scan_down<<<(unsigned)nb, 256, 0, s>>>(in, gather_idx, n, n_dev, block_sums, out);
     count_launches(1);
@@ -168,6 +181,7 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 
 // packed look-back word: 2 status bits, 30 count bits
 constexpr uint32_t LB_AGG = 1u << 30, LB_INC = 2u << 30, LB_VAL = (1u << 30) - 1u;
+static_assert(LB_VAL == SORT_MAX_KEYS, "look-back count width");
 constexpr int LB_SPIN_LIMIT = 1 << 20;
 constexpr int LB_WINDOW = 16;
 
