@@ -552,179 +552,197 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
     geo3_recipe(s0, s1, s2, q0, q1, q2, q3, g3);
     float dS[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 
-    for (int v = 0; v < b.n_views; ++v) {
-        const ViewDesc &vw = b.view[v];
-        if (vw.scene != si) continue;
-        const uint64_t e = vw.ent_off + (uint64_t)g;
-        // With one view, every load is issued before the visibility test (the
-        // latency of the test is hidden); with several, most entries reach no
-        // tile and their gradient loads are skipped.
-        const uint32_t tte = tiles_touched[e];
-        if (multi_view && tte == 0u) continue;
-        const float gx = dg[e], gy = dg[M + e], gA = dg[2 * M + e], gB = dg[3 * M + e],
-                    gC = dg[4 * M + e], gop = dg[5 * M + e];
-        const float grgb[3] = {dg[6 * M + e], dg[7 * M + e], dg[8 * M + e]};
-        const uint32_t cl = clamp[e];
-        if (tte == 0u) continue;
-        // the forward's clamp max(c, 0) per channel, read back from its bits
-        const float gc[3] = {(cl & 1u) ? 0.f : grgb[0], (cl & 2u) ? 0.f : grgb[1], (cl & 4u) ? 0.f : grgb[2]};
-
-        // o' = m_g * o
-        d_opac += gm * gop;
-        d_gmask += o * gop;
-
-        // ---- colour (Eq. 2) ----
-        float vx = px - vw.campos[0], vy = py - vw.campos[1], vz = pz - vw.campos[2];
-        const float dn = sqrtf(vx * vx + vy * vy + vz * vz);
-        const float idn = 1.0f / dn;
-        vx *= idn; vy *= idn; vz *= idn;
-        float dvx = 0.f, dvy = 0.f, dvz = 0.f;
-        if (sh_mode) {
-            // c = 0.5 + sum_k Y_k(v) sh_k per channel
-            float Y[16];
-            sh3_basis(vx, vy, vz, Y);
-            float w[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                w[k] = 0.f;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) w[k] = fmaf(gc[ch], __ldg(sc.sh + (int64_t)(ch * 16 + k) * n + g), w[k]);
-            }
-            sh3_grad_acc(vx, vy, vz, w, dvx, dvy, dvz);
-            float *gsh = sc.grads.sh;
-            if (gsh) {
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch)
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        float *dst = gsh + (int64_t)(ch * 16 + k) * n + g;
-                        *dst = first ? Y[k] * gc[ch] : *dst + Y[k] * gc[ch];
-                    }
+    // With several views, the views whose entry of this Gaussian reaches a tile
+    // are found first, 32 at a time, with independent loads (one memory round
+    // trip instead of one per view); the others need no gradient work.
+    for (int v0 = 0; v0 < b.n_views; v0 += 32) {
+        uint32_t live = 1u;   // one view: view 0 (its test follows the eager loads below)
+        if (multi_view) {
+            live = 0u;
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+                const int v = v0 + i;
+                if (v < b.n_views && b.view[v].scene == si &&
+                    tiles_touched[b.view[v].ent_off + (uint64_t)g] != 0u)
+                    live |= 1u << i;
             }
         }
-        if (!sh_mode) {
-            d_c0[0] += gc[0];
-            d_c0[1] += gc[1];
-            d_c0[2] += gc[2];
-        }
-        for (int k0 = lo; k0 < hi; k0 += LOBE_CHUNK) {
-            LobeChunk<DL, DS> lc;
-            lc.load(sc, k0, hi);
+        while (live) {
+            const int v = v0 + __ffs(live) - 1;
+            live &= live - 1u;
+            const ViewDesc &vw = b.view[v];
+            const uint64_t e = vw.ent_off + (uint64_t)g;
+            // With one view, every load is issued before the visibility test (the
+            // latency of the test is hidden).
+            const uint32_t tte = multi_view ? 1u : tiles_touched[e];
+            const float gx = dg[e], gy = dg[M + e], gA = dg[2 * M + e], gB = dg[3 * M + e],
+                        gC = dg[4 * M + e], gop = dg[5 * M + e];
+            const float grgb[3] = {dg[6 * M + e], dg[7 * M + e], dg[8 * M + e]};
+            const uint32_t cl = clamp[e];
+            if (tte == 0u) continue;
+            // the forward's clamp max(c, 0) per channel, read back from its bits
+            const float gc[3] = {(cl & 1u) ? 0.f : grgb[0], (cl & 2u) ? 0.f : grgb[1], (cl & 4u) ? 0.f : grgb[2]};
+
+            // o' = m_g * o
+            d_opac += gm * gop;
+            d_gmask += o * gop;
+
+            // ---- colour (Eq. 2) ----
+            float vx = px - vw.campos[0], vy = py - vw.campos[1], vz = pz - vw.campos[2];
+            const float dn = sqrtf(vx * vx + vy * vy + vz * vz);
+            const float idn = 1.0f / dn;
+            vx *= idn; vy *= idn; vz *= idn;
+            float dvx = 0.f, dvy = 0.f, dvz = 0.f;
+            if (sh_mode) {
+                // c = 0.5 + sum_k Y_k(v) sh_k per channel
+                float Y[16];
+                sh3_basis(vx, vy, vz, Y);
+                float w[16];
 #pragma unroll
-            for (int u = 0; u < LOBE_CHUNK; ++u) {
-                const int k = k0 + u;
-                if (k >= hi) break;
-                const float ax = lc.ax[u], ay = lc.ay[u], az = lc.az[u];
-                const float na = sqrtf(ax * ax + ay * ay + az * az);
-                const float ia = 1.0f / na;
-                const float mx = ax * ia, my = ay * ia, mz = az * ia;
-                const float dot = mx * vx + my * vy + mz * vz;
-                const float sh = lc.sh[u];
-                const float ex = expf(sh * (dot - 1.0f));
-                const float m = lc.m[u];
-                const float a0 = lc.a0[u], a1 = lc.a1[u], a2 = lc.a2[u];
-                const float ga = a0 * gc[0] + a1 * gc[1] + a2 * gc[2];
-                const float de = m * ga;
-                const float dd = de * ex * sh;                 // dL/d(mu_hat . v)
-                const float gmx = dd * vx, gmy = dd * vy, gmz = dd * vz;   // dL/dmu_hat
-                const float pr = mx * gmx + my * gmy + mz * gmz;
-                dvx += dd * mx; dvy += dd * my; dvz += dd * mz;
-                float ga_out[3] = {m * ex * gc[0], m * ex * gc[1], m * ex * gc[2]};
-                float gax[3] = {(gmx - mx * pr) * ia, (gmy - my * pr) * ia, (gmz - mz * pr) * ia};
-                const float gs = de * ex * (dot - 1.0f);
-                const float gml = ex * ga;
-                const sg_grads &gr = sc.grads;
-                if (first) {
-                    if (gr.amp) { gr.amp[k] = ga_out[0]; gr.amp[L + k] = ga_out[1]; gr.amp[2 * L + k] = ga_out[2]; }
-                    if (gr.axis) { gr.axis[k] = gax[0]; gr.axis[L + k] = gax[1]; gr.axis[2 * L + k] = gax[2]; }
-                    if (gr.sharp) gr.sharp[k] = gs;
-                    if (gr.lmask) gr.lmask[k] = gml;
-                } else {
-                    if (gr.amp) { gr.amp[k] += ga_out[0]; gr.amp[L + k] += ga_out[1]; gr.amp[2 * L + k] += ga_out[2]; }
-                    if (gr.axis) { gr.axis[k] += gax[0]; gr.axis[L + k] += gax[1]; gr.axis[2 * L + k] += gax[2]; }
-                    if (gr.sharp) gr.sharp[k] += gs;
-                    if (gr.lmask) gr.lmask[k] += gml;
+                for (int k = 0; k < 16; ++k) {
+                    w[k] = 0.f;
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch)
+                        w[k] = fmaf(gc[ch], __ldg(sc.sh + (int64_t)(ch * 16 + k) * n + g), w[k]);
+                }
+                sh3_grad_acc(vx, vy, vz, w, dvx, dvy, dvz);
+                float *gsh = sc.grads.sh;
+                if (gsh) {
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            float *dst = gsh + (int64_t)(ch * 16 + k) * n + g;
+                            *dst = first ? Y[k] * gc[ch] : *dst + Y[k] * gc[ch];
+                        }
                 }
             }
-        }
-        first = false;
-        // v = (p - cam) / |p - cam|
-        {
-            const float pr = vx * dvx + vy * dvy + vz * dvz;
-            d_mean[0] += (dvx - vx * pr) * idn;
-            d_mean[1] += (dvy - vy * pr) * idn;
-            d_mean[2] += (dvz - vz * pr) * idn;
-        }
+            if (!sh_mode) {
+                d_c0[0] += gc[0];
+                d_c0[1] += gc[1];
+                d_c0[2] += gc[2];
+            }
+            for (int k0 = lo; k0 < hi; k0 += LOBE_CHUNK) {
+                LobeChunk<DL, DS> lc;
+                lc.load(sc, k0, hi);
+#pragma unroll
+                for (int u = 0; u < LOBE_CHUNK; ++u) {
+                    const int k = k0 + u;
+                    if (k >= hi) break;
+                    const float ax = lc.ax[u], ay = lc.ay[u], az = lc.az[u];
+                    const float na = sqrtf(ax * ax + ay * ay + az * az);
+                    const float ia = 1.0f / na;
+                    const float mx = ax * ia, my = ay * ia, mz = az * ia;
+                    const float dot = mx * vx + my * vy + mz * vz;
+                    const float sh = lc.sh[u];
+                    const float ex = expf(sh * (dot - 1.0f));
+                    const float m = lc.m[u];
+                    const float a0 = lc.a0[u], a1 = lc.a1[u], a2 = lc.a2[u];
+                    const float ga = a0 * gc[0] + a1 * gc[1] + a2 * gc[2];
+                    const float de = m * ga;
+                    const float dd = de * ex * sh;                 // dL/d(mu_hat . v)
+                    const float gmx = dd * vx, gmy = dd * vy, gmz = dd * vz;   // dL/dmu_hat
+                    const float pr = mx * gmx + my * gmy + mz * gmz;
+                    dvx += dd * mx; dvy += dd * my; dvz += dd * mz;
+                    float ga_out[3] = {m * ex * gc[0], m * ex * gc[1], m * ex * gc[2]};
+                    float gax[3] = {(gmx - mx * pr) * ia, (gmy - my * pr) * ia, (gmz - mz * pr) * ia};
+                    const float gs = de * ex * (dot - 1.0f);
+                    const float gml = ex * ga;
+                    const sg_grads &gr = sc.grads;
+                    if (first) {
+                        if (gr.amp) { gr.amp[k] = ga_out[0]; gr.amp[L + k] = ga_out[1]; gr.amp[2 * L + k] = ga_out[2]; }
+                        if (gr.axis) { gr.axis[k] = gax[0]; gr.axis[L + k] = gax[1]; gr.axis[2 * L + k] = gax[2]; }
+                        if (gr.sharp) gr.sharp[k] = gs;
+                        if (gr.lmask) gr.lmask[k] = gml;
+                    } else {
+                        if (gr.amp) {
+                            gr.amp[k] += ga_out[0]; gr.amp[L + k] += ga_out[1]; gr.amp[2 * L + k] += ga_out[2];
+                        }
+                        if (gr.axis) { gr.axis[k] += gax[0]; gr.axis[L + k] += gax[1]; gr.axis[2 * L + k] += gax[2]; }
+                        if (gr.sharp) gr.sharp[k] += gs;
+                        if (gr.lmask) gr.lmask[k] += gml;
+                    }
+                }
+            }
+            first = false;
+            // v = (p - cam) / |p - cam|
+            {
+                const float pr = vx * dvx + vy * dvy + vz * dvz;
+                d_mean[0] += (dvx - vx * pr) * idn;
+                d_mean[1] += (dvy - vy * pr) * idn;
+                d_mean[2] += (dvz - vz * pr) * idn;
+            }
 
-        // ---- geometry: recompute the projection (after the colour part, so that
-        // its intermediates are not live across the lobe loop) ----
-        Geo G;
-        project_view(vw, px, py, pz, g3, o, gm, G);
+            // ---- geometry: recompute the projection (after the colour part, so that
+            // its intermediates are not live across the lobe loop) ----
+            Geo G;
+            project_view(vw, px, py, pz, g3, o, gm, G);
 
-        // ---- projected centre: x = fx t_x / t_z + cx - 0.5 ----
-        const float itz = 1.0f / G.tz;
-        float dtx = vw.fx * itz * gx;
-        float dty = vw.fy * itz * gy;
-        float dtz = -(vw.fx * G.tx * gx + vw.fy * G.ty * gy) * itz * itz;
+            // ---- projected centre: x = fx t_x / t_z + cx - 0.5 ----
+            const float itz = 1.0f / G.tz;
+            float dtx = vw.fx * itz * gx;
+            float dty = vw.fy * itz * gy;
+            float dtz = -(vw.fx * G.tx * gx + vw.fy * G.ty * gy) * itz * itz;
 
-        // ---- conic (A, B, C) = (c, -b, a) / det ----
-        const float a = G.ca, bb = G.cb, c = G.cc;
-        const float id2 = 1.0f / (G.det * G.det);
-        const float da = (-c * c * gA + bb * c * gB - bb * bb * gC) * id2;
-        const float db = (2.f * bb * c * gA - (a * c + bb * bb) * gB + 2.f * a * bb * gC) * id2;
-        const float dc = (-bb * bb * gA + a * bb * gB - a * a * gC) * id2;
+            // ---- conic (A, B, C) = (c, -b, a) / det ----
+            const float a = G.ca, bb = G.cb, c = G.cc;
+            const float id2 = 1.0f / (G.det * G.det);
+            const float da = (-c * c * gA + bb * c * gB - bb * bb * gC) * id2;
+            const float db = (2.f * bb * c * gA - (a * c + bb * bb) * gB + 2.f * a * bb * gC) * id2;
+            const float dc = (-bb * bb * gA + a * bb * gB - a * a * gC) * id2;
 
-        // ---- Sigma_2D = A Sigma A^T (A = J W) ----
-        float SA0[3], SA1[3];
+            // ---- Sigma_2D = A Sigma A^T (A = J W) ----
+            float SA0[3], SA1[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            SA0[i] = G.S[i][0] * G.A[0][0] + G.S[i][1] * G.A[0][1] + G.S[i][2] * G.A[0][2];
-            SA1[i] = G.S[i][0] * G.A[1][0] + G.S[i][1] * G.A[1][1] + G.S[i][2] * G.A[1][2];
+            for (int i = 0; i < 3; ++i) {
+                SA0[i] = G.S[i][0] * G.A[0][0] + G.S[i][1] * G.A[0][1] + G.S[i][2] * G.A[0][2];
+                SA1[i] = G.S[i][0] * G.A[1][0] + G.S[i][1] * G.A[1][1] + G.S[i][2] * G.A[1][2];
+            }
+            float dA0[3], dA1[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                dA0[i] = 2.f * da * SA0[i] + db * SA1[i];
+                dA1[i] = db * SA0[i] + 2.f * dc * SA1[i];
+            }
+            // symmetric gradient w.r.t. Sigma_3D, then M (Sigma = M M^T)
+            float Gs[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    Gs[i][j] = 2.f * da * G.A[0][i] * G.A[0][j] +
+                               db * (G.A[0][i] * G.A[1][j] + G.A[1][i] * G.A[0][j]) +
+                               2.f * dc * G.A[1][i] * G.A[1][j];
+            // dL/dSigma_3D summed over the views; chained to scale and rotation once
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) dS[i][j] += Gs[i][j];
+            // J entries
+            const float *V = vw.V;
+            const float dJ00 = dA0[0] * V[0] + dA0[1] * V[1] + dA0[2] * V[2];
+            const float dJ02 = dA0[0] * V[8] + dA0[1] * V[9] + dA0[2] * V[10];
+            const float dJ11 = dA1[0] * V[4] + dA1[1] * V[5] + dA1[2] * V[6];
+            const float dJ12 = dA1[0] * V[8] + dA1[1] * V[9] + dA1[2] * V[10];
+            const float itz2 = itz * itz;
+            dtz += -(vw.fx * dJ00 + vw.fy * dJ11) * itz2;
+            {
+                const float limx = 1.3f * (0.5f * (float)vw.W / vw.fx);
+                const float limy = 1.3f * (0.5f * (float)vw.H / vw.fy);
+                const bool inx = G.ux >= -limx && G.ux <= limx;
+                const bool iny = G.uy >= -limy && G.uy <= limy;
+                // J02 = -fx ccx / tz^2, ccx = clamp(tx/tz) tz
+                const float dccx = -vw.fx * itz2 * dJ02;
+                const float dccy = -vw.fy * itz2 * dJ12;
+                dtz += 2.f * vw.fx * G.ccx * itz2 * itz * dJ02 + 2.f * vw.fy * G.ccy * itz2 * itz * dJ12;
+                if (inx) dtx += dccx; else dtz += dccx * fminf(limx, fmaxf(-limx, G.ux));
+                if (iny) dty += dccy; else dtz += dccy * fminf(limy, fmaxf(-limy, G.uy));
+            }
+            // t = W p + t
+            d_mean[0] += V[0] * dtx + V[4] * dty + V[8] * dtz;
+            d_mean[1] += V[1] * dtx + V[5] * dty + V[9] * dtz;
+            d_mean[2] += V[2] * dtx + V[6] * dty + V[10] * dtz;
         }
-        float dA0[3], dA1[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            dA0[i] = 2.f * da * SA0[i] + db * SA1[i];
-            dA1[i] = db * SA0[i] + 2.f * dc * SA1[i];
-        }
-        // symmetric gradient w.r.t. Sigma_3D, then M (Sigma = M M^T)
-        float Gs[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                Gs[i][j] = 2.f * da * G.A[0][i] * G.A[0][j] +
-                           db * (G.A[0][i] * G.A[1][j] + G.A[1][i] * G.A[0][j]) +
-                           2.f * dc * G.A[1][i] * G.A[1][j];
-        // dL/dSigma_3D summed over the views; chained to scale and rotation once
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) dS[i][j] += Gs[i][j];
-        // J entries
-        const float *V = vw.V;
-        const float dJ00 = dA0[0] * V[0] + dA0[1] * V[1] + dA0[2] * V[2];
-        const float dJ02 = dA0[0] * V[8] + dA0[1] * V[9] + dA0[2] * V[10];
-        const float dJ11 = dA1[0] * V[4] + dA1[1] * V[5] + dA1[2] * V[6];
-        const float dJ12 = dA1[0] * V[8] + dA1[1] * V[9] + dA1[2] * V[10];
-        const float itz2 = itz * itz;
-        dtz += -(vw.fx * dJ00 + vw.fy * dJ11) * itz2;
-        {
-            const float limx = 1.3f * (0.5f * (float)vw.W / vw.fx);
-            const float limy = 1.3f * (0.5f * (float)vw.H / vw.fy);
-            const bool inx = G.ux >= -limx && G.ux <= limx;
-            const bool iny = G.uy >= -limy && G.uy <= limy;
-            // J02 = -fx ccx / tz^2, ccx = clamp(tx/tz) tz
-            const float dccx = -vw.fx * itz2 * dJ02;
-            const float dccy = -vw.fy * itz2 * dJ12;
-            dtz += 2.f * vw.fx * G.ccx * itz2 * itz * dJ02 + 2.f * vw.fy * G.ccy * itz2 * itz * dJ12;
-            if (inx) dtx += dccx; else dtz += dccx * fminf(limx, fmaxf(-limx, G.ux));
-            if (iny) dty += dccy; else dtz += dccy * fminf(limy, fmaxf(-limy, G.uy));
-        }
-        // t = W p + t
-        d_mean[0] += V[0] * dtx + V[4] * dty + V[8] * dtz;
-        d_mean[1] += V[1] * dtx + V[5] * dty + V[9] * dtz;
-        d_mean[2] += V[2] * dtx + V[6] * dty + V[10] * dtz;
     }
 
     const sg_grads &gr = sc.grads;
