@@ -556,7 +556,9 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
     // are found first, 32 at a time, with independent loads (one memory round
     // trip instead of one per view); the others need no gradient work.
     for (int v0 = 0; v0 < b.n_views; v0 += 32) {
-        uint32_t live = 1u;   // one view: view 0 (its test follows the eager loads below)
+        // one view: view 0 when it sees this Gaussian's scene (its tile test
+        // follows the eager loads below)
+        uint32_t live = b.view[0].scene == si ? 1u : 0u;
         if (multi_view) {
             live = 0u;
 #pragma unroll 8

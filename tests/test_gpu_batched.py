@@ -161,3 +161,31 @@ def test_batched_one_or_two_tiles(sizes):
     n, st = br.status()
     assert st == sgsplat.SG_OK and 0 < n <= br.capacity
     _check_batched(br, [scene], cams, [0] * len(cams), seed=7)
+
+
+def test_batched_scene_without_views():
+    """Two scenes and one view that sees only the smaller one: the larger scene
+    has no view, so its gradients are zero, and the seen scene's gradients are
+    the one-view oracle's (the adjoint's one-view path tests the view's scene)."""
+    rng = np.random.default_rng(730)
+    scenes = [synth.make_scene(rng, n, lobes=synth.LOBE_MIX, means="cube", cube_side=1.3, masks="uniform")
+              for n in (4100, 700)]
+    cams = [synth.make_camera(40, 40, 45.0)]
+    view_scene = [1]
+    ds = [DeviceScene.from_host(s) for s in scenes]
+    br = render.BatchedRenderer(ds, cams, view_scene)
+    br.forward()
+    n, st = br.status()
+    assert st == sgsplat.SG_OK and 0 < n <= br.capacity
+    res, _ = oracle.render(scenes[1], cams)
+    img, T, last = (_flat_views(t, cams, ch)[0] for t, ch in ((br.img, 3), (br.T_final, 1), (br.last, 1)))
+    check_image(img, T, last, res[0], cams[0])
+    dimgs = masked_dimg(np.random.default_rng(731), cams, res)
+    for g in br.grads[0].values():
+        g.fill_(7.0)   # gradients are overwritten, never accumulated
+    br.backward(torch.from_numpy(dimgs[0].reshape(-1)).cuda())
+    torch.cuda.synchronize()
+    for k, v in br.grads[0].items():
+        assert torch.count_nonzero(v) == 0, k
+    _, g = oracle.render(scenes[1], cams, dimgs=dimgs)
+    check_grads(br.grads[1], g)
