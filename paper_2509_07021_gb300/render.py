@@ -137,6 +137,111 @@ class HostStep:
         return self.host_img, self.host_grads
 
 
+@dataclass
+class _Slot:
+    scene: DeviceScene
+    grads: dict
+    d_img: torch.Tensor | None = None
+    bwd_done: torch.cuda.Event | None = None    # last step using the slot finished its backward
+    down_done: torch.cuda.Event | None = None   # ... and its gradients are on the host
+
+
+class PipelinedStep:
+    """Handle of one queued HostPipeline step."""
+
+    def __init__(self, done: torch.cuda.Event, host_img, host_grads):
+        self.done, self.host_img, self.host_grads = done, host_img, host_grads
+
+    def wait(self):
+        """Blocks until the step's image and gradients are in its host buffers."""
+        self.done.synchronize()
+        return self.host_img, self.host_grads
+
+
+class HostPipeline:
+    """Host-resident forward + backward steps queued back to back, with the
+    copies of neighbouring steps overlapped (a training or serving loop whose
+    scenes, upstream gradients, images and gradients live in pinned host memory).
+
+    Two device slots (scene, upstream gradient, gradients) alternate between
+    steps. Step i computes on the caller's stream while step i+1's scene and
+    upstream gradient go up on an upload stream and step i-1's image and
+    gradients come down on a download stream; each copy waits only for the
+    step that last used its slot. The per-step copies are the same as
+    HostStep's; they leave the critical path when steps follow one another.
+
+    submit() queues one step (it returns once the forward's pair count is
+    known, as render_forward does) and gives a handle whose wait() returns
+    once that step's image and gradients are in its host buffers; finish()
+    waits for every queued step. Host input buffers must stay unchanged, and
+    host output buffers unread, until the step's wait() returns.
+    """
+
+    def __init__(self, like: DeviceScene, cams):
+        self.cams = cams
+        self.dev = like.means.device
+        self.slots = []
+        for _ in range(2):
+            kw = {k: torch.empty_like(getattr(like, k)) for k in like.FLOAT_FIELDS + ("lobe_off",)}
+            scene = DeviceScene(dtype_geom=like.dtype_geom, dtype_lobe=like.dtype_lobe,
+                                dtype_sharp=like.dtype_sharp,
+                                sh=None if like.sh is None else torch.empty_like(like.sh), **kw)
+            self.slots.append(_Slot(scene, alloc_grads(scene)))
+        self.up = torch.cuda.Stream(device=self.dev)
+        self.down = torch.cuda.Stream(device=self.dev)
+        self.i = 0
+
+    def submit(self, host_scene: dict, host_d_img, host_img, host_grads: dict) -> PipelinedStep:
+        slot = self.slots[self.i & 1]
+        main = torch.cuda.current_stream(self.dev)
+        fresh = slot.bwd_done is None
+        if slot.d_img is None or slot.d_img.shape != host_d_img.shape:
+            slot.d_img = torch.empty(host_d_img.shape, dtype=host_d_img.dtype, device=self.dev)
+            fresh = True
+        with torch.cuda.stream(self.up):
+            if fresh:
+                # memory allocated on the caller's stream may be a block that work
+                # still queued there uses (the caching allocator orders it after
+                # that work only on the caller's stream)
+                self.up.wait_stream(main)
+            else:                           # the slot's previous step has read its inputs
+                self.up.wait_event(slot.bwd_done)
+            for k, t in host_scene.items():
+                getattr(slot.scene, k).copy_(t, non_blocking=True)
+            slot.d_img.copy_(host_d_img, non_blocking=True)
+            up_done = self.up.record_event()
+        main.wait_event(up_done)
+        out = render_forward(slot.scene, self.cams)
+        if slot.down_done is not None:      # the slot's previous gradients are on the host
+            main.wait_event(slot.down_done)
+        render_backward(slot.scene, self.cams, out, slot.d_img, slot.grads)
+        slot.bwd_done = main.record_event()
+        with torch.cuda.stream(self.down):
+            self.down.wait_event(slot.bwd_done)
+            host_img.copy_(out.img.view(host_img.shape), non_blocking=True)
+            for k, t in host_grads.items():
+                t.copy_(slot.grads[k], non_blocking=True)
+            slot.down_done = self.down.record_event()
+        out.img.record_stream(self.down)
+        self.i += 1
+        return PipelinedStep(slot.down_done, host_img, host_grads)
+
+    def finish(self):
+        """Waits for every queued step."""
+        for slot in self.slots:
+            if slot.down_done is not None:
+                slot.down_done.synchronize()
+
+    @staticmethod
+    def bytes_moved(host_scene: dict, host_d_img, host_img, host_grads: dict):
+        """Host->device and device->host bytes of one step."""
+        up = sum(t.numel() * t.element_size() for t in host_scene.values())
+        up += host_d_img.numel() * host_d_img.element_size()
+        down = host_img.numel() * host_img.element_size()
+        down += sum(t.numel() * t.element_size() for t in host_grads.values())
+        return up, down
+
+
 class SGRasterize(torch.autograd.Function):
     """img, T_final, last = SGRasterize.apply(means, scales, quats, opac, gmask, c0,
     lobe_off, axis, sharp, amp, lmask, cams)
