@@ -33,8 +33,10 @@ METRIC = "fwd+bwd ms/view & Mpixel/s (1080p, 1M Gaussians, ≤4 SG); batched vs 
 UNIT = "Mpixel/s"
 L2_FLUSH_BYTES = 512 << 20
 
-# Algorithmic FP32 work per evaluated (pixel, Gaussian) pair, FMA = 2 flops
-# (derivation in the design doc): forward 23, backward 69.
+# Algorithmic FP32 work per evaluated (pixel, Gaussian) pair, FMA = 2 flops:
+# forward 23 (quadratic form, exponent, alpha tests, transmittance and colour
+# update), backward 69 (about 14 for power and alpha, 46 for the adjoint, 9 for
+# the warp reduction amortised over the pairs).
 FLOPS_PER_EVAL = {"blend_fwd": 23.0, "blend_bwd": 69.0}
 TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic_1m_1080p.md")
 

@@ -8,14 +8,15 @@ input generator, which holds none of the method's arithmetic).
 What it follows:
   * SG lobe and colour model, Eq. 1-2 (Sec. 3.2): c(v) = c0 + sum_i a_i e^{s_i(mu_i.v - 1)}.
     The degree-3 SH colour of the 3DGS baseline it replaces is in sg_sh_oracle.py.
-    Soft-pruning masks (the BASELINE form of Sec. 3.3's soft pruning): m_l multiplies the
+    Soft-pruning masks (a differentiable form of Sec. 3.3's pruning): m_l multiplies the
     whole lobe term, m_g multiplies opacity.
   * Primitive model and front-to-back compositing, Sec. 3.1: a Gaussian with centre mu,
     covariance Sigma = R S S^T R^T, opacity o, projected with the EWA Jacobian and blended
     as C = sum_i c_i alpha_i prod_{j<i}(1 - alpha_j).
   * The compositing rules inherited from 3DGS that the paper keeps (0.3 px low-pass
     dilation, 3-sigma radius, 16x16 tiles, 1/255 skip, 0.99 clamp, 1e-4 stop, near plane
-    0.2, 1.3x guard band) -- the readings are listed in the design doc.
+    0.2, 1.3x guard band): the paper states only the blend sum, so these are read as the
+    rules of the rasterizer it builds on.
 
 Discrete decisions (cull, radius, tile rectangle, depth key) are taken with the
 binary32 recipe below, the same recipe the GPU uses, so that tile lists can be
@@ -133,7 +134,7 @@ def _clamp_tile(f, n):
 
 def decisions_fp32(scene, cam) -> Decisions:
     """Cull / radius / tile rectangle / depth key in binary32, one rounding per
-    operation in the written order, no fused multiply-add (the design doc lists the recipe)."""
+    operation in the written order, no fused multiply-add (the steps below are the recipe)."""
     with np.errstate(all="ignore"):
         p = scene.means.astype(F32)
         V = cam.viewmat.astype(F32)

@@ -375,6 +375,19 @@ class BatchedRenderer:
         self.graph.replay()
 
 
+def render_batched(scenes, cams, view_scene=None, **kw) -> BatchedRenderer:
+    """Renders many scenes x cameras in one forward call: view_scene[v] is the
+    scene of camera v (all scene 0 when omitted). Returns the BatchedRenderer
+    holding the flat outputs (img, T_final, last, view_image(v)); its
+    backward(d_img) gives every scene's gradients, summed over its views.
+    Keyword arguments go to BatchedRenderer (headroom, pair_capacity)."""
+    if view_scene is None:
+        view_scene = [0] * len(cams)
+    r = BatchedRenderer(scenes, cams, view_scene, **kw)
+    r.forward()
+    return r
+
+
 def l1_loss_grad(renderer: BatchedRenderer, targets):
     """Upstream gradient of the per-view mean L1 loss against `targets`
     (flat, packed like img), summed over views: sign(img - target) / (3 H W)."""

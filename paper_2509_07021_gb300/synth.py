@@ -18,7 +18,7 @@ Scene layout (planar structure of arrays, float32 unless stated):
 
 The distributions follow the workloads the paper trains on (0.4-2.7 M
 Gaussians per scene, Table 13; 0-3 lobes after pruning, Fig. 5) scaled to the
-five benchmark configurations described in the design doc.
+five benchmark workloads built by config0() .. config4() below.
 """
 from __future__ import annotations
 
@@ -246,7 +246,7 @@ def rng_for(config: int, salt: int = 0):
 
 
 # ---------------------------------------------------------------------------
-# The five workloads (sizes stated in the design doc)
+# The five workloads
 # ---------------------------------------------------------------------------
 
 def config0():

@@ -74,6 +74,22 @@ def test_batched_multi_scene_parity(persistent):
         sgsplat.sg_set_tuning(**old)
 
 
+def test_render_batched_function():
+    """render.render_batched: one call renders every view; the same outputs as a
+    BatchedRenderer driven by hand."""
+    scenes, cams, view_scene = _batch(5)
+    ds = [DeviceScene.from_host(s) for s in scenes]
+    r = render.render_batched(ds, cams, view_scene)
+    br = render.BatchedRenderer(ds, cams, view_scene)
+    br.forward()
+    torch.cuda.synchronize()
+    assert torch.equal(r.img, br.img) and torch.equal(r.T_final, br.T_final) and torch.equal(r.last, br.last)
+    for v, cam in enumerate(cams):
+        res, _ = oracle.render(scenes[view_scene[v]], [cam])
+        check_image(*(_flat_views(t, cams, ch)[v] for t, ch in ((r.img, 3), (r.T_final, 1), (r.last, 1))),
+                    res[0], cam)
+
+
 def test_persistent_plain_form():
     scenes, cams, _ = _batch(1)
     old = sgsplat.sg_get_tuning()
