@@ -276,6 +276,14 @@ def cpu_baseline_line(scene, cam, d_img, n_tiles):
     dt = time.perf_counter() - t0
     line["small_forward"] = {"ms_per_view": 1e3 * dt, "workload": "1,000 Gaussians x 3 lobes, 128x128, "
                              "forward only, whole frame", "cores": threads}
+    s1, c1, _ = synth.config1()
+    d1 = synth.upstream_grad(np.random.default_rng(synth.SEED_BASE + 11), c1[0])
+    n1 = max(4, n_tiles // 3)
+    total_h, est_h, _ = oracle_sample(s1, c1[0], d1, n1, seed=2)
+    line["half_million"] = {"value": mpx / est_h, "unit": UNIT, "s_per_view": est_h, "cores": threads,
+                            "workload": "500k Gaussians, 1920x1080, lobes 0-4, fwd+bwd",
+                            "sample": f"full-frame preprocess + tile sort, blend on {n1} random tiles "
+                                      f"scaled to the frame ({total_h:.1f} s wall)"}
     return line
 
 
