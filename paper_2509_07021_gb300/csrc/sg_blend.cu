@@ -448,8 +448,10 @@ __device__ __forceinline__ void bwd_adjoint(const PairEval &p, float dy, const f
 // keeping Sg = sum over later pairs of (c . g) alpha T, so that
 //   dL/dalpha_i = T_i (c_i . g) - (Sg + T_final (bg . g)) / (1 - alpha_i).
 // Per-thread sums over its P pixels are reduced over the warp before the
-// atomics. Accumulated per pair (in dg order):
-//   0,1: dL/dx, dL/dy   2..4: dL/dA, dL/dB, dL/dC   5: dL/do'   6..8: dL/drgb
+// atomics. Accumulated per pair (in dg order), with dG = dL/dalpha G (so that
+// dL/dpower = o' dG) and (dx, dy) = pixel - centre:
+//   0,1: sum dG dx, sum dG dy   2..4: sum dG dx^2, sum dG dx dy, sum dG dy^2
+//   5: dL/do' = sum dG   6..8: dL/drgb
 template <int P, bool COUNT>
 __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, StagedB &sm, int *smax,
                                                const uint2 *__restrict__ ranges,
@@ -547,20 +549,9 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
                     bwd_adjoint(pe[hh], row.dy, r, bl, T[j], Sg[j], g0[j], g1[j], g2[j], v);
                 }
             }
-            if (__any_sync(0xffffffffu, any)) {
-                // power log2(e) = qa dx^2 + qb dx dy + qc dy^2 with (qa, qb, qc) =
-                // -log2(e) (A/2, B, C/2), dL/dpower = o' dG and d/dx = -d/d(dx):
-                //   dL/dx = -o' sum dG (2 qa dx + qb dy) / log2(e), likewise dL/dy,
-                //   dL/dA = -o' sum dG dx^2 / 2, dL/dB = -o' sum dG dx dy, dL/dC = -o' sum dG dy^2 / 2
-                const float o = r.y, kxy = -o * (1.f / LOG2E);
-                const float sx = v[0], sy = v[1];
-                v[0] = kxy * fmaf(2.f * q.z, sx, q.w * sy);
-                v[1] = kxy * fmaf(2.f * r.x, sy, q.w * sx);
-                v[2] *= -0.5f * o;
-                v[3] *= -o;
-                v[4] *= -0.5f * o;
-                warp_sum9_atomic(v, dg, M, sm.id[k]);
-            }
+            // the moments are linear in dG: the conic factors and o' are applied
+            // once per entry by the preprocess adjoint, after the sum over tiles
+            if (__any_sync(0xffffffffu, any)) warp_sum9_atomic(v, dg, M, sm.id[k]);
         }
     }
 }

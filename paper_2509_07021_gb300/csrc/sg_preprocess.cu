@@ -519,7 +519,8 @@ cudaError_t launch_preprocess(const Batch &hb, const Batch *db, Rec *rec, uint32
 // ---------------------------------------------------------------------------
 // K8 preprocess backward
 // ---------------------------------------------------------------------------
-// dg layout: planar [9][M]: dx, dy, dA, dB, dC, do', dr, dg, db per entry.
+// dg layout: planar [9][M] per entry: the blend adjoint's sums of dG dx, dG dy,
+// dG dx^2, dG dx dy, dG dy^2 (dG = dL/dalpha G), then dL/do', dL/dr, dL/dg, dL/db.
 // Resident blocks per SM requested for the preprocess adjoint (it is bound by
 // the latency of its parameter loads, so occupancy matters more than registers).
 #ifndef SG_PRE_BWD_MIN_BLOCKS
@@ -577,8 +578,9 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
             // With one view, every load is issued before the visibility test (the
             // latency of the test is hidden).
             const uint32_t tte = multi_view ? 1u : tiles_touched[e];
-            const float gx = dg[e], gy = dg[M + e], gA = dg[2 * M + e], gB = dg[3 * M + e],
-                        gC = dg[4 * M + e], gop = dg[5 * M + e];
+            // moments of dG = dL/dalpha G over the entry's pixels (dx, dy = pixel - centre)
+            const float mdx = dg[e], mdy = dg[M + e], mdxx = dg[2 * M + e], mdxy = dg[3 * M + e],
+                        mdyy = dg[4 * M + e], gop = dg[5 * M + e];
             const float grgb[3] = {dg[6 * M + e], dg[7 * M + e], dg[8 * M + e]};
             const uint32_t cl = clamp[e];
             if (tte == 0u) continue;
@@ -679,6 +681,11 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
             // its intermediates are not live across the lobe loop) ----
             Geo G;
             project_view(vw, px, py, pz, g3, o, gm, G);
+            // dL/dpower = o' dG with power = -(A dx^2 + C dy^2) / 2 - B dx dy and
+            // d/dx = -d/d(dx): the gradients of the centre and of the conic
+            const float gx = G.op * (G.conA * mdx + G.conB * mdy);
+            const float gy = G.op * (G.conB * mdx + G.conC * mdy);
+            const float gA = -0.5f * G.op * mdxx, gB = -G.op * mdxy, gC = -0.5f * G.op * mdyy;
 
             // ---- projected centre: x = fx t_x / t_z + cx - 0.5 ----
             const float itz = 1.0f / G.tz;
