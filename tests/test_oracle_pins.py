@@ -537,6 +537,40 @@ def test_rect_matches_fp64_away_from_boundaries(orc):
     np.testing.assert_allclose(dec.xy32[vis], xy, rtol=1e-6, atol=1e-4)
 
 
+def test_depth_keys_and_conic_against_fp64(orc):
+    """The binary32 recipe's depth t_z = ((V20 px + V21 py) + V22 pz) + V23 lies within
+    the forward error bound of a 4-term dot product, gamma_4 sum |terms|, of the FP64
+    depth; any pair the binary32 keys order differently from FP64 depth lies within
+    the two bounds of each other (near-equal depths only). The binary32 conic stays
+    within a relative 1e-5 of the FP64 projection's."""
+    rng = np.random.default_rng(9)
+    scene = synth.make_scene(rng, 4000, lobes=0, means="cube", cube_side=2.0, masks="uniform")
+    cam = synth.make_camera(160, 120, 150.0, viewmat=synth.look_at((0.7, -0.4, 0.3), (0.1, 0.2, 4.0)))
+    dec = orc.decisions_fp32(scene, cam)
+    vis = np.nonzero(dec.visible)[0]
+    assert len(vis) > 3000
+    z32 = dec.depth_bits[vis].view(np.float32).astype(np.float64)
+    V = np.asarray(cam.viewmat, np.float32).astype(np.float64)
+    p = scene.means.astype(np.float64)[:, vis]
+    terms = np.stack([V[2, 0] * p[0], V[2, 1] * p[1], V[2, 2] * p[2], np.full(len(vis), V[2, 3])])
+    z64 = terms.sum(0)
+    u = 2.0 ** -24
+    bound = 4 * u / (1 - 4 * u) * np.abs(terms).sum(0)
+    assert np.all(np.abs(z32 - z64) <= bound)
+    # order of the keys (ties by index, as the stable sort) against FP64 depth
+    order = np.lexsort((vis, dec.depth_bits[vis]))
+    zs, bs = z64[order], bound[order]
+    i, j = np.triu_indices(len(zs), 1)
+    inverted = zs[j] < zs[i]
+    assert inverted.sum() <= 10
+    assert np.all(zs[i][inverted] - zs[j][inverted] <= bs[i][inverted] + bs[j][inverted])
+    P = orc.leaves(scene, requires_grad=False)
+    _, con, _, _ = orc.project_fp64(P, cam, vis, scene.lobe_off)
+    con = con.numpy()
+    nrm = np.sqrt(con[:, 0] ** 2 + 2 * con[:, 1] ** 2 + con[:, 2] ** 2)
+    assert (np.abs(dec.conic32[vis].astype(np.float64) - con).max(1) / nrm).max() < 1e-5
+
+
 def test_tiled_equals_brute_force(orc):
     for seed in range(3):
         rng = np.random.default_rng(100 + seed)
