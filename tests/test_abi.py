@@ -121,6 +121,45 @@ def test_invalid_arguments_rejected_on_host(L):
     assert st == sgsplat.SG_ERR_INVALID_ARG
 
 
+def test_batched_arguments_rejected_on_host(L):
+    a, b = _cpu_scene(10, 1), _cpu_scene(20, 2)
+    cams = [synth.make_camera(32, 32, 40.0), synth.make_camera(48, 16, 40.0)]
+    q = sgsplat.sg_batched_workspace_query([a, b], cams, [0, 1], 1000)
+    assert q["n_entries"] == 30 and q["n_tiles"] == 4 + 3
+    # a view of a scene the call does not hold
+    with pytest.raises(sgsplat.SGError) as e:
+        sgsplat.sg_batched_workspace_query([a, b], cams, [0, 2], 0)
+    assert e.value.status == sgsplat.SG_ERR_INVALID_ARG and "scene index" in str(e.value)
+    # the scenes of one call share their storage types
+    h = DeviceScene.from_host(synth.make_scene(np.random.default_rng(1), 10, lobes=1), device="cpu",
+                              storage="f16")
+    with pytest.raises(sgsplat.SGError) as e:
+        sgsplat.sg_batched_workspace_query([a, h], cams, [0, 1], 0)
+    assert e.value.status == sgsplat.SG_ERR_INVALID_ARG and "share" in str(e.value)
+
+
+def test_noalloc_backward_rejected_on_host(L):
+    """The no-alloc backward refuses a missing gradient struct, a misaligned
+    workspace and a call whose scratch exceeds its static array, before it
+    touches a device."""
+    ds = _cpu_scene(10, 1)
+    cams = sgsplat.camera_array([synth.make_camera(32, 32, 40.0)])
+    P = ctypes.c_void_p
+    g = sgsplat.grads_struct({})
+    s = ds.struct()
+    st = L.sg_render_backward_noalloc(ctypes.byref(s), cams, 1, P(256), 1 << 20, P(256), P(256), P(256),
+                                      None, None)
+    assert st == sgsplat.SG_ERR_INVALID_ARG
+    st = L.sg_render_backward_noalloc(ctypes.byref(s), cams, 1, P(8), 1 << 20, P(256), P(256), P(256),
+                                      ctypes.byref(g), None)
+    assert st == sgsplat.SG_ERR_INVALID_ARG and "aligned" in sgsplat.sg_last_error()
+    big = ds.struct()
+    big.n = sgsplat.SG_NOALLOC_SCRATCH_BYTES // 36 + 1000   # sizes only: never dereferenced
+    st = L.sg_render_backward_noalloc(ctypes.byref(big), cams, 1, P(256), 1 << 20, P(256), P(256),
+                                      P(256), ctypes.byref(g), None)
+    assert st == sgsplat.SG_ERR_WORKSPACE and "static scratch" in sgsplat.sg_last_error()
+
+
 def test_workspace_too_small_for_fixed_part(L):
     ds = _cpu_scene(10, 1)
     cams = [synth.make_camera(32, 32, 40.0)]
