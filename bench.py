@@ -38,14 +38,23 @@ L2_FLUSH_BYTES = 512 << 20
 # update), backward 69 (about 14 for power and alpha, 46 for the adjoint, 9 for
 # the warp reduction amortised over the pairs).
 FLOPS_PER_EVAL = {"blend_fwd": 23.0, "blend_bwd": 69.0}
-TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic_1m_1080p.md")
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
+# stage's kernel at this workload, from one ncu capture, together with the
+# digest of the CUDA sources it was taken on: reported as roofline.traffic only
+# while the sources are unchanged (any kernel change makes it null until the
+# next capture).
+RECORDED_TRAFFIC = {
+    "sources": "",
+    "bytes": {},
+}
 
 
-def kernel_source_digest():
+def kernel_source_digest(root=None):
     """sha256 over the CUDA sources (any kernel change invalidates recorded counters)."""
     import hashlib
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2509_07021_gb300", "csrc")
+    csrc = os.path.join(root or ROOT, "paper_2509_07021_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if name.endswith((".cu", ".cuh")):
             with open(os.path.join(csrc, name), "rb") as f:
@@ -53,27 +62,16 @@ def kernel_source_digest():
     return h.hexdigest()
 
 
-def recorded_traffic(stage):
-    """DRAM bytes per launch of a stage's kernel from the committed ncu summary,
-    or None when the sources changed since the capture (or no capture exists).
-    Table rows: | stage | kernel | dram bytes per launch | ... |, with a line
-    'source sha256: <digest>' naming the sources the counters were taken on."""
-    try:
-        text = open(TRAFFIC_TABLE).read()
-    except OSError:
+def recorded_traffic(stage, table=None, root=None):
+    """DRAM bytes per launch of a stage's kernel from the recorded capture, or
+    None when the sources changed since (or the stage was not captured)."""
+    table = RECORDED_TRAFFIC if table is None else table
+    if not table.get("sources") or table["sources"] != kernel_source_digest(root):
         return None
-    import re
-    m = re.search(r"source sha256:\s*`?([0-9a-f]{64})", text)
-    if not m or m.group(1) != kernel_source_digest():
-        return None
-    for line in text.splitlines():
-        cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) >= 3 and cells[0] == stage:
-            try:
-                return float(cells[2].replace(",", ""))
-            except ValueError:
-                return None
-    return None
+    v = table.get("bytes", {}).get(stage)
+    return None if v is None else float(v)
+
+
 # GB300 FP32 (non-tensor) peak: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
@@ -170,15 +168,21 @@ class ClockSampler:
         self.proc = None
         self.path = None
 
-    def start(self):
+    def start(self, interval_ms=50, ready_timeout=10.0):
+        """Starts nvidia-smi and returns once its first sample is on file, so
+        that its start-up never overlaps a timed region."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "20"],
+                 "--format=csv,noheader,nounits", "-lms", str(int(interval_ms))],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-            time.sleep(0.3)   # let the sampler start before the timed region
+            t0 = time.time()
+            while time.time() - t0 < ready_timeout and self.proc.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.05)
         except Exception:
             self.proc = None
 
@@ -220,16 +224,25 @@ class ClockSampler:
 # the oracle on the host cores (cpu_baseline / --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(scene, cam, d_img, n_tiles, seed=0):
-    """One bounded oracle sample of the workload: full preprocess and tile
-    sort of the frame, then forward + backward blend on n_tiles random tiles
-    (upstream gradient restricted to them). Returns (seconds, est. seconds
-    for the full frame, threads)."""
+def oracle_fixed_time(scene, cam):
+    """Seconds of the oracle's full-frame part of a step: decisions and the
+    tile lists of every tile."""
     import oracle
     t0 = time.perf_counter()
     dec = oracle.decisions_fp32(scene, cam)
     oracle.tile_lists(dec, cam)
-    t_fixed_lists = time.perf_counter() - t0
+    return time.perf_counter() - t0
+
+
+def oracle_sample(scene, cam, d_img, n_tiles, seed=0, t_fixed=None):
+    """One bounded oracle sample of the workload: the full-frame preprocess and
+    tile lists, then forward + backward blend on n_tiles random tiles (upstream
+    gradient restricted to them). t_fixed: the seconds of the full-frame part
+    (oracle_fixed_time), measured here when not given. Returns (seconds of
+    the sample, estimated seconds for the whole frame, threads)."""
+    import oracle
+    if t_fixed is None:
+        t_fixed = oracle_fixed_time(scene, cam)
     sel = np.zeros(cam.n_tiles, bool)
     sel[np.random.default_rng(seed).choice(cam.n_tiles, n_tiles, replace=False)] = True
     t1 = time.perf_counter()
@@ -238,12 +251,11 @@ def oracle_sample(scene, cam, d_img, n_tiles, seed=0):
     m = m[:cam.height, :cam.width]
     oracle.render_backward(res, scene, cam, d_img * m[None])
     t_sample = time.perf_counter() - t1
-    total = t_fixed_lists + t_sample
-    # the sample repeats the preprocess/sort once more inside render_forward:
-    # count it once, scale the per-tile blend part to the whole frame
-    t_blend = max(t_sample - t_fixed_lists, 0.0)
+    # the sample holds the full-frame part once; scale the rest (the blend of
+    # the sampled tiles) to the whole frame
+    t_blend = max(t_sample - t_fixed, 0.0)
     est_full = t_sample - t_blend + t_blend * cam.n_tiles / n_tiles
-    return total, est_full, oracle.num_threads()
+    return t_sample, est_full, oracle.num_threads()
 
 
 def cpu_baseline_line(scene, cam, d_img, n_tiles):
@@ -355,30 +367,41 @@ def stage_rooflines(stages_ms, counts, evals, hbm_gbs):
     return out
 
 
+def step_stats(ms):
+    """min / median / mean / max of per-step milliseconds."""
+    return {"min": float(min(ms)), "median": float(statistics.median(ms)), "mean": float(statistics.mean(ms)),
+            "max": float(max(ms))}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
     scene, cams, d_img = workload()
     cam = cams[0]
     n_tiles = max(4, args.cpu_tiles // 3)
+    t_fixed = oracle_fixed_time(scene, cam)
     for _ in range(args.warmup):
-        oracle_sample(scene, cam, d_img, n_tiles)
+        oracle_sample(scene, cam, d_img, n_tiles, t_fixed=t_fixed)
     ests, totals = [], []
     threads = 1
     for i in range(args.steps):
-        total, est, threads = oracle_sample(scene, cam, d_img, n_tiles, seed=i)
+        total, est, threads = oracle_sample(scene, cam, d_img, n_tiles, seed=i, t_fixed=t_fixed)
         ests.append(est)
         totals.append(total)
-    ms = 1e3 * float(np.mean(ests))
-    value = cam.width * cam.height / 1e6 / (ms / 1e3)
+    frame_ms = 1e3 * float(np.mean(ests))
+    value = cam.width * cam.height / 1e6 / (frame_ms / 1e3)
+    wall_ms = 1e3 * float(np.mean(totals))
+    sample = (f"each step: full-frame preprocess + tile sort, fwd+bwd blend on {n_tiles} random tiles "
+              f"(measured wall {wall_ms / 1e3:.1f} s/step); value = the frame's pixels over the frame "
+              f"time estimated by scaling the blend part to all {cam.n_tiles} tiles "
+              f"({frame_ms / 1e3:.1f} s/frame)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall_ms,
+            "frame_ms_estimate": frame_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, cams),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"each step: full-frame preprocess + tile sort, fwd+bwd blend "
-                                       f"on {n_tiles} random tiles, blend scaled to the frame "
-                                       f"(mean wall {np.mean(totals):.1f} s/step)"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -407,6 +430,8 @@ def run_ours(args, world, rank, local):
         render.render_backward(ds, cams, out, d_img, grads)
         return out
 
+    clocks = ClockSampler(local)
+    clocks.start()
     tuned = None
     if args.shape:
         f, b, fp, bp = (int(x) for x in args.shape.split(","))
@@ -442,33 +467,45 @@ def run_ours(args, world, rank, local):
     share = {k: round(v["ms"] / tot_stage_ms, 4) for k, v in fl_stages.items()}
     stages_ms = {k: round(v["ms"] / n_break, 4) for k, v in fl_stages.items()}
 
-    # ---- timed region (device events per step, L2 flushed between steps); only
-    # the dominant stage is bracketed, for its live average launch duration ----
+    # ---- timed region: W fresh warm-up steps right before it (the GPU is not
+    # left idle in between), then K steps, each bracketed by CUDA events and
+    # synchronised, the L2 flushed before each; only the dominant stage is
+    # bracketed inside the step, for its live average launch duration ----
     dom_index = [sgsplat.sg_profile_stage_name(i) for i in range(sgsplat.SG_PROFILE_STAGES)].index(dom)
     sgsplat.sg_profile_set_stages(1 << dom_index)
-    sgsplat.sg_profile_read(reset=True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
-    launches0 = sgsplat.sg_kernel_launches()
-    barrier(world)
-    torch.cuda.synchronize()
-    wall0 = time.time()
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        starts[i].record()
-        step()
-        ends[i].record()
-    torch.cuda.synchronize()
-    wall1 = time.time()
-    barrier(world)
-    launches = sgsplat.sg_kernel_launches() - launches0
+
+    def timed_steps():
+        for i in range(max(args.warmup, 1)):
+            flush.fill_(i & 0xFF)
+            step()
+        torch.cuda.synchronize()
+        sgsplat.sg_profile_read(reset=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        n0 = sgsplat.sg_kernel_launches()
+        t0 = time.time()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            starts[i].record()
+            step()
+            ends[i].record()
+            ends[i].synchronize()
+        t1 = time.time()
+        n1 = sgsplat.sg_kernel_launches()
+        barrier(world)
+        return [s.elapsed_time(e) for s, e in zip(starts, ends)], t0, t1, n1 - n0
+
+    per_step, wall0, wall1, launches = timed_steps()
     clk = clocks.stop(wall0, wall1)
-    sgsplat.sg_profile_enable(0)
     prof = sgsplat.sg_profile_read(reset=True)
-    t_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    ms_step = max_over_ranks(t_ms / args.steps, world)
+    # the same K steps again with the clock sampler stopped (does sampling disturb the steps?)
+    check_steps, _, _, _ = timed_steps()
+    sgsplat.sg_profile_enable(0)
+    sgsplat.sg_profile_read(reset=True)
+    stats = step_stats(per_step)
+    ms_step = max_over_ranks(stats["median"], world)
     px = cam.width * cam.height
     value = world * px / (ms_step / 1e3) / 1e6
 
@@ -513,9 +550,13 @@ def run_ours(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(args, cams, {"n_pairs": n_pairs,
-                                                   "tuning": sgsplat.sg_get_tuning(),
-                                                   "autotune_ms": tuned and tuned.get("ms")}),
+            "config": workload_config(args, cams),
+            "step_ms": dict(stats, timing="CUDA events per step, synchronised each step; ms_per_step is "
+                                          "the median", per_step=[round(x, 4) for x in per_step]),
+            "timing_check": {"sampler_off": step_stats(check_steps),
+                             "note": "the same K steps again with the nvidia-smi sampler stopped"},
+            "workload_stats": {"n_pairs": n_pairs, "tuning": sgsplat.sg_get_tuning(),
+                               "autotune_ms": tuned and tuned.get("ms")},
             "roofline": roof, "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches),
             "stages_ms_per_step": stages_ms,
@@ -545,7 +586,7 @@ def _timed(fn, steps, warmup, flush):
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
-    tot = 0.0
+    ms = []
     for i in range(steps):
         flush.fill_(i & 0xFF)
         a = torch.cuda.Event(enable_timing=True)
@@ -554,8 +595,8 @@ def _timed(fn, steps, warmup, flush):
         fn()
         b.record()
         torch.cuda.synchronize()
-        tot += a.elapsed_time(b)
-    return tot / steps
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
 
 
 def render_vram(ds, cams, d_img, grads, static_bytes):

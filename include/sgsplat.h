@@ -197,6 +197,10 @@ typedef struct sg_ws_layout {
  * (host only; the same arguments as the forward call). */
 int sg_workspace_layout(const sg_scene *scene, const sg_camera *cams, int n_views, size_t ws_bytes,
                         sg_ws_layout *out);
+/* The same for a batched workspace (the arguments of sg_render_batched_forward;
+ * entries are numbered view after view, each view's n of its scene). */
+int sg_batched_workspace_layout(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
+                                const int32_t *view_scene, int n_views, size_t ws_bytes, sg_ws_layout *out);
 
 /*
  * Stage profiling (off by default; process wide, not thread safe against

@@ -19,8 +19,11 @@ What it follows:
     rules of the rasterizer it builds on.
 
 Discrete decisions (cull, radius, tile rectangle, depth key) are taken with the
-binary32 recipe below, the same recipe the GPU uses, so that tile lists can be
+binary32 recipe below, the same recipe the GPU uses, so that they can be
 compared bit for bit; every value that feeds an image or a gradient is FP64.
+Tile lists follow the rasterizer the paper keeps: a visible Gaussian gets a
+pair in every tile of its 3-sigma rectangle, each tile's list in ascending
+(depth, index) order.
 
 The adjoint: per-Gaussian formulas (projection, conic, SG colour) are written
 once in torch float64 and differentiated by autograd; the per-pixel blend
@@ -119,8 +122,7 @@ class Decisions:
     depth_bits: np.ndarray   # [N] uint32 bits of the binary32 camera-space depth
     xy32: np.ndarray         # [N,2] binary32 projected centre (reported only)
     conic32: np.ndarray      # [N,3] binary32 conic (reported only)
-    reach_t: np.ndarray | None = None   # [N] binary32 tile-binning bound on q (-1: reaches nothing)
-    touched: np.ndarray | None = None   # [N] int64 tiles of the rectangle the bound reaches
+    touched: np.ndarray | None = None   # [N] int64 tiles of the 3-sigma rectangle (0 when culled)
 
 
 def _clamp_tile(f, n):
@@ -207,127 +209,29 @@ def decisions_fp32(scene, cam) -> Decisions:
         depth_bits = tz.astype(F32).view(np.uint32).copy()
         dec = Decisions(vis, rad, rect, depth_bits,
                         np.stack([px, py], 1), np.stack([conA, conB, conC], 1))
-        dec.reach_t = np.where(op_ok, reach_threshold(opd), F32(-1.0)).astype(F32)
-        g, ty, c0, c1 = reach_rows(dec)
-        dec.touched = np.bincount(g, weights=(c1 - c0), minlength=len(vis)).astype(np.int64)
+        dec.touched = np.where(vis, (tx1 - tx0) * (ty1 - ty0), 0).astype(np.int64)
         return dec
-
-
-# ---------------------------------------------------------------------------
-# Tile binning recipe (binary32, identical order of operations on the GPU side)
-# ---------------------------------------------------------------------------
-# A pair (tile, Gaussian) can blend only where alpha = o' exp(-q/2) >= 1/255,
-# q = A dx^2 + 2 B dx dy + C dy^2, i.e. inside q <= 2 ln(255 o'). A tile of the
-# 3-sigma rectangle gets a pair iff its box of pixel centres meets that ellipse,
-# enlarged (1 % + 0.01 in q, 0.02 px) so that rounding can only keep extra
-# tiles. Tiles left out are ones where every pixel skips the pair, so lists,
-# images and gradients are those of the full rectangle minus skipped pairs.
-
-def _hexf(h):
-    return F32(float.fromhex(h))
-
-
-_TR = {"c7": _hexf("0x1.24924ap-3"), "c5": _hexf("0x1.99999ap-3"), "c3": _hexf("0x1.555556p-2"),
-       "inv_ln2": _hexf("0x1.715476p+0"), "ln2x2": _hexf("0x1.62e430p+0"),
-       "grow": _hexf("0x1.028f5cp+0"), "add": _hexf("0x1.47ae14p-7"), "pad": _hexf("0x1.47ae14p-6"),
-       "inv16": _hexf("0x1p-4")}
-
-
-def log2_recipe(x):
-    """log2 of positive normal binary32 x: exponent + ln(m)/ln 2, m in [1, 2),
-    ln m = 2 atanh(s), s = (m - 1)/(m + 1), series to s^7; one rounding per step."""
-    x = np.asarray(x, F32)
-    u = x.view(np.uint32)
-    e = (((u >> np.uint32(23)) & np.uint32(255)).astype(np.int32) - 127).astype(F32)
-    m = ((u & np.uint32(0x007FFFFF)) | np.uint32(0x3F800000)).view(F32)
-    one = F32(1.0)
-    s_ = (m - one) / (m + one)
-    s2 = s_ * s_
-    P = s2 * _TR["c7"] + _TR["c5"]
-    P = P * s2 + _TR["c3"]
-    P = P * s2 + one
-    lnm = (F32(2.0) * s_) * P
-    return e + lnm * _TR["inv_ln2"]
-
-
-def reach_threshold(opd):
-    """Enlarged bound 2 ln(255 o') * 1.01 + 0.01 (binary32 recipe)."""
-    with np.errstate(all="ignore"):
-        t0 = _TR["ln2x2"] * log2_recipe(F32(255.0) * np.asarray(opd, F32))
-        return t0 * _TR["grow"] + _TR["add"]
-
-
-def reach_rows(dec: Decisions):
-    """For every tile row of every visible Gaussian's rectangle, the columns
-    [c0, c1) whose pixel-centre boxes the enlarged ellipse meets.
-    Returns (gaussian id, ty, c0, c1) arrays over all (Gaussian, row)."""
-    f = F32
-    ids_v = np.nonzero(dec.visible)[0]
-    r = dec.rect[ids_v].astype(np.int64)
-    h = r[:, 3] - r[:, 1]
-    g = np.repeat(ids_v, h)
-    start = np.repeat(np.cumsum(h) - h, h)
-    ty = np.repeat(r[:, 1], h) + (np.arange(int(h.sum()), dtype=np.int64) - start)
-    x0 = dec.rect[g, 0].astype(np.int64)
-    x1 = dec.rect[g, 2].astype(np.int64)
-    with np.errstate(all="ignore"):
-        A, B, C = (dec.conic32[g, k].astype(f) for k in range(3))
-        x, y = dec.xy32[g, 0].astype(f), dec.xy32[g, 1].astype(f)
-        t = dec.reach_t[g].astype(f)
-        det = A * C - B * B
-        ok = (A > 0) & (C > 0) & (det > 0) & np.isfinite(t) & np.isfinite(det)
-        At = A * t
-        ymax = np.sqrt(At / det)
-        xmax = np.sqrt((C * t) / det)
-        m = (B * xmax) / C
-        iA = f(1.0) / A
-        mode = np.where(~(t >= 0), 0, np.where(ok & np.isfinite(ymax) & np.isfinite(m) & np.isfinite(At)
-                                                & np.isfinite(iA), 1, 2))
-        pad = _TR["pad"]
-        lo = np.maximum((f(16.0) * ty.astype(f) - y) - pad, -ymax)
-        hi = np.minimum(((f(16.0) * ty.astype(f) + f(15.0)) - y) + pad, ymax)
-        nonempty = lo <= hi
-        dr = np.minimum(np.maximum(-m, lo), hi)
-        dl = np.minimum(np.maximum(m, lo), hi)
-        sr = np.sqrt(np.maximum(f(0.0), At - det * (dr * dr)))
-        sl = np.sqrt(np.maximum(f(0.0), At - det * (dl * dl)))
-        xr = (x + (sr - B * dr) * iA) + pad
-        xl = (x - (sl + B * dl) * iA) - pad
-        fx0 = (16 * x0 - 16).astype(f)
-        fx1 = (16 * x1).astype(f)
-        a = np.ceil((np.minimum(np.maximum(xl, fx0), fx1) - f(15.0)) * _TR["inv16"])
-        b = np.floor(np.minimum(np.maximum(xr, fx0), fx1) * _TR["inv16"])
-    a = np.where(mode == 1, a, 0).astype(np.int64)
-    b = np.where(mode == 1, b, 0).astype(np.int64)
-    c0 = np.maximum(x0, a)
-    c1 = np.maximum(c0, np.minimum(x1, b + 1))
-    c0 = np.where(mode == 2, x0, np.where((mode == 1) & nonempty, c0, x0))
-    c1 = np.where(mode == 2, x1, np.where((mode == 1) & nonempty, c1, x0))
-    return g, ty, c0, c1
 
 
 # ---------------------------------------------------------------------------
 # Duplicate, sort, ranges (tile lists)
 # ---------------------------------------------------------------------------
 
-def tile_lists(dec: Decisions, cam, tile_offset=0, full_rect=False):
-    """Pairs (tile, Gaussian) for the tiles of every visible Gaussian's rectangle
-    that the tile-binning recipe keeps (every tile of the rectangle with
-    full_rect=True), sorted by the 64-bit key (tile << 32 | depth bits), equal
-    keys by Gaussian id.
+def tile_lists(dec: Decisions, cam, tile_offset=0):
+    """Pairs (tile, Gaussian) for every tile of every visible Gaussian's 3-sigma
+    rectangle (the rule of the 3DGS rasterizer the paper keeps, Sec. 3.1 and
+    Sec. 4), sorted by the 64-bit key (tile << 32 | depth bits), equal keys by
+    Gaussian id.
 
     Returns keys [K] uint64, ids [K] int64, ranges [n_tiles, 2] int64.
     """
-    if full_rect:
-        ids_v = np.nonzero(dec.visible)[0]
-        r = dec.rect[ids_v].astype(np.int64)
-        h = r[:, 3] - r[:, 1]
-        g = np.repeat(ids_v, h)
-        start = np.repeat(np.cumsum(h) - h, h)
-        ty = np.repeat(r[:, 1], h) + (np.arange(int(h.sum()), dtype=np.int64) - start)
-        c0, c1 = dec.rect[g, 0].astype(np.int64), dec.rect[g, 2].astype(np.int64)
-    else:
-        g, ty, c0, c1 = reach_rows(dec)
+    ids_v = np.nonzero(dec.visible)[0]
+    r = dec.rect[ids_v].astype(np.int64)
+    h = r[:, 3] - r[:, 1]
+    g = np.repeat(ids_v, h)
+    start = np.repeat(np.cumsum(h) - h, h)
+    ty = np.repeat(r[:, 1], h) + (np.arange(int(h.sum()), dtype=np.int64) - start)
+    c0, c1 = dec.rect[g, 0].astype(np.int64), dec.rect[g, 2].astype(np.int64)
     cnt = c1 - c0
     K = int(cnt.sum())
     gid = np.repeat(g, cnt)

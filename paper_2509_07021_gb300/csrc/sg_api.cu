@@ -699,11 +699,11 @@ int sg_workspace_query(const sg_scene *scene, const sg_camera *cams, int n_views
     return SG_OK;
 }
 
-int sg_workspace_layout(const sg_scene *scene, const sg_camera *cams, int n_views, size_t ws_bytes,
-                        sg_ws_layout *out) {
+static int layout_of(const sg_scene *scenes, int n_scenes, const sg_camera *cams, const int32_t *view_scene,
+                     int n_views, size_t ws_bytes, sg_ws_layout *out) {
     if (!out) return fail(SG_ERR_INVALID_ARG, "out must not be NULL");
     std::unique_ptr<Batch> hb(new Batch);
-    int st = build_batch(scene, 1, cams, nullptr, n_views, false, *hb);
+    int st = build_batch(scenes, n_scenes, cams, view_scene, n_views, false, *hb);
     if (st != SG_OK) return st;
     const uint64_t cap = capacity_for(*hb, ws_bytes);
     if (cap == UINT64_MAX) return fail(SG_ERR_WORKSPACE, "workspace smaller than its fixed part");
@@ -717,6 +717,17 @@ int sg_workspace_layout(const sg_scene *scene, const sg_camera *cams, int n_view
     out->pair_entry = L.pval_final;
     out->total_bytes = L.total;
     return SG_OK;
+}
+
+int sg_workspace_layout(const sg_scene *scene, const sg_camera *cams, int n_views, size_t ws_bytes,
+                        sg_ws_layout *out) {
+    return layout_of(scene, 1, cams, nullptr, n_views, ws_bytes, out);
+}
+
+int sg_batched_workspace_layout(const sg_scene *scenes, int n_scenes, const sg_camera *cams,
+                                const int32_t *view_scene, int n_views, size_t ws_bytes, sg_ws_layout *out) {
+    if (!view_scene) return fail(SG_ERR_INVALID_ARG, "view_scene must not be NULL");
+    return layout_of(scenes, n_scenes, cams, view_scene, n_views, ws_bytes, out);
 }
 
 int sg_render_forward(const sg_scene *scene, const sg_camera *cams, int n_views, void *ws, size_t ws_bytes,

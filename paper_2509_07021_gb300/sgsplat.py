@@ -29,6 +29,7 @@ EXPORTS = ("sg_version", "sg_last_error", "sg_workspace_query", "sg_workspace_la
            "sg_profile_stage_name", "sg_kernel_launches", "sg_render_backward_noalloc",
            "sg_set_tuning", "sg_get_tuning", "sg_batched_workspace_query",
            "sg_render_batched_forward", "sg_render_batched_backward", "sg_forward_status",
+           "sg_batched_workspace_layout",
            "sg_render_forward_importance", "sg_admm_workspace_bytes", "sg_admm_opacity_step",
            "sg_admm_sharpness_step", "sg_admm_penalty_grad", "sg_postprocess_workspace_bytes",
            "sg_postprocess_plan", "sg_postprocess_apply")
@@ -145,6 +146,9 @@ def lib():
         L.sg_batched_workspace_query.argtypes = [PS, ctypes.c_int, PC, _P, ctypes.c_int, ctypes.c_uint64,
                                                  ctypes.POINTER(sg_sizes)]
         L.sg_batched_workspace_query.restype = ctypes.c_int
+        L.sg_batched_workspace_layout.argtypes = [PS, ctypes.c_int, PC, _P, ctypes.c_int, ctypes.c_size_t,
+                                                  ctypes.POINTER(sg_ws_layout)]
+        L.sg_batched_workspace_layout.restype = ctypes.c_int
         L.sg_render_batched_forward.argtypes = [PS, ctypes.c_int, PC, _P, ctypes.c_int, _P, ctypes.c_size_t,
                                                 _P, _P, _P, _P, _P]
         L.sg_render_forward_importance.argtypes = [PS, PC, ctypes.c_int, _P, ctypes.c_size_t, _P, _P, _P,
@@ -464,6 +468,14 @@ def sg_batched_workspace_query(scenes, cams, view_scene, pair_capacity: int) -> 
     _check(lib().sg_batched_workspace_query(scene_array(scenes), len(scenes), camera_array(cams),
                                             _view_scene_array(view_scene), len(cams),
                                             int(pair_capacity), ctypes.byref(out)))
+    return out.as_dict()
+
+
+def sg_batched_workspace_layout(scenes, cams, view_scene, ws_bytes: int) -> dict:
+    out = sg_ws_layout()
+    _check(lib().sg_batched_workspace_layout(scene_array(scenes), len(scenes), camera_array(cams),
+                                             _view_scene_array(view_scene), len(cams), int(ws_bytes),
+                                             ctypes.byref(out)))
     return out.as_dict()
 
 

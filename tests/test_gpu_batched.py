@@ -9,7 +9,7 @@ import oracle
 from paper_2509_07021_gb300 import render, sgsplat, synth
 from paper_2509_07021_gb300.sgsplat import DeviceScene
 
-from parity_util import check_grads, check_image, masked_dimg
+from parity_util import GpuView, check_decisions, check_grads, check_image, gpu_view_lists, masked_dimg
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
@@ -44,10 +44,12 @@ def _check_batched(br, scenes, cams, view_scene, seed):
     Ts = _flat_views(br.T_final, cams, 1)
     lasts = _flat_views(br.last, cams, 1)
     results = []
+    gv = GpuView.batched(br)
     for v, cam in enumerate(cams):
         res, _ = oracle.render(scenes[view_scene[v]], [cam])
         results.append(res[0])
-        check_image(imgs[v], Ts[v], lasts[v], res[0], cam)
+        check_decisions(gv, cams, [(v, scenes[view_scene[v]], res[0])])
+        check_image(imgs[v], Ts[v], lasts[v], res[0], cam, gpu_view_lists(gv, cams, v))
     rng = np.random.default_rng(seed)
     dimgs = masked_dimg(rng, cams, results)
     br.backward(torch.from_numpy(np.concatenate([d.reshape(-1) for d in dimgs])).cuda())
@@ -84,10 +86,11 @@ def test_render_batched_function():
     br.forward()
     torch.cuda.synchronize()
     assert torch.equal(r.img, br.img) and torch.equal(r.T_final, br.T_final) and torch.equal(r.last, br.last)
+    gv = GpuView.batched(r)
     for v, cam in enumerate(cams):
         res, _ = oracle.render(scenes[view_scene[v]], [cam])
         check_image(*(_flat_views(t, cams, ch)[v] for t, ch in ((r.img, 3), (r.T_final, 1), (r.last, 1))),
-                    res[0], cam)
+                    res[0], cam, gpu_view_lists(gv, cams, v))
 
 
 def test_persistent_plain_form():
@@ -195,7 +198,9 @@ def test_batched_scene_without_views():
     assert st == sgsplat.SG_OK and 0 < n <= br.capacity
     res, _ = oracle.render(scenes[1], cams)
     img, T, last = (_flat_views(t, cams, ch)[0] for t, ch in ((br.img, 3), (br.T_final, 1), (br.last, 1)))
-    check_image(img, T, last, res[0], cams[0])
+    gv = GpuView.batched(br)
+    check_decisions(gv, cams, [(0, scenes[1], res[0])])
+    check_image(img, T, last, res[0], cams[0], gpu_view_lists(gv, cams, 0))
     dimgs = masked_dimg(np.random.default_rng(731), cams, res)
     for g in br.grads[0].values():
         g.fill_(7.0)   # gradients are overwritten, never accumulated

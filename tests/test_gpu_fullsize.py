@@ -8,10 +8,12 @@
 * the stress workload: 6M Gaussians, 60 % / 50 % exact-zero masks, a packed
   cluster, 16 views in one batched call, one view checked.
 
-Tile lists, tiles_touched and ranges of the checked views are compared bit
-for bit over the whole frame; images, T, last and gradients on the sampled
-tiles (the upstream gradient is zero elsewhere, so the oracle's gradients are
-exact for it)."""
+Over the whole frame of every checked view: the tile lists are ordered
+sub-lists of the oracle's 3-sigma-rectangle lists, every pair left out is
+proven unreachable in FP64, and lists, tiles_touched and ranges equal the
+library's binning rule bit for bit. Images, T, last and gradients on the
+sampled tiles (the upstream gradient is zero elsewhere, so the oracle's
+gradients are exact for it)."""
 import numpy as np
 import pytest
 import torch
@@ -52,11 +54,11 @@ def test_headline_scene_1m_1080p():
     torch.cuda.synchronize()
     sel = _sample(cam, 32, 31)
     results, _ = oracle.render(scene, cams, tile_sel=[sel])
-    gv = GpuView(ds, cams, out)
-    check_decisions(gv, scene, cams, results)
+    gv = GpuView.plain(ds, cams, out)
+    check_decisions(gv, cams, [(0, scene, results[0])])
     rep = check_image(unpack_views(out.img, cams, 3)[0], unpack_views(out.T_final, cams, 1)[0],
-                      unpack_views(out.last, cams, 1)[0], results[0], cam, pixel_mask_of_tiles(cam, sel),
-                      gpu_lists=gpu_view_lists(gv, cams, 0))
+                      unpack_views(out.last, cams, 1)[0], results[0], cam, gpu_view_lists(gv, cams, 0),
+                      pixel_mask_of_tiles(cam, sel))
     assert rep["ambiguous"] <= 0.01 * rep["pixels"]
     dimgs = masked_dimg(np.random.default_rng(32), cams, results, [sel])
     _, g_orc = oracle.render(scene, cams, dimgs=dimgs, tile_sel=[sel])
@@ -77,15 +79,17 @@ def _batched_views(scenes, cams, view_scene, checks, seed):
     torch.cuda.synchronize()
     d_all = np.zeros(br.d_img.numel(), np.float32)
     oracle_grads = {}
+    gv = GpuView.batched(br)
     for v, n_tiles in checks:
         cam, s = cams[v], view_scene[v]
         sel = _sample(cam, n_tiles, seed + v)
         res, _ = oracle.render(scenes[s], [cam], tile_sel=[sel])
+        check_decisions(gv, cams, [(v, scenes[s], res[0])])
         o, npx = int(br.offsets[v]), br.npix[v]
         img = br.img[3 * o:3 * (o + npx)].view(3, cam.height, cam.width).cpu().numpy()
         T = br.T_final[o:o + npx].view(cam.height, cam.width).cpu().numpy()
         last = br.last[o:o + npx].view(cam.height, cam.width).cpu().numpy()
-        check_image(img, T, last, res[0], cam, pixel_mask_of_tiles(cam, sel))
+        check_image(img, T, last, res[0], cam, gpu_view_lists(gv, cams, v), pixel_mask_of_tiles(cam, sel))
         dimg = masked_dimg(np.random.default_rng(seed + 100 + v), [cam], res, [sel])[0]
         d_all[3 * o:3 * (o + npx)] = dimg.reshape(-1)
         _, g = oracle.render(scenes[s], [cam], dimgs=[dimg], tile_sel=[sel])

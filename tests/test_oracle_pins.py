@@ -391,120 +391,63 @@ def test_mask_readings(orc):
 # Tiling and sorting
 # ---------------------------------------------------------------------------
 
-def _row_cols_scalar(dec, g, ty):
-    """The tile-binning recipe for one Gaussian and one tile row, in numpy
-    float32 scalars (a loop-by-loop restatement of the vectorised oracle)."""
-    f = np.float32
-    from oracle.sg_oracle import _TR, log2_recipe
-    x0, x1 = int(dec.rect[g, 0]), int(dec.rect[g, 2])
-    A, B, C = (f(v) for v in dec.conic32[g])
-    x, y = f(dec.xy32[g, 0]), f(dec.xy32[g, 1])
-    t = f(dec.reach_t[g])
-    if not t >= 0:
-        return x0, x0
-    det = f(A * C - B * B)
-    if not (A > 0 and C > 0 and det > 0 and np.isfinite(t) and np.isfinite(det)):
-        return x0, x1
-    At = f(A * t)
-    ymax = f(np.sqrt(f(At / det)))
-    xmax = f(np.sqrt(f(f(C * t) / det)))
-    m = f(f(B * xmax) / C)
-    iA = f(f(1.0) / A)
-    if not all(np.isfinite(v) for v in (ymax, m, At, iA)):
-        return x0, x1
-    pad = _TR["pad"]
-    lo = max(f(f(f(16 * ty) - y) - pad), -ymax)
-    hi = min(f(f(f(16 * ty + 15) - y) + pad), ymax)
-    if not lo <= hi:
-        return x0, x0
-    dr = min(max(-m, lo), hi)
-    dl = min(max(m, lo), hi)
-    sr = f(np.sqrt(max(f(0), f(At - f(det * f(dr * dr))))))
-    sl = f(np.sqrt(max(f(0), f(At - f(det * f(dl * dl))))))
-    xr = f(f(x + f(f(sr - f(B * dr)) * iA)) + pad)
-    xl = f(f(x - f(f(sl + f(B * dl)) * iA)) - pad)
-    fx0, fx1 = f(16 * x0 - 16), f(16 * x1)
-    a = int(np.ceil(f(f(min(max(xl, fx0), fx1) - f(15)) * _TR["inv16"])))
-    b = int(np.floor(f(min(max(xr, fx0), fx1) * _TR["inv16"])))
-    c0 = max(x0, a)
-    return c0, max(c0, min(x1, b + 1))
-
-
 def test_tile_lists_match_python_loop(orc):
+    """The oracle's lists against a plain loop over the rule of the rasterizer
+    the paper keeps: tile t's list holds every visible Gaussian whose 3-sigma
+    rectangle contains t, in ascending (depth bits, index) order."""
     rng = np.random.default_rng(7)
     scene = synth.make_scene(rng, 150, lobes=1, means="cube", masks="uniform")
     cam = synth.make_camera(70, 50, 70.0)
     dec = orc.decisions_fp32(scene, cam)
     keys, ids, ranges = orc.tile_lists(dec, cam)
-    cols = {(g, ty): _row_cols_scalar(dec, g, ty) for g in range(scene.n) if dec.visible[g]
-            for ty in range(dec.rect[g, 1], dec.rect[g, 3])}
-    dropped = 0
+    total = 0
     for t in range(cam.n_tiles):
         tx, ty = t % cam.tiles_x, t // cam.tiles_x
-        in_rect = [g for g in range(scene.n) if dec.visible[g]
+        members = [g for g in range(scene.n) if dec.visible[g]
                    and dec.rect[g, 0] <= tx < dec.rect[g, 2] and dec.rect[g, 1] <= ty < dec.rect[g, 3]]
-        members = [g for g in in_rect if cols[g, ty][0] <= tx < cols[g, ty][1]]
-        dropped += len(in_rect) - len(members)
         members.sort(key=lambda g: (int(dec.depth_bits[g]), g))
         got = ids[ranges[t, 0]:ranges[t, 1]].tolist()
         assert got == members, t
         assert all(int(k) >> 32 == t for k in keys[ranges[t, 0]:ranges[t, 1]])
-    assert ranges[-1, 1] == len(ids)
-    assert dropped > 0
+        total += len(members)
+    assert ranges[-1, 1] == len(ids) == total
     np.testing.assert_array_equal(dec.touched, np.bincount(ids, minlength=scene.n))
-
-
-def _box_min_q(con, xy, tx, ty):
-    """FP64 minimum of q = A dx^2 + 2 B dx dy + C dy^2 over the box of pixel
-    centres of tile (tx, ty)."""
-    A, B, C = con[:, 0], con[:, 1], con[:, 2]
-    lx, hx = tx * 16.0 - xy[:, 0], tx * 16.0 + 15.0 - xy[:, 0]
-    ly, hy = ty * 16.0 - xy[:, 1], ty * 16.0 + 15.0 - xy[:, 1]
-    best = np.where((lx <= 0) & (hx >= 0) & (ly <= 0) & (hy >= 0), 0.0, np.inf)
-    for fx in (lx, hx):
-        dy = np.clip(-B * fx / C, ly, hy)
-        best = np.minimum(best, A * fx * fx + 2 * B * fx * dy + C * dy * dy)
-    for fy in (ly, hy):
-        dx = np.clip(-B * fy / A, lx, hx)
-        best = np.minimum(best, A * dx * dx + 2 * B * dx * fy + C * fy * fy)
-    return best
+    rect_area = (dec.rect[:, 2] - dec.rect[:, 0]) * (dec.rect[:, 3] - dec.rect[:, 1])
+    np.testing.assert_array_equal(dec.touched, np.where(dec.visible, rect_area, 0))
 
 
 @pytest.mark.parametrize("seed", [0, 1])
-def test_tile_binning_leaves_out_only_unreachable_tiles(orc, seed):
-    """Every tile of a 3-sigma rectangle that the binning recipe leaves out is one
-    where the FP64 geometry puts every pixel outside q <= 2 ln(255 o') (alpha below
-    1/255 everywhere), and the recipe keeps every tile some pixel of which is inside."""
+def test_library_binning_leaves_out_only_unreachable_tiles(orc, seed):
+    """The library's tighter binning (restated in tight_binning) keeps an
+    ordered sub-list of the oracle's lists, every pair it leaves out has
+    q > 2 ln(255 o') on its whole tile in FP64 (alpha below 1/255 at every
+    pixel, so the blend skips it there), and every pair it keeps is reachable
+    or within the bound's enlargement."""
+    from parity_util import box_min_q, unreachable
+    import tight_binning
     rng = np.random.default_rng(300 + seed)
     scene = synth.make_scene(rng, 3000, lobes=1, means="cube", cube_side=1.5, masks="uniform")
     scene.scales *= np.exp(rng.normal(0.0, 0.7, scene.scales.shape)).astype(np.float32)  # anisotropic
     cam = synth.make_camera(200, 150, 180.0)
-    dec = orc.decisions_fp32(scene, cam)
-    _, ids_full, ranges_full = orc.tile_lists(dec, cam, full_rect=True)
-    keys, ids, ranges = orc.tile_lists(dec, cam)
     res = orc.render_forward(scene, cam)
-    tile_full = np.repeat(np.arange(cam.n_tiles), ranges_full[:, 1] - ranges_full[:, 0])
-    tile_kept = np.repeat(np.arange(cam.n_tiles), ranges[:, 1] - ranges[:, 0])
-    full = set(zip(tile_full.tolist(), ids_full.tolist()))
-    kept = set(zip(tile_kept.tolist(), ids.tolist()))
-    assert kept <= full and len(kept) < 0.9 * len(full)
-    out = np.array(sorted(full - kept))
-    t, g = out[:, 0], out[:, 1]
-    qmin = _box_min_q(res.conic[g], res.xy[g], t % cam.tiles_x, t // cam.tiles_x)
-    thr = 2.0 * np.log(255.0 * res.op[g])
-    assert np.all(qmin > thr)
-    inn = np.array(sorted(kept))
-    qk = _box_min_q(res.conic[inn[:, 1]], res.xy[inn[:, 1]], inn[:, 0] % cam.tiles_x, inn[:, 0] // cam.tiles_x)
-    # kept tiles are reachable or within the enlargement of the bound
-    assert np.all(qk <= 1.02 * 2.0 * np.log(255.0 * res.op[inn[:, 1]]) + 0.5)
+    dec = res.dec
+    bound = tight_binning.binning_bound(scene)
+    keep = tight_binning.kept_pairs(dec, bound, cam, res.keys, res.ids)
+    tiles = (res.keys >> np.uint64(32)).astype(np.int64)
+    assert 0 < keep.sum() < 0.9 * len(keep)
+    assert unreachable(res, cam, tiles[~keep], res.ids[~keep]).all()
+    g = res.ids[keep]
+    qk = box_min_q(res.conic[g], res.xy[g], tiles[keep] % cam.tiles_x, tiles[keep] // cam.tiles_x)
+    assert np.all(qk <= 1.02 * 2.0 * np.log(255.0 * res.op[g]) + 0.5)
+    np.testing.assert_array_equal(tight_binning.touched(dec, bound), np.bincount(g, minlength=scene.n))
 
 
-def test_log2_recipe_accuracy(orc):
-    """The binning's log2 (atanh series on the mantissa) against FP64 log2 over the
+def test_log2_recipe_accuracy():
+    """The library's binning log2 (atanh series on the mantissa) against FP64 log2 over the
     range 255 o' takes: the series stops at s^7 with s <= 1/3, so the error is at
     most (2 / ln 2) s^9 / (9 (1 - s^2)) = 1.8e-5 (plus binary32 rounding); exact at
     powers of two."""
-    from oracle.sg_oracle import log2_recipe
+    from tight_binning import log2_recipe
     x = np.concatenate([np.geomspace(1.0, 255.0, 4001), 2.0 ** np.arange(0, 8)]).astype(np.float32)
     got = log2_recipe(x).astype(np.float64)
     ref = np.log2(x.astype(np.float64))
@@ -580,15 +523,8 @@ def test_tiled_equals_brute_force(orc):
         img, T, last = orc.brute_force(scene, cam, gate=True)
         np.testing.assert_array_equal(res.img, img)
         np.testing.assert_array_equal(res.T_final, T)
-        # last blended Gaussian: the brute force counts positions in the 3-sigma
-        # gated order (the full-rectangle lists), the tiled walk in the binned lists
-        _, ids_full, rg_full = orc.tile_lists(res.dec, cam, full_rect=True)
-        ty, tx = np.meshgrid(np.arange(32) // 16, np.arange(32) // 16, indexing="ij")
-        tile = ty * cam.tiles_x + tx
-        m = last > 0
-        np.testing.assert_array_equal(m, res.last > 0)
-        np.testing.assert_array_equal(ids_full[rg_full[tile[m], 0] + last[m] - 1],
-                                      res.ids[res.ranges[tile[m], 0] + res.last[m] - 1])
+        # positions in the 3-sigma gated (depth, index) order are those of the tile lists
+        np.testing.assert_array_equal(res.last, last)
         assert res.last.max() > 0
 
 
