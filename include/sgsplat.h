@@ -238,7 +238,15 @@ typedef struct sg_tuning {
     int32_t bwd_pixels_per_thread;
     int32_t fwd_persistent;   /* 1: resident blocks pull tiles, longest lists first */
     int32_t bwd_persistent;
-    int32_t reserved[4];
+    /* Bound on the polls a radix-sort block makes of a predecessor that has not
+     * yet published its digit counts (the decoupled look-back of the depth and
+     * tile sorts) before it gives up: 0 = the default 2^20 (about a second).
+     * A block that gives up records SG_ERR_TIMEOUT (returned by the plain
+     * forward, kept in the batched form's device status) and leaves that
+     * call's outputs unspecified but every access inside its buffers.
+     * Small values exist to test that path. */
+    int32_t sort_wait_polls;
+    int32_t reserved[3];
 } sg_tuning;
 int sg_set_tuning(const sg_tuning *t);
 int sg_get_tuning(sg_tuning *t);

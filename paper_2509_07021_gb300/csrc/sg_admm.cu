@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(256) k_prox_dual(int64_t n, int64_t kappa, con
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const uint32_t i = order[r];
+    if (i >= n) return;   // a stale word left by a sort whose bounded wait gave up
     const float xi = x[i], li = lam[i];
     const float z = __fadd_rn(xi, li);
     const float xt = r < kappa ? z : 0.0f;

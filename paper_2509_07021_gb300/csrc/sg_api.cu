@@ -102,7 +102,7 @@ struct StageTimer {
 };
 
 // Process-wide kernel shape choices (sg_set_tuning); defaults from measurement.
-constexpr sg_tuning kDefaultTuning = {2, 8, 0, 1, {0, 0, 0, 0}};
+constexpr sg_tuning kDefaultTuning = {2, 8, 0, 1, 0, {0, 0, 0}};
 sg_tuning &tuning() {
     static sg_tuning t = kDefaultTuning;
     return t;
@@ -464,11 +464,7 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     // grids sized by the capacity (at most SORT_MAX_KEYS pairs); counts read on the device
     const uint64_t cap_dev = std::min<uint64_t>(cap, SORT_MAX_KEYS);
     uint64_t K = cap_dev;
-    if (sync) {
-        SG_CUDA(cudaEventRecord(rb->ev, stream), "read pairs");
-    } else {
-        SG_CUDA(launch_capacity_status(counters, cap_dev, stream), "capacity status");
-    }
+    if (!sync) SG_CUDA(launch_capacity_status(counters, cap_dev, stream), "capacity status");
     // duplicate into the buffer from which an even/odd number of tile passes ends in *_final
     uint32_t *pk_final = reinterpret_cast<uint32_t *>(w + L.pkey_final);
     uint32_t *pv_final = reinterpret_cast<uint32_t *>(w + L.pval_final);
@@ -487,10 +483,13 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     {
         StageTimer t(ST_TILE_SORT, stream);
         // the last pass also bounds every tile's range in the sorted pairs
+        // plain form: the sorts' merged status also goes to the host word next to the pair count
         SG_CUDA(launch_radix_sort(k0, v0, k1, v1, counters + CNT_PAIRS, K, L.tile_bits, hist, aux_tile, stream,
-                                  counters + CNT_STATUS, nullptr, true, ranges, L.n_tiles, true),
+                                  counters + CNT_STATUS, nullptr, true, ranges, L.n_tiles, true,
+                                  rb ? rb->dev_ptr + 1 : nullptr),
                 "tile sort");
     }
+    if (sync) SG_CUDA(cudaEventRecord(rb->ev, stream), "read pairs");
     unsigned long long *evals =
         counting ? reinterpret_cast<unsigned long long *>(counters + CNT_EVALS) : nullptr;
     if (counting) SG_CUDA(cudaMemsetAsync(evals, 0, 8, stream), "clear counter");
@@ -528,7 +527,7 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         const volatile uint64_t *mirror = rb->host;
         const uint64_t n_pairs = mirror[0];
         if (mirror[1] == SG_ERR_TIMEOUT)
-            return fail(SG_ERR_TIMEOUT, "depth sort: a bounded device wait expired");
+            return fail(SG_ERR_TIMEOUT, "a sort's bounded device wait expired (outputs unspecified)");
         if (n_pairs > cap_dev) {
             const WsLayout need = make_layout(b, n_pairs);
             fill_sizes(b, need, n_pairs, out);
@@ -666,12 +665,15 @@ int64_t sg_kernel_launches(void) { return launch_counter().load(); }
 int sg_set_tuning(const sg_tuning *t) {
     if (!t) {
         tuning() = kDefaultTuning;
+        set_sort_wait_polls(0);
         return SG_OK;
     }
     if (!ppt_ok(t->fwd_pixels_per_thread) || !ppt_ok(t->bwd_pixels_per_thread))
         return fail(SG_ERR_INVALID_ARG, "pixels per thread must be 1, 2, 4 or 8 (got %d, %d)",
                     t->fwd_pixels_per_thread, t->bwd_pixels_per_thread);
+    if (t->sort_wait_polls < 0) return fail(SG_ERR_INVALID_ARG, "sort_wait_polls = %d < 0", t->sort_wait_polls);
     tuning() = *t;
+    set_sort_wait_polls((uint32_t)t->sort_wait_polls);
     return SG_OK;
 }
 

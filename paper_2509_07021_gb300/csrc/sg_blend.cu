@@ -126,6 +126,19 @@ __device__ __forceinline__ void stage(StagedN<NB> &sm, int slot, const Rec &rc, 
     sm.mask[slot] = CULL ? reach_mask(rc, x0, y0) : 0xFFu;
 }
 
+// Stages the list entry e, or, for an id outside the call's n_entries (a stale
+// word left by a sort whose bounded wait gave up), a slot no pixel evaluates.
+template <bool CULL, int NB>
+__device__ __forceinline__ void stage_entry(StagedN<NB> &sm, int slot, const Rec *__restrict__ rec, uint32_t e,
+                                            uint64_t n_entries, float x0, float y0) {
+    if (e < n_entries) {
+        stage<CULL>(sm, slot, rec[e], e, x0, y0);
+    } else {
+        sm.id[slot] = 0u;
+        sm.mask[slot] = 0u;
+    }
+}
+
 // Pixel (column, row inside the tile) of slot j of this thread. For P >= 2 the
 // slots 2i and 2i + 1 lie in the same pixel row (sub-blocks 2s and 2s + 1).
 template <int P>
@@ -235,10 +248,8 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
         for (int j = 0; j < P; ++j) all = all && done[j];
         if (__syncthreads_count(all) == NT) break;
         const int cnt = min(BATCH, n - base);
-        for (int k = threadIdx.x; k < cnt; k += NT) {
-            const uint32_t e = pval[rg.x + base + k];
-            stage<!COUNT>(sm, k, rec[e], e, x0, y0);
-        }
+        for (int k = threadIdx.x; k < cnt; k += NT)
+            stage_entry<!COUNT>(sm, k, rec, pval[rg.x + base + k], b.n_entries, x0, y0);
         __syncthreads();
         // the importance sums are warp collectives: there, only whole warps leave
         if (IMP ? __all_sync(0xffffffffu, all) : all) continue;
@@ -285,7 +296,9 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
             if (IMP && __any_sync(0xffffffffu, wsum != 0.f)) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-                if ((threadIdx.x & 31) == 0) atomicAdd(imp + (sm.id[k] - (uint32_t)vw->ent_off), wsum);
+                // only an entry of this view's scene (a stale id from another view is left out)
+                const uint32_t li = sm.id[k] - (uint32_t)vw->ent_off;
+                if ((threadIdx.x & 31) == 0 && li < (uint32_t)vw->n) atomicAdd(imp + li, wsum);
             }
         }
     }
@@ -506,10 +519,8 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
         const int start = max(0, end - BWD_BATCH);
         const int cnt = end - start;
         __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += NT) {
-            const uint32_t e = pval[rg.x + start + k];
-            stage<!COUNT>(sm, k, rec[e], e, x0, y0);
-        }
+        for (int k = threadIdx.x; k < cnt; k += NT)
+            stage_entry<!COUNT>(sm, k, rec, pval[rg.x + start + k], b.n_entries, x0, y0);
         __syncthreads();
         // warps whose pixels all end before this batch have nothing to add
         if (__all_sync(0xffffffffu, tmax <= start)) continue;

@@ -119,8 +119,8 @@ struct TileReach {
 };
 
 // The tile binning is a decision recipe like cull and rectangle: every step is
-// one binary32 operation with round-to-nearest (no contraction), so that the
-// FP64 oracle, repeating it in numpy float32, gets the same tiles. Its
+// one binary32 operation with round-to-nearest (no contraction), so that a
+// restatement in numpy float32 states exactly which tiles are kept. Its
 // constants are exact binary32 values (hexadecimal literals).
 constexpr float TR_C7 = 0x1.24924ap-3f;      // 1/7
 constexpr float TR_C5 = 0x1.99999ap-3f;      // 1/5
@@ -250,6 +250,8 @@ constexpr uint32_t SORT_DROP_KEY = 0xFFFFFFFFu;
 // aux_zeroed: the caller has already zeroed the aux region in this stream.
 // hist_ready: the caller has also written every pass's digit histogram into
 // aux and zeroed the sort_flag_words(max_n, bits) look-back words of hist.
+// status_mirror (nullable): receives *status after the sort (host memory mapped
+// into the device, read by the host behind an event).
 // ranges (nullable): keys are ids below n_ranges; the sort also writes each
 // id's [first, last + 1) position range in the sorted output, (0, 0) for an id
 // with no key. On entry every range must hold (RANGE_EMPTY, 0).
@@ -258,8 +260,12 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
                               uint64_t *aux, cudaStream_t s, uint64_t *status = nullptr,
                               uint64_t *kept_out = nullptr, bool aux_zeroed = false, uint2 *ranges = nullptr,
-                              uint64_t n_ranges = 0, bool hist_ready = false);
+                              uint64_t n_ranges = 0, bool hist_ready = false, uint64_t *status_mirror = nullptr);
 int radix_passes(int bits);
+// Bound on a sort block's polls of an unpublished predecessor before it gives
+// up and records SG_ERR_TIMEOUT (0: the default, 2^20).
+void set_sort_wait_polls(uint32_t polls);
+uint32_t sort_wait_polls();
 // Look-back flag words a sort of up to max_n keys of `bits` bits uses.
 uint64_t sort_flag_words(uint64_t max_n, int bits);
 

@@ -11,6 +11,8 @@
 // stable, so the result is identical to the 64-bit sort.
 #include "sg_internal.cuh"
 
+#include <atomic>
+
 namespace sgk {
 
 __host__ __device__ __forceinline__ int radix_passes_dev(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
@@ -56,12 +58,17 @@ __device__ __forceinline__ T block_exclusive(T x, T &total, T *sh /* >= 32 */) {
 // ---------------------------------------------------------------------------
 // exclusive scan: reduce -> spine -> downsweep
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t scan_load(const uint32_t *in, const uint32_t *idx, uint64_t i) {
-    return idx ? in[idx[i]] : in[i];
+// With idx, in[idx[i]]; an index outside in's n_in items reads 0. (Indices
+// come from a sort whose bounded wait may have given up, leaving stale words
+// in its output: the gather stays inside the array whatever they hold.)
+__device__ __forceinline__ uint32_t scan_load(const uint32_t *in, const uint32_t *idx, uint64_t i, uint64_t n_in) {
+    if (!idx) return in[i];
+    const uint32_t e = idx[i];
+    return e < n_in ? in[e] : 0u;
 }
 
 __global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *__restrict__ in,
-                                                     const uint32_t *__restrict__ idx, uint64_t n,
+                                                     const uint32_t *__restrict__ idx, uint64_t n_in, uint64_t n,
                                                      const uint64_t *__restrict__ n_dev,
                                                      uint64_t *__restrict__ sums) {
     __shared__ uint64_t sh[33];
@@ -71,7 +78,7 @@ __global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *__restrict_
 #pragma unroll 4
     for (int i = 0; i < SCAN_TILE / 256; ++i) {
         const uint64_t j = base + (uint64_t)i * 256 + threadIdx.x;
-        if (j < n) acc += scan_load(in, idx, j);
+        if (j < n) acc += scan_load(in, idx, j, n_in);
     }
     uint64_t tot;
     block_exclusive<uint64_t>(acc, tot, sh);
@@ -103,7 +110,7 @@ __global__ void __launch_bounds__(1024) k_scan_spine(uint64_t *__restrict__ sums
 }
 
 __global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ in,
-                                                   const uint32_t *__restrict__ idx, uint64_t n,
+                                                   const uint32_t *__restrict__ idx, uint64_t n_in, uint64_t n,
                                                    const uint64_t *__restrict__ n_dev,
                                                    const uint64_t *__restrict__ sums,
                                                    uint32_t *__restrict__ out) {
@@ -116,7 +123,7 @@ __global__ void __launch_bounds__(256) k_scan_down(const uint32_t *__restrict__ 
     for (int i = 0; i < SCAN_TILE / 256; ++i) {
         const int p = i * 256 + threadIdx.x;
         const uint64_t j = base + p;
-        buf[p + (p >> 5)] = j < n ? scan_load(in, idx, j) : 0u;
+        buf[p + (p >> 5)] = j < n ? scan_load(in, idx, j, n_in) : 0u;
     }
     __syncthreads();
     uint32_t loc[16];
@@ -157,11 +164,11 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
         if (total) return cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
         return cudaSuccess;
     }
-    k_scan_reduce<<<(unsigned)nb, 256, 0, s>>>(in, gather_idx, n, n_dev, block_sums);
+    k_scan_reduce<<<(unsigned)nb, 256, 0, s>>>(in, gather_idx, n, n, n_dev, block_sums);
     count_launches(1);
     k_scan_spine<<<1, 1024, 0, s>>>(block_sums, nb, total, mirror, status_src);
     count_launches(1);
-    k_scan_down<<<(unsigned)nb, 256, 0, s>>>(in, gather_idx, n, n_dev, block_sums, out);
+    k_scan_down<<<(unsigned)nb, 256, 0, s>>>(in, gather_idx, n, n, n_dev, block_sums, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -182,8 +189,17 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t
 // packed look-back word: 2 status bits, 30 count bits
 constexpr uint32_t LB_AGG = 1u << 30, LB_INC = 2u << 30, LB_VAL = (1u << 30) - 1u;
 static_assert(LB_VAL == SORT_MAX_KEYS, "look-back count width");
-constexpr int LB_SPIN_LIMIT = 1 << 20;
+constexpr uint32_t LB_SPIN_LIMIT = 1u << 20;   // default bound on unanswered look-back polls
 constexpr int LB_WINDOW = 16;
+
+// Process-wide bound on the polls a block makes of an unpublished predecessor
+// before it gives up (sg_tuning.sort_wait_polls; 0 = LB_SPIN_LIMIT).
+static std::atomic<uint32_t> g_spin_limit{0};
+void set_sort_wait_polls(uint32_t polls) { g_spin_limit.store(polls); }
+uint32_t sort_wait_polls() {
+    const uint32_t v = g_spin_limit.load();
+    return v ? v : LB_SPIN_LIMIT;
+}
 
 struct SortAux {
     uint32_t hist[4][RS_RADIX];   // global digit counts per pass
@@ -262,7 +278,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_os_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint64_t *__restrict__ n_dev, uint64_t max_n, int pass, int shift,
     uint32_t mask, bool drop, uint32_t *__restrict__ flags, SortAux *aux, uint2 *__restrict__ ranges,
-    uint64_t n_ranges) {
+    uint64_t n_ranges, uint32_t spin_limit) {
     constexpr int NW = RS_THREADS / 32;
     constexpr int PER_WARP = RS_TILE / NW;   // 512 consecutive keys per warp
     __shared__ uint32_t cnt[NW][RS_RADIX];
@@ -329,7 +345,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_os_pass(
     // add counts until the nearest tile that carries its inclusive prefix;
     // a tile not yet published stops the step and is re-read.
     uint32_t excl = 0u;
-    int spins = 0;
+    uint32_t spins = 0;
     for (int64_t p = (int64_t)t - 1; p >= 0;) {
         uint32_t fv[LB_WINDOW];
 #pragma unroll
@@ -348,7 +364,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_os_pass(
         if (found) break;
         p -= used;
         if (stalled) {
-            if (++spins > LB_SPIN_LIMIT) {
+            if (++spins >= spin_limit) {
                 atomicExch(&aux->status, (uint32_t)SG_ERR_TIMEOUT);
                 break;
             }
@@ -401,13 +417,17 @@ uint64_t sort_flag_words(uint64_t max_n, int bits) {
 
 // Status and kept count (one thread); ids that got no key get the range (0, 0).
 // no_pass: the keys had no bits, so no pass ran and every key is id 0.
+// status_mirror (nullable, host memory mapped into the device): receives the
+// status word after this sort's own status is merged in.
 __global__ void k_os_finish(const SortAux *aux, uint64_t *status, uint64_t *kept_out, uint2 *ranges,
-                            uint64_t n_ranges, bool no_pass, const uint64_t *n_dev, uint64_t max_n) {
+                            uint64_t n_ranges, bool no_pass, const uint64_t *n_dev, uint64_t max_n,
+                            uint64_t *status_mirror) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && !no_pass) {
         if (status && aux->status) *status = aux->status;
         if (kept_out) *kept_out = aux->kept;
     }
+    if (i == 0 && status_mirror) *status_mirror = status ? *status : 0u;
     if (!ranges || i >= n_ranges) return;
     if (no_pass) {
         const uint64_t nd = *n_dev, n = nd <= max_n ? nd : 0;   // none when over capacity
@@ -420,15 +440,22 @@ __global__ void k_os_finish(const SortAux *aux, uint64_t *status, uint64_t *kept
 cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
                               uint64_t *scan_sums, cudaStream_t s, uint64_t *status, uint64_t *kept_out,
-                              bool aux_zeroed, uint2 *ranges, uint64_t n_ranges, bool hist_ready) {
+                              bool aux_zeroed, uint2 *ranges, uint64_t n_ranges, bool hist_ready,
+                              uint64_t *status_mirror) {
     const uint32_t nblocks = (uint32_t)div_up(max_n, RS_TILE);
     const int passes = radix_passes(bits);
     const uint64_t fgrid = ranges ? std::max<uint64_t>(div_up(n_ranges, 256), 1) : 1;
     if (nblocks == 0 || passes == 0) {
         // nothing to sort; ranges still get their final values
         if (ranges) {
-            k_os_finish<<<(unsigned)fgrid, 256, 0, s>>>(reinterpret_cast<SortAux *>(scan_sums), nullptr, nullptr,
-                                                       ranges, n_ranges, passes == 0, n_dev, max_n);
+            k_os_finish<<<(unsigned)fgrid, 256, 0, s>>>(reinterpret_cast<SortAux *>(scan_sums), status, nullptr,
+                                                       ranges, n_ranges, passes == 0, n_dev, max_n, status_mirror);
+            count_launches(1);
+            return cudaGetLastError();
+        }
+        if (status_mirror) {
+            k_os_finish<<<1, 1, 0, s>>>(reinterpret_cast<SortAux *>(scan_sums), status, nullptr, nullptr, 0, true,
+                                        n_dev, max_n, status_mirror);
             count_launches(1);
             return cudaGetLastError();
         }
@@ -437,6 +464,7 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
     if (max_n > (uint64_t)LB_VAL) return cudaErrorInvalidValue;   // counts must fit the look-back word
     SortAux *aux = reinterpret_cast<SortAux *>(scan_sums);
     const bool drop = kept_out != nullptr;
+    const uint32_t spin_limit = sort_wait_polls();
     const uint64_t pass_words = (uint64_t)nblocks * RS_RADIX;
     if (!hist_ready) {
         if (!aux_zeroed) {
@@ -456,15 +484,15 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
         const uint64_t *np = (drop && p > 0) ? &aux->kept : n_dev;
         uint2 *rg = p == passes - 1 ? ranges : nullptr;
         k_os_pass<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, np, max_n, p, shift, mask, drop && p == 0,
-                                                 hist + pass_words * p, aux, rg, n_ranges);
+                                                 hist + pass_words * p, aux, rg, n_ranges, spin_limit);
         count_launches(1);
         uint32_t *t;
         t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
     }
-    if (status || kept_out || ranges) {
+    if (status || kept_out || ranges || status_mirror) {
         k_os_finish<<<(unsigned)fgrid, ranges ? 256 : 1, 0, s>>>(aux, status, kept_out, ranges, n_ranges, false,
-                                                                 n_dev, max_n);
+                                                                 n_dev, max_n, status_mirror);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -529,7 +557,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
     uint32_t e = 0, tt = 0, rows = 0, rx = 0, ry = 0, tbase = 0, tx = 1;
     if (j < V) {
         e = sorted_ent[j];
-        tt = tiles_touched[e];
+        tt = e < M ? tiles_touched[e] : 0u;   // a stale id (see scan_load) reaches no tile
         if (tt) {
             const Batch &b = *bp;
             const ViewDesc &vw = b.view[find_entry_view(b, e)];

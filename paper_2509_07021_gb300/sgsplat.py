@@ -81,7 +81,11 @@ class sg_ws_layout(ctypes.Structure):
 class sg_tuning(ctypes.Structure):
     _fields_ = [("fwd_pixels_per_thread", ctypes.c_int32), ("bwd_pixels_per_thread", ctypes.c_int32),
                 ("fwd_persistent", ctypes.c_int32), ("bwd_persistent", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("sort_wait_polls", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+TUNING_FIELDS = ("fwd_pixels_per_thread", "bwd_pixels_per_thread", "fwd_persistent", "bwd_persistent",
+                 "sort_wait_polls")
 
 
 class SGError(RuntimeError):
@@ -425,17 +429,16 @@ def sg_render_backward_noalloc(scene: DeviceScene, cams, ws, T_final, last, d_im
 
 
 def sg_set_tuning(fwd_pixels_per_thread=None, bwd_pixels_per_thread=None, fwd_persistent=None,
-                  bwd_persistent=None):
-    """Sets the blend kernels' shapes (unset fields keep their value); no
-    arguments restores the defaults."""
-    args = (fwd_pixels_per_thread, bwd_pixels_per_thread, fwd_persistent, bwd_persistent)
+                  bwd_persistent=None, sort_wait_polls=None):
+    """Sets the kernels' tuning (unset fields keep their value); no arguments
+    restores the defaults."""
+    args = (fwd_pixels_per_thread, bwd_pixels_per_thread, fwd_persistent, bwd_persistent, sort_wait_polls)
     if all(a is None for a in args):
         _check(lib().sg_set_tuning(None))
         return
     cur = sg_get_tuning()
     t = sg_tuning()
-    for name, val in zip(("fwd_pixels_per_thread", "bwd_pixels_per_thread", "fwd_persistent",
-                          "bwd_persistent"), args):
+    for name, val in zip(TUNING_FIELDS, args):
         setattr(t, name, int(cur[name] if val is None else val))
     _check(lib().sg_set_tuning(ctypes.byref(t)))
 
@@ -443,9 +446,7 @@ def sg_set_tuning(fwd_pixels_per_thread=None, bwd_pixels_per_thread=None, fwd_pe
 def sg_get_tuning() -> dict:
     t = sg_tuning()
     _check(lib().sg_get_tuning(ctypes.byref(t)))
-    return {"fwd_pixels_per_thread": int(t.fwd_pixels_per_thread),
-            "bwd_pixels_per_thread": int(t.bwd_pixels_per_thread),
-            "fwd_persistent": int(t.fwd_persistent), "bwd_persistent": int(t.bwd_persistent)}
+    return {k: int(getattr(t, k)) for k in TUNING_FIELDS}
 
 
 # ---------------------------------------------------------------------------
