@@ -427,8 +427,16 @@ int sg_postprocess_apply(const sg_scene *in, float tau_opacity, float tau_sharpn
  *    sg_sizes.bwd_ws_bytes up to that size (about 465,000 (view, Gaussian)
  *    entries). Larger calls return SG_ERR_WORKSPACE and do nothing.
  *  - Every GPU that loads the library holds the 16 MiB until the process
- *    exits. The first call on a device looks up the array's device address
- *    (once per device); make that first call before any stream capture.
+ *    exits. The CUDA runtime places the array when it loads this library's
+ *    device code on a device, which with lazy module loading can be as late
+ *    as this entry point's first call there; that first call also looks up
+ *    the array's device address (once per device). Make the first call on
+ *    each device (or run any other call of this library there) before a
+ *    region that must not allocate, and before any stream capture.
+ *  - Host side it uses the calling thread's stack, no heap: about 20 KB of
+ *    batch table plus a kernel-parameter block of up to 32 KB while the
+ *    setup kernel is launched. Threads with small stacks should call it
+ *    with at least 64 KB of stack free.
  *  - All calls share the one array: calls that overlap on the GPU (other
  *    streams, other threads) race and give wrong gradients. The array keeps
  *    the last call's contents; each call clears what it accumulates into.

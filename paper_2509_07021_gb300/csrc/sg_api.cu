@@ -497,6 +497,7 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     st = blend_shape(false, reinterpret_cast<uint32_t *>(w + L.order),
                      reinterpret_cast<uint32_t *>(counters + CNT_QUEUE), shape);
     if (st != SG_OK) return st;
+    shape.status = counters + CNT_STATUS;
     shape.importance = want_importance && !counting;
     if (shape.importance)
         for (int s = 0; s < n_scenes; ++s)
@@ -581,6 +582,7 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
     st = blend_shape(true, reinterpret_cast<uint32_t *>(bw + BL.order),
                      reinterpret_cast<uint32_t *>(counters + CNT_QUEUE), shape);
     if (st != SG_OK) return st;
+    shape.status = reinterpret_cast<const uint64_t *>(w + L.counters) + CNT_STATUS;   // the forward's
     {
         StageTimer t(ST_SETUP, stream);
         SG_CUDA(launch_setup(b, db, counters, stream), "setup");
@@ -1049,6 +1051,7 @@ extern "C" int sg_render_backward_noalloc(const sg_scene *scene, const sg_camera
     const uint64_t M = L.M;
     BlendShape shape{};   // one block per tile: no tile order or work counter needed
     shape.pixels_per_thread = tuning().bwd_pixels_per_thread;
+    shape.status = reinterpret_cast<const uint64_t *>(w + L.counters) + CNT_STATUS;   // the forward's
     // the setup kernel rewrites the table and counters; the accumulators are cleared
     SG_CUDA(launch_setup(b, db, counters, stream), "setup");
     if (M > 0) SG_CUDA(cudaMemsetAsync(dg, 0, 9 * M * sizeof(float), stream), "clear 2D gradients");

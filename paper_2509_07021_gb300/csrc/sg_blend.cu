@@ -126,19 +126,6 @@ __device__ __forceinline__ void stage(StagedN<NB> &sm, int slot, const Rec &rc, 
     sm.mask[slot] = CULL ? reach_mask(rc, x0, y0) : 0xFFu;
 }
 
-// Stages the list entry e, or, for an id outside the call's n_entries (a stale
-// word left by a sort whose bounded wait gave up), a slot no pixel evaluates.
-template <bool CULL, int NB>
-__device__ __forceinline__ void stage_entry(StagedN<NB> &sm, int slot, const Rec *__restrict__ rec, uint32_t e,
-                                            uint64_t n_entries, float x0, float y0) {
-    if (e < n_entries) {
-        stage<CULL>(sm, slot, rec[e], e, x0, y0);
-    } else {
-        sm.id[slot] = 0u;
-        sm.mask[slot] = 0u;
-    }
-}
-
 // Pixel (column, row inside the tile) of slot j of this thread. For P >= 2 the
 // slots 2i and 2i + 1 lie in the same pixel row (sub-blocks 2s and 2s + 1).
 template <int P>
@@ -208,13 +195,15 @@ __device__ __forceinline__ void add_evals(uint32_t ne, unsigned long long *evals
 // (also sums alpha T per Gaussian into its scene's importance array).
 enum : int { FWD_PLAIN = 0, FWD_COUNT = 1, FWD_IMPORTANCE = 2 };
 
+// lists_ok false: a sort's bounded wait gave up in this forward (its lists may
+// hold stale words): every tile renders as an empty list.
 template <int P, int MODE>
 __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, Staged &sm,
                                                const uint2 *__restrict__ ranges,
                                                const uint32_t *__restrict__ pval,
                                                const Rec *__restrict__ rec, float *__restrict__ img,
                                                float *__restrict__ T_final, int32_t *__restrict__ last,
-                                               uint32_t &ne) {
+                                               uint32_t &ne, bool lists_ok) {
     constexpr int NT = BLEND_THREADS / P;
     constexpr bool COUNT = MODE == FWD_COUNT;
     constexpr bool IMP = MODE == FWD_IMPORTANCE;
@@ -222,7 +211,7 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
     const ViewDesc *vw;
     tile_of_block(b, tile, tx, ty, vw);
     const uint2 rg = ranges[tile];
-    const int n = (int)(rg.y - rg.x);
+    const int n = lists_ok ? (int)(rg.y - rg.x) : 0;
     float *imp = IMP ? b.scene[vw->scene].importance : nullptr;
 
     float fpx[P], fpy[P], T[P], c0[P], c1[P], c2[P];
@@ -248,8 +237,10 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
         for (int j = 0; j < P; ++j) all = all && done[j];
         if (__syncthreads_count(all) == NT) break;
         const int cnt = min(BATCH, n - base);
-        for (int k = threadIdx.x; k < cnt; k += NT)
-            stage_entry<!COUNT>(sm, k, rec, pval[rg.x + base + k], b.n_entries, x0, y0);
+        for (int k = threadIdx.x; k < cnt; k += NT) {
+            const uint32_t e = pval[rg.x + base + k];
+            stage<!COUNT>(sm, k, rec[e], e, x0, y0);
+        }
         __syncthreads();
         // the importance sums are warp collectives: there, only whole warps leave
         if (IMP ? __all_sync(0xffffffffu, all) : all) continue;
@@ -326,13 +317,14 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const uint32_t *__restrict__ pval, const Rec *__restrict__ rec,
             float *__restrict__ img, float *__restrict__ T_final, int32_t *__restrict__ last,
             const uint32_t *__restrict__ tile_order, uint32_t *__restrict__ queue, uint32_t n_tiles,
-            unsigned long long *__restrict__ evals) {
+            unsigned long long *__restrict__ evals, const uint64_t *__restrict__ status) {
     __shared__ Staged sm;
     __shared__ uint32_t s_item;
     const Batch &b = *bp;
     uint32_t ne = 0;
+    const bool lists_ok = *status != (uint64_t)SG_ERR_TIMEOUT;
     if (!PERSIST) {
-        blend_fwd_tile<P, MODE>(b, blockIdx.x, sm, ranges, pval, rec, img, T_final, last, ne);
+        blend_fwd_tile<P, MODE>(b, blockIdx.x, sm, ranges, pval, rec, img, T_final, last, ne, lists_ok);
     } else {
         for (;;) {
             if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
@@ -341,7 +333,7 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             __syncthreads();
             if (item >= n_tiles) break;
             blend_fwd_tile<P, MODE>(b, tile_order ? tile_order[item] : item, sm, ranges, pval, rec, img,
-                                    T_final, last, ne);
+                                    T_final, last, ne, lists_ok);
         }
     }
     if (MODE == FWD_COUNT) add_evals(ne, evals);
@@ -354,13 +346,13 @@ static void fwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const 
     const unsigned grid = PERSIST ? (unsigned)sh.grid : n_tiles;
     if (evals)
         k_blend_fwd<P, FWD_COUNT, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
-            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, evals);
+            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, evals, sh.status);
     else if (sh.importance)
         k_blend_fwd<P, FWD_IMPORTANCE, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
-            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, nullptr);
+            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, nullptr, sh.status);
     else
         k_blend_fwd<P, FWD_PLAIN, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
-            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, nullptr);
+            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, nullptr, sh.status);
 }
 
 template <bool PERSIST>
@@ -384,6 +376,7 @@ cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 
     if (n_tiles == 0) return cudaSuccess;
     const bool persist = sh.persistent;
     if (persist && (sh.grid <= 0 || sh.queue == nullptr)) return cudaErrorInvalidValue;
+    if (sh.status == nullptr) return cudaErrorInvalidValue;
     cudaError_t e = persist ? fwd_dispatch<true>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s)
                             : fwd_dispatch<false>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s);
     if (e != cudaSuccess) return e;
@@ -465,6 +458,8 @@ __device__ __forceinline__ void bwd_adjoint(const PairEval &p, float dy, const f
 // dL/dpower = o' dG) and (dx, dy) = pixel - centre:
 //   0,1: sum dG dx, sum dG dy   2..4: sum dG dx^2, sum dG dx dy, sum dG dy^2
 //   5: dL/do' = sum dG   6..8: dL/drgb
+// lists_ok false: a sort of the forward gave up a bounded wait (its lists may
+// hold stale words): no pair contributes.
 template <int P, bool COUNT>
 __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, StagedB &sm, int *smax,
                                                const uint2 *__restrict__ ranges,
@@ -473,7 +468,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
                                                const float *__restrict__ T_final,
                                                const int32_t *__restrict__ last,
                                                const float *__restrict__ d_img, float *__restrict__ dg,
-                                               uint64_t M, uint32_t &ne) {
+                                               uint64_t M, uint32_t &ne, bool lists_ok) {
     constexpr int NT = BLEND_THREADS / P;
     int tx, ty;
     const ViewDesc *vw;
@@ -512,6 +507,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
     int maxlast = 0;
 #pragma unroll
     for (int i = 0; i < (NT + 31) / 32; ++i) maxlast = max(maxlast, smax[i]);
+    if (!lists_ok) maxlast = 0;
     const int sub0 = (int)(threadIdx.x >> 5) * P;
     const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
 
@@ -519,8 +515,10 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
         const int start = max(0, end - BWD_BATCH);
         const int cnt = end - start;
         __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += NT)
-            stage_entry<!COUNT>(sm, k, rec, pval[rg.x + start + k], b.n_entries, x0, y0);
+        for (int k = threadIdx.x; k < cnt; k += NT) {
+            const uint32_t e = pval[rg.x + start + k];
+            stage<!COUNT>(sm, k, rec[e], e, x0, y0);
+        }
         __syncthreads();
         // warps whose pixels all end before this batch have nothing to add
         if (__all_sync(0xffffffffu, tmax <= start)) continue;
@@ -574,15 +572,17 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const float *__restrict__ T_final, const int32_t *__restrict__ last,
             const float *__restrict__ d_img, float *__restrict__ dg, uint64_t M,
             const uint32_t *__restrict__ tile_order, uint32_t *__restrict__ queue, uint32_t n_tiles,
-            unsigned long long *__restrict__ evals) {
+            unsigned long long *__restrict__ evals, const uint64_t *__restrict__ status) {
     constexpr int NT = BLEND_THREADS / P;
     __shared__ StagedB sm;
     __shared__ int smax[(NT + 31) / 32];
     __shared__ uint32_t s_item;
     const Batch &b = *bp;
     uint32_t ne = 0;
+    const bool lists_ok = *status != (uint64_t)SG_ERR_TIMEOUT;
     if (!PERSIST) {
-        blend_bwd_tile<P, COUNT>(b, blockIdx.x, sm, smax, ranges, pval, rec, T_final, last, d_img, dg, M, ne);
+        blend_bwd_tile<P, COUNT>(b, blockIdx.x, sm, smax, ranges, pval, rec, T_final, last, d_img, dg, M, ne,
+                                 lists_ok);
     } else {
         for (;;) {
             if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
@@ -591,7 +591,7 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             __syncthreads();
             if (item >= n_tiles) break;
             blend_bwd_tile<P, COUNT>(b, tile_order ? tile_order[item] : item, sm, smax, ranges, pval, rec,
-                                     T_final, last, d_img, dg, M, ne);
+                                     T_final, last, d_img, dg, M, ne, lists_ok);
         }
     }
     if (COUNT) add_evals(ne, evals);
@@ -604,10 +604,10 @@ static void bwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const 
     const unsigned grid = PERSIST ? (unsigned)sh.grid : n_tiles;
     if (evals)
         k_blend_bwd<P, true, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
-            db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, evals);
+            db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, evals, sh.status);
     else
         k_blend_bwd<P, false, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
-            db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, nullptr);
+            db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, nullptr, sh.status);
 }
 
 template <bool PERSIST>
@@ -632,6 +632,7 @@ cudaError_t launch_blend_backward(const Batch *db, uint32_t n_tiles, const uint2
     if (n_tiles == 0) return cudaSuccess;
     const bool persist = sh.persistent;
     if (persist && (sh.grid <= 0 || sh.queue == nullptr)) return cudaErrorInvalidValue;
+    if (sh.status == nullptr) return cudaErrorInvalidValue;
     cudaError_t e = persist
         ? bwd_dispatch<true>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, sh, evals, s)
         : bwd_dispatch<false>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, sh, evals, s);

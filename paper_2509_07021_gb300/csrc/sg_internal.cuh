@@ -289,6 +289,7 @@ struct BlendShape {
     uint32_t *queue;              // persistent: zeroed work counter
     int grid;                     // persistent: resident blocks
     bool importance;              // forward: accumulate SceneDesc::importance
+    const uint64_t *status;       // the forward's status word: SG_ERR_TIMEOUT = lists unusable
 };
 
 cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
