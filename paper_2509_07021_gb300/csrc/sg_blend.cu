@@ -56,14 +56,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Gaussians staged per batch in the backward (smaller batches leave room for
 // more resident blocks of the one-warp, 8-pixels-per-thread shape).
 #ifndef SG_BWD_BATCH
-#define SG_BWD_BATCH 128
+#define SG_BWD_BATCH 64
 #endif
 constexpr int BWD_BATCH = SG_BWD_BATCH;
 static_assert(BWD_BATCH % 32 == 0 && BWD_BATCH <= 256, "backward batch");
 static_assert(BATCH % 32 == 0 && BATCH <= 1024, "forward batch");
 // Minimum resident blocks requested for the 8-pixels-per-thread backward.
 #ifndef SG_BWD8_MIN_BLOCKS
-#define SG_BWD8_MIN_BLOCKS 20
+#define SG_BWD8_MIN_BLOCKS 24
 #endif
 
 template <int NB>
@@ -462,6 +462,7 @@ __device__ __forceinline__ void bwd_adjoint(const PairEval &p, float dy, const f
 // hold stale words): no pair contributes.
 template <int P, bool COUNT>
 __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, StagedB &sm, int *smax,
+                                               float4 *__restrict__ spx, int *__restrict__ slot_last,
                                                const uint2 *__restrict__ ranges,
                                                const uint32_t *__restrict__ pval,
                                                const Rec *__restrict__ rec,
@@ -476,41 +477,53 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
     const uint2 rg = ranges[tile];
     const uint64_t HW = (uint64_t)vw->W * (uint64_t)vw->H;
     const float *gi = d_img + 3 * vw->pix_off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub0 = warp * P;
 
-    // Sg starts at T_final (bg . g), the background's share of every dL/dalpha
-    float fpx[P], fpy[P], T[P], g0[P], g1[P], g2[P], Sg[P];
-    int mylast[P];
+    // Per pixel slot: T and Sg in registers (they change along the walk); the
+    // upstream gradient and the last blended position, read-only here, in
+    // this thread's own shared-memory slots (one 16-byte word per pixel:
+    // g0, g1, g2, last), which keeps registers for more resident warps.
+    // Sg starts at T_final (bg . g), the background's share of every dL/dalpha.
+    // slot_last[s]: the largest last position over the pixels of sub-block s.
+    float T[P], Sg[P];
     int tmax = 0;
 #pragma unroll
     for (int j = 0; j < P; ++j) {
         int cx, cy;
         slot_pixel<P>(j, cx, cy);
         const int px = tx * TILE + cx, py = ty * TILE + cy;
-        fpx[j] = (float)px;
-        fpy[j] = (float)py;
-        T[j] = 1.f; g0[j] = g1[j] = g2[j] = 0.f; Sg[j] = 0.f; mylast[j] = 0;
+        float4 pg = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+        T[j] = 1.f;
+        Sg[j] = 0.f;
+        int lst = 0;
         if (px < vw->W && py < vw->H) {
             const uint64_t pix = (uint64_t)py * (uint64_t)vw->W + (uint64_t)px;
-            mylast[j] = last[vw->pix_off + pix];
+            lst = last[vw->pix_off + pix];
             const float tf = T_final[vw->pix_off + pix];
+            pg = make_float4(gi[pix], gi[HW + pix], gi[2 * HW + pix], __int_as_float(lst));
             T[j] = tf;
-            g0[j] = gi[pix];
-            g1[j] = gi[HW + pix];
-            g2[j] = gi[2 * HW + pix];
-            Sg[j] = tf * (g0[j] * vw->bg[0] + g1[j] * vw->bg[1] + g2[j] * vw->bg[2]);
+            Sg[j] = tf * (pg.x * vw->bg[0] + pg.y * vw->bg[1] + pg.z * vw->bg[2]);
         }
-        tmax = max(tmax, mylast[j]);
+        spx[(sub0 + j) * 32 + lane] = pg;
+        const int sl = __reduce_max_sync(0xffffffffu, lst);
+        if (lane == 0) slot_last[sub0 + j] = sl;
+        tmax = max(tmax, lst);
     }
     const int wmax = __reduce_max_sync(0xffffffffu, tmax);
-    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = wmax;
+    if (lane == 0) smax[warp] = wmax;
     __syncthreads();
     int maxlast = 0;
 #pragma unroll
     for (int i = 0; i < (NT + 31) / 32; ++i) maxlast = max(maxlast, smax[i]);
     if (!lists_ok) maxlast = 0;
-    const int sub0 = (int)(threadIdx.x >> 5) * P;
     const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
 
+    // Slots with a pixel whose walk reaches position pos (slot_last > pos):
+    // walking back, a slot turns live once and stays live, so the mask is
+    // rebuilt only when pos drops below the next slot's last (at most P times).
+    uint32_t live_slots = 0u;
+    int next_on = 0x7fffffff;   // rebuild when pos < next_on
     for (int end = maxlast; end > 0; end -= BWD_BATCH) {
         const int start = max(0, end - BWD_BATCH);
         const int cnt = end - start;
@@ -524,7 +537,18 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
         if (__all_sync(0xffffffffu, tmax <= start)) continue;
         for (int k = cnt - 1; k >= 0; --k) {
             const int pos = start + k;
-            const uint32_t msk = sm.mask[k] >> sub0;
+            if (pos < next_on) {   // warp-uniform
+                live_slots = 0u;
+                int nx = -1;
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    const int sl = slot_last[sub0 + j];
+                    if (sl > pos) live_slots |= 1u << j;
+                    else nx = max(nx, sl);
+                }
+                next_on = nx;   // the next slot turns live once pos drops below its last
+            }
+            const uint32_t msk = (sm.mask[k] >> sub0) & live_slots;
             if ((msk & ((1u << P) - 1u)) == 0u) continue;   // warp-uniform
             const float4 q = sm.q[k], r = sm.r[k];
             const float bl = sm.s[k];
@@ -537,16 +561,21 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
             for (int j0 = 0; j0 < P; j0 += RS) {
                 const uint32_t bits = (msk >> j0) & ((1u << RS) - 1u);
                 if (!bits) continue;                           // warp-uniform
+                float4 pg[RS];
+#pragma unroll
+                for (int hh = 0; hh < RS; ++hh) pg[hh] = spx[(sub0 + j0 + hh) * 32 + lane];
+                int cx, cy;
+                slot_pixel<P>(j0, cx, cy);
                 RowEval row;
-                eval_row(fpy[j0], q, r, row);
+                eval_row((float)(ty * TILE + cy), q, r, row);
                 // both pixels of the row first, with no branch between them
                 PairEval pe[RS];
                 bool ok[RS];
 #pragma unroll
                 for (int hh = 0; hh < RS; ++hh) {
-                    const int j = j0 + hh;
-                    eval_pixel(fpx[j], q, r, row, pe[hh]);
-                    const bool live = ((bits >> hh) & 1u) && pos < mylast[j];
+                    slot_pixel<P>(j0 + hh, cx, cy);
+                    eval_pixel((float)(tx * TILE + cx), q, r, row, pe[hh]);
+                    const bool live = ((bits >> hh) & 1u) && pos < __float_as_int(pg[hh].w);
                     if (COUNT) ne += live ? 1u : 0u;
                     ok[hh] = live && !(pe[hh].p2 > 0.f || pe[hh].alpha < ALPHA_MIN);
                 }
@@ -555,7 +584,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
                     const int j = j0 + hh;
                     if (!ok[hh]) continue;
                     any = true;
-                    bwd_adjoint(pe[hh], row.dy, r, bl, T[j], Sg[j], g0[j], g1[j], g2[j], v);
+                    bwd_adjoint(pe[hh], row.dy, r, bl, T[j], Sg[j], pg[hh].x, pg[hh].y, pg[hh].z, v);
                 }
             }
             // the moments are linear in dG: the conic factors and o' are applied
@@ -575,14 +604,16 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             unsigned long long *__restrict__ evals, const uint64_t *__restrict__ status) {
     constexpr int NT = BLEND_THREADS / P;
     __shared__ StagedB sm;
+    __shared__ float4 spx[BLEND_THREADS];   // per pixel slot: upstream gradient and last position
+    __shared__ int slot_last[BLEND_THREADS / 32];
     __shared__ int smax[(NT + 31) / 32];
     __shared__ uint32_t s_item;
     const Batch &b = *bp;
     uint32_t ne = 0;
     const bool lists_ok = *status != (uint64_t)SG_ERR_TIMEOUT;
     if (!PERSIST) {
-        blend_bwd_tile<P, COUNT>(b, blockIdx.x, sm, smax, ranges, pval, rec, T_final, last, d_img, dg, M, ne,
-                                 lists_ok);
+        blend_bwd_tile<P, COUNT>(b, blockIdx.x, sm, smax, spx, slot_last, ranges, pval, rec, T_final, last,
+                                 d_img, dg, M, ne, lists_ok);
     } else {
         for (;;) {
             if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
@@ -590,8 +621,8 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const uint32_t item = s_item;
             __syncthreads();
             if (item >= n_tiles) break;
-            blend_bwd_tile<P, COUNT>(b, tile_order ? tile_order[item] : item, sm, smax, ranges, pval, rec,
-                                     T_final, last, d_img, dg, M, ne, lists_ok);
+            blend_bwd_tile<P, COUNT>(b, tile_order ? tile_order[item] : item, sm, smax, spx, slot_last, ranges,
+                                     pval, rec, T_final, last, d_img, dg, M, ne, lists_ok);
         }
     }
     if (COUNT) add_evals(ne, evals);

@@ -286,15 +286,22 @@ def test_autograd_l1_loss_matches_oracle_adjoint():
 # ---------------------------------------------------------------------------
 
 def unambiguous_gaussians(results, n):
-    """Gaussians in no tile list of a tile that holds an ambiguous pixel of
-    any of the views (their importance has one correct value)."""
+    """Gaussians that reach no ambiguous pixel of any view: where every pixel a
+    Gaussian can blend at (alpha >= 1/255 in FP64, with a margin) has only
+    unambiguous decisions, its sum of weights has one correct value."""
     ok = np.ones(n, bool)
     for r in results:
         H, W = r.ambiguous.shape
         tiles_x = (W + 15) // 16
-        ty, tx = np.nonzero(r.ambiguous)
-        for t in np.unique((ty // 16) * tiles_x + tx // 16):
-            ok[r.ids[r.ranges[t, 0]:r.ranges[t, 1]]] = False
+        for py, px in zip(*np.nonzero(r.ambiguous)):
+            t = (py // 16) * tiles_x + px // 16
+            ids = r.ids[r.ranges[t, 0]:r.ranges[t, 1]]
+            dx, dy = px - r.xy[ids, 0], py - r.xy[ids, 1]
+            con = r.conic[ids]
+            q = con[:, 0] * dx * dx + 2 * con[:, 1] * dx * dy + con[:, 2] * dy * dy
+            with np.errstate(all="ignore"):
+                bound = 2.0 * np.log(255.0 * r.op[ids]) * 1.01 + 0.1
+            ok[ids[~(q > bound)]] = False
     return ok
 
 
