@@ -246,7 +246,13 @@ typedef struct sg_tuning {
      * call's outputs unspecified but every access inside its buffers.
      * Small values exist to test that path. */
     int32_t sort_wait_polls;
-    int32_t reserved[3];
+    /* Gaussians each blend block stages per shared-memory batch: the forward
+     * 32, 64 or 128, the backward 32 or 64 (0 = 64). Larger batches need fewer
+     * block barriers per list; smaller ones waste less staging on lists that
+     * end early. */
+    int32_t fwd_batch;
+    int32_t bwd_batch;
+    int32_t reserved[1];
 } sg_tuning;
 int sg_set_tuning(const sg_tuning *t);
 int sg_get_tuning(sg_tuning *t);
@@ -258,8 +264,9 @@ int sg_get_tuning(sg_tuning *t);
  * already be large enough, else the forward's SG_ERR_CAPACITY is returned).
  * Each candidate runs one untimed forward + backward, then `reps` (1..100)
  * timed ones (CUDA events on `stream`, synchronised here). The forward and the
- * backward each take their fastest shape; the choice is installed as by
- * sg_set_tuning and written to *chosen. times_ms (nullable, 16 floats) receives
+ * backward each take their fastest shape, then, with those shapes, their
+ * fastest batch size (fwd_batch 32 / 64 / 128, bwd_batch 32 / 64); the choice
+ * is installed as by sg_set_tuning and written to *chosen. times_ms (nullable, 16 floats) receives
  * the mean forward times of candidates c = 0..7 (P = 2^(c/2), persistent =
  * c % 2), then their mean backward times. The outputs and gradients hold the
  * last call's results. On an error the previous tuning is restored.

@@ -1,4 +1,5 @@
-"""Autotuner for the blend kernels' shape (pixels per thread).
+"""Autotuner for the blend kernels' shape (pixels per thread, persistent or
+one block per tile) and shared-memory batch size.
 
 Times each candidate on the caller's own scene and cameras with the library's
 stage events, picks the fastest forward and backward shape independently, and
@@ -15,6 +16,8 @@ import torch
 from . import render, sgsplat
 
 CANDIDATES = (1, 2, 4, 8)
+FWD_BATCHES = (32, 64, 128)
+BWD_BATCHES = (32, 64)
 
 
 def _cache_path():
@@ -60,15 +63,15 @@ def tune(ds, cams, d_img, reps=3, use_cache=True, candidates=CANDIDATES, persist
     if use_cache and key in cache:
         c = cache[key]
         sgsplat.sg_set_tuning(c["fwd_pixels_per_thread"], c["bwd_pixels_per_thread"],
-                              c.get("fwd_persistent", 0), c.get("bwd_persistent", 0))
+                              c.get("fwd_persistent", 0), c.get("bwd_persistent", 0),
+                              fwd_batch=c.get("fwd_batch", 0), bwd_batch=c.get("bwd_batch", 0))
         return dict(c, cached=True)
     grads = render.alloc_grads(ds)
-    timings = {}
     prev = sgsplat.sg_get_tuning()
-    shapes = [(p, q) for q in persistent for p in candidates]
-    for p, q in shapes:
-        sgsplat.sg_set_tuning(p, p, q, q)
-        out = render.render_forward(ds, cams)          # warm-up for this shape
+
+    def measure(**tuning):
+        sgsplat.sg_set_tuning(**tuning)
+        out = render.render_forward(ds, cams)          # warm-up for this choice
         render.render_backward(ds, cams, out, d_img, grads)
         torch.cuda.synchronize()
         sgsplat.sg_profile_enable(sgsplat.SG_PROFILE_EVENTS)
@@ -79,15 +82,33 @@ def tune(ds, cams, d_img, reps=3, use_cache=True, candidates=CANDIDATES, persist
         torch.cuda.synchronize()
         st = sgsplat.sg_profile_read(reset=True)["stages"]
         sgsplat.sg_profile_enable(0)
+        q_f, q_b = tuning["fwd_persistent"], tuning["bwd_persistent"]
         # the persistent forms also pay for their tile order (in tile_ranges / bwd_clear)
-        timings[(p, q)] = {"blend_fwd": (st["blend_fwd"]["ms"] + (st["tile_ranges"]["ms"] if q else 0)) / reps,
-                           "blend_bwd": (st["blend_bwd"]["ms"] + (st["bwd_clear"]["ms"] if q else 0)) / reps}
+        return {"blend_fwd": (st["blend_fwd"]["ms"] + (st["tile_ranges"]["ms"] if q_f else 0)) / reps,
+                "blend_bwd": (st["blend_bwd"]["ms"] + (st["bwd_clear"]["ms"] if q_b else 0)) / reps}
+
+    timings = {}
+    for p, q in [(p, q) for q in persistent for p in candidates]:
+        timings[(p, q)] = measure(fwd_pixels_per_thread=p, bwd_pixels_per_thread=p, fwd_persistent=q,
+                                  bwd_persistent=q, fwd_batch=0, bwd_batch=0)
     best_f = min(timings, key=lambda k: timings[k]["blend_fwd"])
     best_b = min(timings, key=lambda k: timings[k]["blend_bwd"])
-    sgsplat.sg_set_tuning(best_f[0], best_b[0], best_f[1], best_b[1])
+    # then the batch sizes for the chosen shapes
+    batch_ms = {}
+    for i in range(max(len(FWD_BATCHES), len(BWD_BATCHES))):
+        fb = FWD_BATCHES[min(i, len(FWD_BATCHES) - 1)]
+        bb = BWD_BATCHES[min(i, len(BWD_BATCHES) - 1)]
+        batch_ms[(fb, bb)] = measure(fwd_pixels_per_thread=best_f[0], bwd_pixels_per_thread=best_b[0],
+                                     fwd_persistent=best_f[1], bwd_persistent=best_b[1], fwd_batch=fb,
+                                     bwd_batch=bb)
+    fwd_batch = min(batch_ms, key=lambda k: batch_ms[k]["blend_fwd"])[0]
+    bwd_batch = min(batch_ms, key=lambda k: batch_ms[k]["blend_bwd"])[1]
+    sgsplat.sg_set_tuning(best_f[0], best_b[0], best_f[1], best_b[1], fwd_batch=fwd_batch, bwd_batch=bwd_batch)
     res = {"fwd_pixels_per_thread": best_f[0], "bwd_pixels_per_thread": best_b[0],
            "fwd_persistent": best_f[1], "bwd_persistent": best_b[1],
+           "fwd_batch": fwd_batch, "bwd_batch": bwd_batch,
            "ms": {f"p{k[0]}{'_persistent' if k[1] else ''}": v for k, v in timings.items()},
+           "batch_ms": {f"fwd{k[0]}_bwd{k[1]}": v for k, v in batch_ms.items()},
            "previous": prev}
     if use_cache:
         cache[key] = res

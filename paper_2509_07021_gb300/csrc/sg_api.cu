@@ -102,7 +102,8 @@ struct StageTimer {
 };
 
 // Process-wide kernel shape choices (sg_set_tuning); defaults from measurement.
-constexpr sg_tuning kDefaultTuning = {2, 8, 0, 1, 0, {0, 0, 0}};
+constexpr sg_tuning kDefaultTuning = {2, 8, 0, 1, 0, 0, 0, {0}};
+constexpr int kDefaultBatch = 64;
 sg_tuning &tuning() {
     static sg_tuning t = kDefaultTuning;
     return t;
@@ -318,7 +319,9 @@ int blend_shape(bool backward, const uint32_t *order, uint32_t *queue, BlendShap
     sh.persistent = (backward ? t.bwd_persistent : t.fwd_persistent) != 0;
     sh.tile_order = sh.persistent ? order : nullptr;
     sh.queue = queue;
-    sh.grid = sh.persistent ? blend_persistent_grid(backward, sh.pixels_per_thread) : 0;
+    const int nb = backward ? t.bwd_batch : t.fwd_batch;
+    sh.batch = nb ? nb : kDefaultBatch;
+    sh.grid = sh.persistent ? blend_persistent_grid(backward, sh.pixels_per_thread, sh.batch) : 0;
     if (sh.persistent && sh.grid <= 0)
         return fail(SG_ERR_CUDA, "persistent blend: occupancy query failed");
     return SG_OK;
@@ -674,6 +677,10 @@ int sg_set_tuning(const sg_tuning *t) {
         return fail(SG_ERR_INVALID_ARG, "pixels per thread must be 1, 2, 4 or 8 (got %d, %d)",
                     t->fwd_pixels_per_thread, t->bwd_pixels_per_thread);
     if (t->sort_wait_polls < 0) return fail(SG_ERR_INVALID_ARG, "sort_wait_polls = %d < 0", t->sort_wait_polls);
+    if (!(t->fwd_batch == 0 || t->fwd_batch == 32 || t->fwd_batch == 64 || t->fwd_batch == 128))
+        return fail(SG_ERR_INVALID_ARG, "fwd_batch must be 0, 32, 64 or 128 (got %d)", t->fwd_batch);
+    if (!(t->bwd_batch == 0 || t->bwd_batch == 32 || t->bwd_batch == 64))
+        return fail(SG_ERR_INVALID_ARG, "bwd_batch must be 0, 32 or 64 (got %d)", t->bwd_batch);
     tuning() = *t;
     set_sort_wait_polls((uint32_t)t->sort_wait_polls);
     return SG_OK;
@@ -814,16 +821,49 @@ int sg_autotune(const sg_scene *scene, const sg_camera *cams, int n_views, void 
         if (tf < best_f) { best_f = tf; bf = c; }
         if (tb < best_b) { best_b = tb; bb = c; }
     }
-    for (auto &e : ev) cudaEventDestroy(e);
-    if (st != SG_OK) {
-        tuning() = saved;
-        return st;
-    }
+    // then the batch sizes for the chosen shapes (forward 32 / 64 / 128, backward 32 / 64)
     sg_tuning t = saved;
     t.fwd_pixels_per_thread = 1 << (bf >> 1);
     t.fwd_persistent = bf & 1;
     t.bwd_pixels_per_thread = 1 << (bb >> 1);
     t.bwd_persistent = bb & 1;
+    int best_fb = 64, best_bb = 64;
+    best_f = best_b = 1e30f;
+    for (int c = 0; c < 3 && st == SG_OK; ++c) {
+        sg_tuning u = t;
+        u.fwd_batch = 32 << c;
+        u.bwd_batch = c < 2 ? 32 << c : 64;
+        tuning() = u;
+        float tf = 0.f, tb = 0.f;
+        for (int r = 0; r <= reps && st == SG_OK; ++r) {
+            sg_sizes sz{};
+            cudaEventRecord(ev[0], s);
+            st = forward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, img, T_final, last, nullptr, &sz, s,
+                              true);
+            if (st != SG_OK) break;
+            cudaEventRecord(ev[1], s);
+            st = backward_impl(scene, 1, cams, nullptr, n_views, ws, ws_bytes, T_final, last, d_img, bwd_ws,
+                               bwd_ws_bytes, grads, s);
+            if (st != SG_OK) break;
+            cudaEventRecord(ev[2], s);
+            const cudaError_t e = cudaEventSynchronize(ev[2]);
+            if (e != cudaSuccess) { st = cuda_fail(e, "autotune"); break; }
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[0], ev[1]);
+            cudaEventElapsedTime(&b, ev[1], ev[2]);
+            if (r > 0) { tf += a; tb += b; }
+        }
+        if (st != SG_OK) break;
+        if (tf < best_f) { best_f = tf; best_fb = u.fwd_batch; }
+        if (c < 2 && tb < best_b) { best_b = tb; best_bb = u.bwd_batch; }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st != SG_OK) {
+        tuning() = saved;
+        return st;
+    }
+    t.fwd_batch = best_fb;
+    t.bwd_batch = best_bb;
     tuning() = t;
     *chosen = t;
     return SG_OK;
@@ -1051,6 +1091,7 @@ extern "C" int sg_render_backward_noalloc(const sg_scene *scene, const sg_camera
     const uint64_t M = L.M;
     BlendShape shape{};   // one block per tile: no tile order or work counter needed
     shape.pixels_per_thread = tuning().bwd_pixels_per_thread;
+    shape.batch = tuning().bwd_batch ? tuning().bwd_batch : kDefaultBatch;
     shape.status = reinterpret_cast<const uint64_t *>(w + L.counters) + CNT_STATUS;   // the forward's
     // the setup kernel rewrites the table and counters; the accumulators are cleared
     SG_CUDA(launch_setup(b, db, counters, stream), "setup");

@@ -36,10 +36,10 @@ __device__ __forceinline__ int find_tile_view(const Batch &b, uint32_t t) {
 // with (qa, qb, qc) = -log2(e) * (A/2, B, C/2), so that
 //   power * log2(e) = qa dx^2 + qb dx dy + qc dy^2   and   exp(power) = 2^(that).
 constexpr float LOG2E = 1.4426950408889634f;
-#ifndef SG_FWD_BATCH
-#define SG_FWD_BATCH 64
-#endif
-constexpr int BATCH = SG_FWD_BATCH;   // Gaussians staged per shared-memory batch (forward)
+// Gaussians staged per shared-memory batch: a run-time choice (sg_tuning
+// fwd_batch / bwd_batch) up to these sizes, which fix the shared memory.
+constexpr int FWD_BATCH_MAX = 128;
+constexpr int BWD_BATCH_MAX = 64;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -53,14 +53,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-// Gaussians staged per batch in the backward (smaller batches leave room for
-// more resident blocks of the one-warp, 8-pixels-per-thread shape).
-#ifndef SG_BWD_BATCH
-#define SG_BWD_BATCH 64
-#endif
-constexpr int BWD_BATCH = SG_BWD_BATCH;
-static_assert(BWD_BATCH % 32 == 0 && BWD_BATCH <= 256, "backward batch");
-static_assert(BATCH % 32 == 0 && BATCH <= 1024, "forward batch");
+static_assert(BWD_BATCH_MAX % 32 == 0 && FWD_BATCH_MAX % 32 == 0, "batch sizes");
 // Minimum resident blocks requested for the 8-pixels-per-thread backward.
 #ifndef SG_BWD8_MIN_BLOCKS
 #define SG_BWD8_MIN_BLOCKS 24
@@ -74,8 +67,7 @@ struct StagedN {
     uint32_t id[NB];
     uint32_t mask[NB];   // sub-blocks of the tile the Gaussian can reach
 };
-using Staged = StagedN<BATCH>;
-using StagedB = StagedN<BWD_BATCH>;
+using StagedB = StagedN<BWD_BATCH_MAX>;
 
 // A 16x16 tile is 8 sub-blocks of 8x4 pixels: sub-block s covers columns
 // 8 (s & 1) .. +7 and rows 4 (s >> 1) .. +3 of the tile. Warp w's pixel slot j
@@ -197,8 +189,8 @@ enum : int { FWD_PLAIN = 0, FWD_COUNT = 1, FWD_IMPORTANCE = 2 };
 
 // lists_ok false: a sort's bounded wait gave up in this forward (its lists may
 // hold stale words): every tile renders as an empty list.
-template <int P, int MODE>
-__device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, Staged &sm,
+template <int P, int MODE, int NB>
+__device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, StagedN<NB> &sm,
                                                const uint2 *__restrict__ ranges,
                                                const uint32_t *__restrict__ pval,
                                                const Rec *__restrict__ rec, float *__restrict__ img,
@@ -231,12 +223,12 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
     }
     const int sub0 = (int)(threadIdx.x >> 5) * P;
     const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
-    for (int base = 0; base < n; base += BATCH) {
+    for (int base = 0; base < n; base += NB) {
         bool all = true;
 #pragma unroll
         for (int j = 0; j < P; ++j) all = all && done[j];
         if (__syncthreads_count(all) == NT) break;
-        const int cnt = min(BATCH, n - base);
+        const int cnt = min(NB, n - base);
         for (int k = threadIdx.x; k < cnt; k += NT) {
             const uint32_t e = pval[rg.x + base + k];
             stage<!COUNT>(sm, k, rec[e], e, x0, y0);
@@ -311,20 +303,20 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
 
 // Persistent form: resident blocks pull tiles from a work counter in the
 // given order (longest lists first); otherwise one block per tile.
-template <int P, int MODE, bool PERSIST>
+template <int P, int MODE, bool PERSIST, int NB>
 __global__ void __launch_bounds__(BLEND_THREADS / P)
 k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const uint32_t *__restrict__ pval, const Rec *__restrict__ rec,
             float *__restrict__ img, float *__restrict__ T_final, int32_t *__restrict__ last,
             const uint32_t *__restrict__ tile_order, uint32_t *__restrict__ queue, uint32_t n_tiles,
             unsigned long long *__restrict__ evals, const uint64_t *__restrict__ status) {
-    __shared__ Staged sm;
+    __shared__ StagedN<NB> sm;
     __shared__ uint32_t s_item;
     const Batch &b = *bp;
     uint32_t ne = 0;
     const bool lists_ok = *status != (uint64_t)SG_ERR_TIMEOUT;
     if (!PERSIST) {
-        blend_fwd_tile<P, MODE>(b, blockIdx.x, sm, ranges, pval, rec, img, T_final, last, ne, lists_ok);
+        blend_fwd_tile<P, MODE, NB>(b, blockIdx.x, sm, ranges, pval, rec, img, T_final, last, ne, lists_ok);
     } else {
         for (;;) {
             if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
@@ -332,27 +324,39 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const uint32_t item = s_item;
             __syncthreads();
             if (item >= n_tiles) break;
-            blend_fwd_tile<P, MODE>(b, tile_order ? tile_order[item] : item, sm, ranges, pval, rec, img,
-                                    T_final, last, ne, lists_ok);
+            blend_fwd_tile<P, MODE, NB>(b, tile_order ? tile_order[item] : item, sm, ranges, pval, rec, img,
+                                        T_final, last, ne, lists_ok);
         }
     }
     if (MODE == FWD_COUNT) add_evals(ne, evals);
 }
 
+template <int P, int MODE, bool PERSIST, int NB>
+static void fwd_launch(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval,
+                       const Rec *rec, float *img, float *T_final, int32_t *last, const BlendShape &sh,
+                       unsigned long long *evals, cudaStream_t s) {
+    const unsigned grid = PERSIST ? (unsigned)sh.grid : n_tiles;
+    k_blend_fwd<P, MODE, PERSIST, NB><<<grid, BLEND_THREADS / P, 0, s>>>(
+        db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, evals, sh.status);
+}
+
+// The plain forward takes the batch size of the tuning; the counting and
+// importance forms (whose results the batch does not change) take 64.
 template <int P, bool PERSIST>
 static void fwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval,
                   const Rec *rec, float *img, float *T_final, int32_t *last, const BlendShape &sh,
                   unsigned long long *evals, cudaStream_t s) {
-    const unsigned grid = PERSIST ? (unsigned)sh.grid : n_tiles;
     if (evals)
-        k_blend_fwd<P, FWD_COUNT, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
-            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, evals, sh.status);
+        fwd_launch<P, FWD_COUNT, PERSIST, 64>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s);
     else if (sh.importance)
-        k_blend_fwd<P, FWD_IMPORTANCE, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
-            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, nullptr, sh.status);
+        fwd_launch<P, FWD_IMPORTANCE, PERSIST, 64>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh,
+                                                   nullptr, s);
+    else if (sh.batch == 32)
+        fwd_launch<P, FWD_PLAIN, PERSIST, 32>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, nullptr, s);
+    else if (sh.batch == 128)
+        fwd_launch<P, FWD_PLAIN, PERSIST, 128>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, nullptr, s);
     else
-        k_blend_fwd<P, FWD_PLAIN, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
-            db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, nullptr, sh.status);
+        fwd_launch<P, FWD_PLAIN, PERSIST, 64>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, nullptr, s);
 }
 
 template <bool PERSIST>
@@ -376,7 +380,8 @@ cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 
     if (n_tiles == 0) return cudaSuccess;
     const bool persist = sh.persistent;
     if (persist && (sh.grid <= 0 || sh.queue == nullptr)) return cudaErrorInvalidValue;
-    if (sh.status == nullptr) return cudaErrorInvalidValue;
+    if (sh.status == nullptr || sh.batch < 32 || sh.batch > FWD_BATCH_MAX || sh.batch % 32 != 0)
+        return cudaErrorInvalidValue;
     cudaError_t e = persist ? fwd_dispatch<true>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s)
                             : fwd_dispatch<false>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s);
     if (e != cudaSuccess) return e;
@@ -469,7 +474,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
                                                const float *__restrict__ T_final,
                                                const int32_t *__restrict__ last,
                                                const float *__restrict__ d_img, float *__restrict__ dg,
-                                               uint64_t M, uint32_t &ne, bool lists_ok) {
+                                               uint64_t M, uint32_t &ne, bool lists_ok, int nb) {
     constexpr int NT = BLEND_THREADS / P;
     int tx, ty;
     const ViewDesc *vw;
@@ -524,8 +529,8 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
     // rebuilt only when pos drops below the next slot's last (at most P times).
     uint32_t live_slots = 0u;
     int next_on = 0x7fffffff;   // rebuild when pos < next_on
-    for (int end = maxlast; end > 0; end -= BWD_BATCH) {
-        const int start = max(0, end - BWD_BATCH);
+    for (int end = maxlast; end > 0; end -= nb) {
+        const int start = max(0, end - nb);
         const int cnt = end - start;
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += NT) {
@@ -601,7 +606,7 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const float *__restrict__ T_final, const int32_t *__restrict__ last,
             const float *__restrict__ d_img, float *__restrict__ dg, uint64_t M,
             const uint32_t *__restrict__ tile_order, uint32_t *__restrict__ queue, uint32_t n_tiles,
-            unsigned long long *__restrict__ evals, const uint64_t *__restrict__ status) {
+            unsigned long long *__restrict__ evals, const uint64_t *__restrict__ status, int nb) {
     constexpr int NT = BLEND_THREADS / P;
     __shared__ StagedB sm;
     __shared__ float4 spx[BLEND_THREADS];   // per pixel slot: upstream gradient and last position
@@ -613,7 +618,7 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
     const bool lists_ok = *status != (uint64_t)SG_ERR_TIMEOUT;
     if (!PERSIST) {
         blend_bwd_tile<P, COUNT>(b, blockIdx.x, sm, smax, spx, slot_last, ranges, pval, rec, T_final, last,
-                                 d_img, dg, M, ne, lists_ok);
+                                 d_img, dg, M, ne, lists_ok, nb);
     } else {
         for (;;) {
             if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
@@ -622,7 +627,7 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             __syncthreads();
             if (item >= n_tiles) break;
             blend_bwd_tile<P, COUNT>(b, tile_order ? tile_order[item] : item, sm, smax, spx, slot_last, ranges,
-                                     pval, rec, T_final, last, d_img, dg, M, ne, lists_ok);
+                                     pval, rec, T_final, last, d_img, dg, M, ne, lists_ok, nb);
         }
     }
     if (COUNT) add_evals(ne, evals);
@@ -635,10 +640,10 @@ static void bwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const 
     const unsigned grid = PERSIST ? (unsigned)sh.grid : n_tiles;
     if (evals)
         k_blend_bwd<P, true, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
-            db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, evals, sh.status);
+            db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, evals, sh.status, sh.batch);
     else
         k_blend_bwd<P, false, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
-            db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, nullptr, sh.status);
+            db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, nullptr, sh.status, sh.batch);
 }
 
 template <bool PERSIST>
@@ -663,7 +668,8 @@ cudaError_t launch_blend_backward(const Batch *db, uint32_t n_tiles, const uint2
     if (n_tiles == 0) return cudaSuccess;
     const bool persist = sh.persistent;
     if (persist && (sh.grid <= 0 || sh.queue == nullptr)) return cudaErrorInvalidValue;
-    if (sh.status == nullptr) return cudaErrorInvalidValue;
+    if (sh.status == nullptr || sh.batch < 32 || sh.batch > BWD_BATCH_MAX || sh.batch % 32 != 0)
+        return cudaErrorInvalidValue;
     cudaError_t e = persist
         ? bwd_dispatch<true>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, sh, evals, s)
         : bwd_dispatch<false>(db, n_tiles, ranges, pval, rec, T_final, last, d_img, dg, M, sh, evals, s);
@@ -684,21 +690,28 @@ static int occupancy_grid(K kernel, int threads) {
     return sms * (per > 0 ? per : 1);
 }
 
-int blend_persistent_grid(bool backward, int p) {
-    // cached per (device, direction, shape); devices beyond 16 are computed each time
-    static int cache[16][2][9] = {};
+template <int NB>
+static int fwd_grid(int p) {
+    switch (p) {
+        case 1: return occupancy_grid(k_blend_fwd<1, FWD_PLAIN, true, NB>, 256);
+        case 2: return occupancy_grid(k_blend_fwd<2, FWD_PLAIN, true, NB>, 128);
+        case 4: return occupancy_grid(k_blend_fwd<4, FWD_PLAIN, true, NB>, 64);
+        case 8: return occupancy_grid(k_blend_fwd<8, FWD_PLAIN, true, NB>, 32);
+    }
+    return 0;
+}
+
+int blend_persistent_grid(bool backward, int p, int batch) {
+    // cached per (device, direction, shape, forward batch); devices beyond 16 are computed each time
+    static int cache[16][2][9][3] = {};
     int dev = 0;
     cudaGetDevice(&dev);
+    const int bi = backward ? 0 : (batch == 32 ? 0 : batch == 128 ? 2 : 1);
     const bool cacheable = dev >= 0 && dev < 16 && p >= 1 && p <= 8;
-    if (cacheable && cache[dev][backward][p]) return cache[dev][backward][p];
+    if (cacheable && cache[dev][backward][p][bi]) return cache[dev][backward][p][bi];
     int g = 0;
     if (!backward) {
-        switch (p) {
-            case 1: g = occupancy_grid(k_blend_fwd<1, FWD_PLAIN, true>, 256); break;
-            case 2: g = occupancy_grid(k_blend_fwd<2, FWD_PLAIN, true>, 128); break;
-            case 4: g = occupancy_grid(k_blend_fwd<4, FWD_PLAIN, true>, 64); break;
-            case 8: g = occupancy_grid(k_blend_fwd<8, FWD_PLAIN, true>, 32); break;
-        }
+        g = bi == 0 ? fwd_grid<32>(p) : bi == 2 ? fwd_grid<128>(p) : fwd_grid<64>(p);
     } else {
         switch (p) {
             case 1: g = occupancy_grid(k_blend_bwd<1, false, true>, 256); break;
@@ -707,7 +720,7 @@ int blend_persistent_grid(bool backward, int p) {
             case 8: g = occupancy_grid(k_blend_bwd<8, false, true>, 32); break;
         }
     }
-    if (cacheable && g > 0) cache[dev][backward][p] = g;
+    if (cacheable && g > 0) cache[dev][backward][p][bi] = g;
     return g;
 }
 

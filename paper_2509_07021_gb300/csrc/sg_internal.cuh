@@ -290,6 +290,7 @@ struct BlendShape {
     int grid;                     // persistent: resident blocks
     bool importance;              // forward: accumulate SceneDesc::importance
     const uint64_t *status;       // the forward's status word: SG_ERR_TIMEOUT = lists unusable
+    int batch;                    // Gaussians staged per shared-memory batch
 };
 
 cudaError_t launch_blend_forward(const Batch *db, uint32_t n_tiles, const uint2 *ranges,
@@ -317,6 +318,6 @@ cudaError_t launch_post_apply(const sg_scene &sc, float tau_o, float tau_s, cons
                               int64_t n_out, int64_t l_out, cudaStream_t s);
 
 // Resident blocks per SM x SMs for the persistent blend of this shape.
-int blend_persistent_grid(bool backward, int pixels_per_thread);
+int blend_persistent_grid(bool backward, int pixels_per_thread, int batch);
 
 }  // namespace sgk

@@ -81,11 +81,12 @@ class sg_ws_layout(ctypes.Structure):
 class sg_tuning(ctypes.Structure):
     _fields_ = [("fwd_pixels_per_thread", ctypes.c_int32), ("bwd_pixels_per_thread", ctypes.c_int32),
                 ("fwd_persistent", ctypes.c_int32), ("bwd_persistent", ctypes.c_int32),
-                ("sort_wait_polls", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("sort_wait_polls", ctypes.c_int32), ("fwd_batch", ctypes.c_int32),
+                ("bwd_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 TUNING_FIELDS = ("fwd_pixels_per_thread", "bwd_pixels_per_thread", "fwd_persistent", "bwd_persistent",
-                 "sort_wait_polls")
+                 "sort_wait_polls", "fwd_batch", "bwd_batch")
 
 
 class SGError(RuntimeError):
@@ -379,6 +380,7 @@ def sg_autotune(scene: DeviceScene, cams, ws, img, T_final, last, d_img, bwd_ws,
     names = [f"p{1 << (k >> 1)}" + ("_persistent" if k & 1 else "") for k in range(8)]
     return {"fwd_pixels_per_thread": t.fwd_pixels_per_thread, "bwd_pixels_per_thread": t.bwd_pixels_per_thread,
             "fwd_persistent": t.fwd_persistent, "bwd_persistent": t.bwd_persistent,
+            "fwd_batch": t.fwd_batch, "bwd_batch": t.bwd_batch,
             "ms": {names[k]: {"fwd_call": times[k], "bwd_call": times[8 + k]} for k in range(8)}}
 
 
@@ -429,10 +431,11 @@ def sg_render_backward_noalloc(scene: DeviceScene, cams, ws, T_final, last, d_im
 
 
 def sg_set_tuning(fwd_pixels_per_thread=None, bwd_pixels_per_thread=None, fwd_persistent=None,
-                  bwd_persistent=None, sort_wait_polls=None):
+                  bwd_persistent=None, sort_wait_polls=None, fwd_batch=None, bwd_batch=None):
     """Sets the kernels' tuning (unset fields keep their value); no arguments
     restores the defaults."""
-    args = (fwd_pixels_per_thread, bwd_pixels_per_thread, fwd_persistent, bwd_persistent, sort_wait_polls)
+    args = (fwd_pixels_per_thread, bwd_pixels_per_thread, fwd_persistent, bwd_persistent, sort_wait_polls,
+            fwd_batch, bwd_batch)
     if all(a is None for a in args):
         _check(lib().sg_set_tuning(None))
         return

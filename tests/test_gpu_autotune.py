@@ -1,5 +1,6 @@
-"""sg_autotune (C ABI): times all eight blend shapes on the caller's buffers,
-installs the fastest forward and backward shape, and leaves correct results."""
+"""sg_autotune (C ABI): times all eight blend shapes, then the batch sizes, on
+the caller's buffers, installs the fastest forward and backward choice, and
+leaves correct results."""
 import numpy as np
 import pytest
 import torch
@@ -31,9 +32,11 @@ def test_autotune_installs_a_valid_choice_and_keeps_results():
         got = sgsplat.sg_autotune(ds, cams, ref.ws, img, T, last, d_img, bwd, grads, reps=2)
         torch.cuda.synchronize()
         t = sgsplat.sg_get_tuning()
-        for k in ("fwd_pixels_per_thread", "bwd_pixels_per_thread", "fwd_persistent", "bwd_persistent"):
+        for k in ("fwd_pixels_per_thread", "bwd_pixels_per_thread", "fwd_persistent", "bwd_persistent",
+                  "fwd_batch", "bwd_batch"):
             assert t[k] == got[k]
         assert t["fwd_pixels_per_thread"] in (1, 2, 4, 8) and t["bwd_persistent"] in (0, 1)
+        assert t["fwd_batch"] in (32, 64, 128) and t["bwd_batch"] in (32, 64)
         assert len(got["ms"]) == 8 and all(v["fwd_call"] > 0 and v["bwd_call"] > 0 for v in got["ms"].values())
         fastest_f = min(got["ms"].values(), key=lambda v: v["fwd_call"])["fwd_call"]
         name = f"p{t['fwd_pixels_per_thread']}" + ("_persistent" if t["fwd_persistent"] else "")

@@ -184,6 +184,24 @@ def test_every_blend_shape(ppt):
         sgsplat.sg_set_tuning(**old)
 
 
+@pytest.mark.parametrize("batches", [(32, 32), (128, 64), (64, 32)])
+def test_every_batch_size(batches):
+    """Every shared-memory batch size of both blend kernels against the oracle,
+    in both the one-block-per-tile and the persistent forms."""
+    rng = np.random.default_rng(610)
+    scene = synth.make_scene(rng, 5000, lobes=synth.LOBE_MIX, means="cube", cube_side=1.4,
+                             masks="uniform")
+    cam = synth.make_camera(70, 50, 70.0, bg=(0.3, 0.1, 0.2))
+    old = sgsplat.sg_get_tuning()
+    try:
+        for persistent in (0, 1):
+            sgsplat.sg_set_tuning(fwd_persistent=persistent, bwd_persistent=persistent, fwd_batch=batches[0],
+                                  bwd_batch=batches[1])
+            run_parity(scene, [cam], seed=14 + persistent)
+    finally:
+        sgsplat.sg_set_tuning(**old)
+
+
 @pytest.mark.parametrize("storage", ["f16", "f16_bf16s"])
 def test_half_precision_storage(storage):
     """Geometry and lobes stored in binary16 (sharpness optionally bfloat16),
@@ -199,6 +217,10 @@ def test_half_precision_storage(storage):
 def test_tuning_rejects_bad_shapes():
     with pytest.raises(sgsplat.SGError):
         sgsplat.sg_set_tuning(3, 4)
+    with pytest.raises(sgsplat.SGError):
+        sgsplat.sg_set_tuning(fwd_batch=48)
+    with pytest.raises(sgsplat.SGError):
+        sgsplat.sg_set_tuning(bwd_batch=128)
     sgsplat.sg_set_tuning()
     t = sgsplat.sg_get_tuning()
     assert (t["fwd_pixels_per_thread"], t["bwd_pixels_per_thread"], t["fwd_persistent"],
