@@ -255,7 +255,7 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     L.dval0 = take(M * 4);
     L.dkey1 = take(M * 4);
     L.dval1 = take(M * 4);
-    L.offsets = take(M * 4);
+    L.dup_flags = take(div_up(M, 256) * 8 + 8);   // the duplicate blocks' look-back words
     L.ranges = take(T * 8);
     L.order = take(T * 4);
     L.fixed_end = o;
@@ -421,7 +421,7 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     uint32_t *dval0 = reinterpret_cast<uint32_t *>(w + L.dval0);
     uint32_t *dkey1 = reinterpret_cast<uint32_t *>(w + L.dkey1);
     uint32_t *dval1 = reinterpret_cast<uint32_t *>(w + L.dval1);
-    uint32_t *offs = reinterpret_cast<uint32_t *>(w + L.offsets);
+    uint64_t *dup_flags = reinterpret_cast<uint64_t *>(w + L.dup_flags);
     uint2 *ranges = reinterpret_cast<uint2 *>(w + L.ranges);
     uint32_t *hist = reinterpret_cast<uint32_t *>(w + L.hist);
     uint64_t *sums = reinterpret_cast<uint64_t *>(w + L.scan_sums);
@@ -439,6 +439,8 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         z.words[1] = SORT_AUX_BYTES / 4;
         z.ptr[2] = reinterpret_cast<uint32_t *>(aux_tile);
         z.words[2] = SORT_AUX_BYTES / 4;
+        z.ptr[3] = reinterpret_cast<uint32_t *>(dup_flags);
+        z.words[3] = 2 * div_up(M, 256);
         StageTimer t(ST_SETUP, stream);
         SG_CUDA(launch_setup(b, db, counters, stream, z), "setup");
     }
@@ -456,18 +458,11 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
                                   stream, counters + CNT_STATUS, counters + CNT_VISIBLE, true),
                 "depth sort");
     }
-    CountReadback *rb = nullptr;   // plain form: where the scan leaves the pair count for the host
+    CountReadback *rb = nullptr;   // plain form: where the duplicate leaves the pair count for the host
     if (sync) SG_CUDA(count_readback(rb), "pair count readback");
-    {
-        StageTimer t(ST_OFFSETS, stream);
-        SG_CUDA(launch_scan(tt, dval0, offs, M, sums, counters + CNT_PAIRS, stream, counters + CNT_VISIBLE,
-                            rb ? rb->dev_ptr : nullptr, counters + CNT_STATUS),
-                "pair offsets");
-    }
     // grids sized by the capacity (at most SORT_MAX_KEYS pairs); counts read on the device
     const uint64_t cap_dev = std::min<uint64_t>(cap, SORT_MAX_KEYS);
     uint64_t K = cap_dev;
-    if (!sync) SG_CUDA(launch_capacity_status(counters, cap_dev, stream), "capacity status");
     // duplicate into the buffer from which an even/odd number of tile passes ends in *_final
     uint32_t *pk_final = reinterpret_cast<uint32_t *>(w + L.pkey_final);
     uint32_t *pv_final = reinterpret_cast<uint32_t *>(w + L.pval_final);
@@ -479,17 +474,19 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     {
         StageTimer t(ST_DUPLICATE, stream);
         // also the tile sort's digit histograms and cleared look-back flags
-        SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, rec, offs, counters, cap_dev, k0, v0, n_views, stream,
-                                 L.tile_passes, aux_tile, hist, sort_flag_words(K, L.tile_bits)),
+        // the pair offsets come from the duplicate blocks' own look-back (no scan kernel)
+        SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, rec, counters, cap_dev, k0, v0, dup_flags,
+                                 rb ? rb->dev_ptr : nullptr, stream, L.tile_passes, aux_tile, hist,
+                                 sort_flag_words(K, L.tile_bits)),
                 "duplicateWithKeys");
     }
     {
         StageTimer t(ST_TILE_SORT, stream);
         // the last pass also bounds every tile's range in the sorted pairs
         // plain form: the sorts' merged status also goes to the host word next to the pair count
-        SG_CUDA(launch_radix_sort(k0, v0, k1, v1, counters + CNT_PAIRS, K, L.tile_bits, hist, aux_tile, stream,
+        SG_CUDA(launch_radix_sort(k0, v0, k1, v1, counters + CNT_WRITTEN, K, L.tile_bits, hist, aux_tile, stream,
                                   counters + CNT_STATUS, nullptr, true, ranges, L.n_tiles, true,
-                                  rb ? rb->dev_ptr + 1 : nullptr),
+                                  rb ? rb->dev_ptr + 1 : nullptr, counters + CNT_STATUS),
                 "tile sort");
     }
     if (sync) SG_CUDA(cudaEventRecord(rb->ev, stream), "read pairs");

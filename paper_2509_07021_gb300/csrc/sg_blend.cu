@@ -188,7 +188,8 @@ __device__ __forceinline__ void add_evals(uint32_t ne, unsigned long long *evals
 enum : int { FWD_PLAIN = 0, FWD_COUNT = 1, FWD_IMPORTANCE = 2 };
 
 // lists_ok false: a sort's bounded wait gave up in this forward (its lists may
-// hold stale words): every tile renders as an empty list.
+// hold stale words): every tile renders as an empty list. (On a capacity
+// overflow the tile sort does not run and every range stays empty.)
 template <int P, int MODE, int NB>
 __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, StagedN<NB> &sm,
                                                const uint2 *__restrict__ ranges,

@@ -76,7 +76,9 @@ enum : int {
     CNT_TILES = 4,     // tiles
     CNT_QUEUE = 5,     // persistent-blend work counter
     CNT_VISIBLE = 6,   // entries with at least one pair (the depth order's length)
-    CNT_N = 8
+    CNT_DUP_BLOCK = 7, // duplicate kernel: next logical block
+    CNT_WRITTEN = 8,   // pairs the duplicate wrote (min(pairs, capacity)): the tile sort's count
+    CNT_N = 10
 };
 
 // Radix sort / scan geometry.
@@ -93,7 +95,7 @@ constexpr int SCAN_TILE = 4096;
 // forward and the backward of one call).
 struct WsLayout {
     size_t batch, counters, rec, tiles_touched, rect, clamp, dkey0, dval0, dkey1, dval1,
-        offsets, ranges, order, scan_sums, hist, aux_tile, fixed_end;
+        dup_flags, ranges, order, scan_sums, hist, aux_tile, fixed_end;
     size_t pval_final, pkey_final, pval_tmp, pkey_tmp, total;
     uint64_t M, n_tiles, cap;
     uint32_t hist_blocks;     // radix blocks of the larger sort
@@ -211,10 +213,10 @@ void count_launches(int n);
 // Regions the setup kernel fills: word i of region r gets even[r] if i is
 // even, else 0 (even[r] = 0: plain zeroing).
 struct ZeroRegions {
-    static constexpr int N = 3;
-    uint32_t *ptr[N] = {nullptr, nullptr, nullptr};
-    uint64_t words[N] = {0, 0, 0};
-    uint32_t even[N] = {0, 0, 0};
+    static constexpr int N = 4;
+    uint32_t *ptr[N] = {nullptr, nullptr, nullptr, nullptr};
+    uint64_t words[N] = {0, 0, 0, 0};
+    uint32_t even[N] = {0, 0, 0, 0};
 };
 cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStream_t s,
                          const ZeroRegions &z = ZeroRegions());
@@ -252,6 +254,9 @@ constexpr uint32_t SORT_DROP_KEY = 0xFFFFFFFFu;
 // aux and zeroed the sort_flag_words(max_n, bits) look-back words of hist.
 // status_mirror (nullable): receives *status after the sort (host memory mapped
 // into the device, read by the host behind an event).
+// skip_status (nullable): when it holds a status other than SG_OK (a bounded
+// wait gave up, so the input may hold stale words the histograms do not count;
+// or the pairs overflowed the capacity) the passes do nothing.
 // ranges (nullable): keys are ids below n_ranges; the sort also writes each
 // id's [first, last + 1) position range in the sorted output, (0, 0) for an id
 // with no key. On entry every range must hold (RANGE_EMPTY, 0).
@@ -260,7 +265,8 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
                               uint64_t *aux, cudaStream_t s, uint64_t *status = nullptr,
                               uint64_t *kept_out = nullptr, bool aux_zeroed = false, uint2 *ranges = nullptr,
-                              uint64_t n_ranges = 0, bool hist_ready = false, uint64_t *status_mirror = nullptr);
+                              uint64_t n_ranges = 0, bool hist_ready = false, uint64_t *status_mirror = nullptr,
+                              const uint64_t *skip_status = nullptr);
 int radix_passes(int bits);
 // Bound on a sort block's polls of an unpublished predecessor before it gives
 // up and records SG_ERR_TIMEOUT (0: the default, 2^20).
@@ -269,17 +275,24 @@ uint32_t sort_wait_polls();
 // Look-back flag words a sort of up to max_n keys of `bits` bits uses.
 uint64_t sort_flag_words(uint64_t max_n, int bits);
 
+// duplicateWithKeys over the depth-sorted entries. Every block of 256 entries
+// finds the offset of its pairs by a decoupled look-back over its predecessors'
+// pair counts (dup_flags: div_up(M, 256) zeroed 64-bit words, and
+// counters[CNT_DUP_BLOCK] zeroed), so no separate scan runs. The last block
+// writes the pair total to counters[CNT_PAIRS] (and to mirror[0], host memory
+// mapped into the device, when given), min(total, cap) to counters[CNT_WRITTEN],
+// and SG_ERR_CAPACITY to counters[CNT_STATUS] when the pairs exceed cap; pairs
+// at positions >= cap are not written. A status of SG_ERR_TIMEOUT on entry
+// (a sort gave up a bounded wait) makes the kernel write nothing.
 cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,
                              const uint32_t *tiles_touched, const uint2 *rect, const Rec *rec,
-                             const uint32_t *offsets, const uint64_t *counters, uint64_t cap,
-                             uint32_t *pkey, uint32_t *pval, int n_views, cudaStream_t s, int hist_passes = 0,
+                             uint64_t *counters, uint64_t cap, uint32_t *pkey, uint32_t *pval,
+                             uint64_t *dup_flags, uint64_t *mirror, cudaStream_t s, int hist_passes = 0,
                              uint64_t *sort_aux = nullptr, uint32_t *flags = nullptr, uint64_t flag_words = 0);
 // Tiles by descending list length (256 length buckets) into order[n_tiles];
 // scratch: 512 words.
 cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *scratch,
                               cudaStream_t s);
-// counters[CNT_STATUS] = SG_ERR_CAPACITY when the pairs exceed cap.
-cudaError_t launch_capacity_status(uint64_t *counters, uint64_t cap, cudaStream_t s);
 
 // Blend launch shape.
 struct BlendShape {

@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_os_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint64_t *__restrict__ n_dev, uint64_t max_n, int pass, int shift,
     uint32_t mask, bool drop, uint32_t *__restrict__ flags, SortAux *aux, uint2 *__restrict__ ranges,
-    uint64_t n_ranges, uint32_t spin_limit) {
+    uint64_t n_ranges, uint32_t spin_limit, const uint64_t *__restrict__ skip_status) {
     constexpr int NW = RS_THREADS / 32;
     constexpr int PER_WARP = RS_TILE / NW;   // 512 consecutive keys per warp
     __shared__ uint32_t cnt[NW][RS_RADIX];
@@ -289,6 +289,8 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_os_pass(
     __shared__ uint32_t shs[33];
     __shared__ uint32_t s_tile;
 
+    // an earlier bounded wait gave up (stale words) or the pairs overflowed (uniform)
+    if (skip_status && *skip_status != 0ull) return;
     if (threadIdx.x == 0) s_tile = atomicAdd(&aux->tile_ctr[pass], 1u);
     __syncthreads();
     const uint32_t t = s_tile;
@@ -441,7 +443,7 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
                               uint64_t *scan_sums, cudaStream_t s, uint64_t *status, uint64_t *kept_out,
                               bool aux_zeroed, uint2 *ranges, uint64_t n_ranges, bool hist_ready,
-                              uint64_t *status_mirror) {
+                              uint64_t *status_mirror, const uint64_t *skip_status) {
     const uint32_t nblocks = (uint32_t)div_up(max_n, RS_TILE);
     const int passes = radix_passes(bits);
     const uint64_t fgrid = ranges ? std::max<uint64_t>(div_up(n_ranges, 256), 1) : 1;
@@ -484,7 +486,8 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
         const uint64_t *np = (drop && p > 0) ? &aux->kept : n_dev;
         uint2 *rg = p == passes - 1 ? ranges : nullptr;
         k_os_pass<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, np, max_n, p, shift, mask, drop && p == 0,
-                                                 hist + pass_words * p, aux, rg, n_ranges, spin_limit);
+                                                 hist + pass_words * p, aux, rg, n_ranges, spin_limit,
+                                                 skip_status);
         count_launches(1);
         uint32_t *t;
         t = ki; ki = ko; ko = t;
@@ -525,39 +528,117 @@ __device__ __forceinline__ void hist_key_run(uint32_t (*h)[RS_RADIX], int passes
     }
 }
 
-// One block per 256 depth-sorted entries. The block's pairs go, entry by entry
-// and row by row, to [offsets[first entry], + the block's total): work items are
-// (entry, tile row); each finds its reached columns once and writes that run
-// (row-major inside an entry), so a large rectangle is spread over the whole
-// block and the stores stay coalesced. With hist_passes > 0 the kernel also
-// prepares the tile sort: it clears its look-back flags and adds exactly the
-// keys it writes to the digit histograms of its hist_passes passes.
+// Decoupled look-back words of the duplicate blocks: 2 status bits (aggregate,
+// inclusive prefix) and a 62-bit pair count.
+constexpr uint64_t DL_AGG = 1ull << 62, DL_INC = 2ull << 62, DL_VAL = (1ull << 62) - 1ull;
+
+__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed64(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" : : "l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Exclusive prefix of the pair counts of logical blocks [0, blk) (warp 0 of the
+// block; all its lanes return it). The block has published its own count
+// (DL_AGG) before it calls this, so successors never wait on a block that waits. Predecessors are read 32 at a time;
+// a run of ready words ending in an inclusive prefix completes the sum. Unready
+// words are polled at most spin_limit times; past that the status word gets
+// SG_ERR_TIMEOUT and the (smaller) partial prefix is returned.
+__device__ __forceinline__ uint64_t dup_lookback(uint64_t *__restrict__ dflags, uint64_t blk, uint64_t count,
+                                                 uint32_t spin_limit, uint64_t *status) {
+    const int lane = threadIdx.x & 31;
+    uint64_t excl = 0;
+    int64_t p = (int64_t)blk - 1;
+    uint32_t spins = 0;
+    while (p >= 0) {
+        const int64_t q = p - lane;
+        const uint64_t f = q >= 0 ? ld_relaxed64(dflags + q) : DL_INC;   // before block 0: prefix 0
+        const uint32_t unready = __ballot_sync(0xffffffffu, (f & ~DL_VAL) == 0ull);
+        const uint32_t inc = __ballot_sync(0xffffffffu, (f & DL_INC) != 0ull);
+        const int first_unready = unready ? __ffs(unready) - 1 : 32;
+        const int first_inc = inc ? __ffs(inc) - 1 : 32;
+        if (first_inc < first_unready) {
+            excl += warp_sum64(lane <= first_inc ? (f & DL_VAL) : 0ull);
+            break;
+        }
+        excl += warp_sum64(lane < first_unready ? (f & DL_VAL) : 0ull);
+        p -= first_unready;
+        if (first_unready < 32) {
+            if (++spins >= spin_limit) {
+                if (lane == 0) atomicExch(reinterpret_cast<unsigned long long *>(status),
+                                          (unsigned long long)SG_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    if (lane == 0) st_relaxed64(dflags + blk, DL_INC | ((excl + count) & DL_VAL));
+    return excl;
+}
+
+// One block per 256 depth-sorted entries, in the order the blocks start
+// (logical index from counters[CNT_DUP_BLOCK]). The block's pairs go, entry by
+// entry and row by row, to [out0, out0 + the block's total), out0 from the
+// look-back over the earlier blocks' totals: work items are (entry, tile row);
+// each finds its reached columns once and writes that run (row-major inside an
+// entry), so a large rectangle is spread over the whole block and the stores
+// stay coalesced. Positions at or past cap are not written. With hist_passes > 0
+// the kernel also prepares the tile sort: it clears its look-back flags and
+// adds exactly the keys it writes to the digit histograms of its hist_passes
+// passes.
 __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp, uint64_t M,
                                                    const uint32_t *__restrict__ sorted_ent,
                                                    const uint32_t *__restrict__ tiles_touched,
                                                    const uint2 *__restrict__ rect, const Rec *__restrict__ rec,
-                                                   const uint32_t *__restrict__ offsets,
-                                                   const uint64_t *__restrict__ counters, uint64_t cap,
+                                                   uint64_t *__restrict__ counters, uint64_t cap,
                                                    uint32_t *__restrict__ pkey,
                                                    uint32_t *__restrict__ pval, int hist_passes,
                                                    SortAux *__restrict__ aux, uint32_t *__restrict__ flags,
-                                                   uint64_t flag_words) {
+                                                   uint64_t flag_words, uint64_t *__restrict__ dflags,
+                                                   uint64_t *mirror, uint32_t spin_limit) {
     __shared__ uint32_t s_rinc[256], s_e[256], s_rx[256], s_ry[256], s_base[256], s_tx[256];
     __shared__ TileReach s_R[256];
     __shared__ uint32_t shs[33];
     __shared__ uint32_t h[4][RS_RADIX];
+    __shared__ unsigned long long s_blk, s_out0;
     // the tile sort's look-back flags start at zero (its passes run after this kernel)
     for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < flag_words; i += (uint64_t)gridDim.x * 256)
         flags[i] = 0u;
     for (int i = threadIdx.x; i < 4 * RS_RADIX; i += 256) h[i / RS_RADIX][i % RS_RADIX] = 0u;
-    if (counters[CNT_PAIRS] > cap) return;   // capacity exceeded: the host reports it (uniform)
-    const uint64_t j0 = (uint64_t)blockIdx.x * 256;
+    // a sort gave up a bounded wait: its order may hold stale words (uniform)
+    if (counters[CNT_STATUS] == (uint64_t)SG_ERR_TIMEOUT) return;
+    if (threadIdx.x == 0)
+        s_blk = atomicAdd(reinterpret_cast<unsigned long long *>(counters + CNT_DUP_BLOCK), 1ull);
+    __syncthreads();
+    const uint64_t blk = s_blk;
+    const uint64_t j0 = blk * 256;
     const uint64_t j = j0 + threadIdx.x;
     const uint64_t V = min(M, counters[CNT_VISIBLE]);   // entries in depth order with at least one pair
+    if (j0 >= V) {   // no entry: only the first block, when there is none at all, reports the zero total
+        if (V == 0 && blk == 0 && threadIdx.x == 0 && mirror) mirror[0] = 0;
+        return;
+    }
     uint32_t e = 0, tt = 0, rows = 0, rx = 0, ry = 0, tbase = 0, tx = 1;
     if (j < V) {
         e = sorted_ent[j];
         tt = e < M ? tiles_touched[e] : 0u;   // a stale id (see scan_load) reaches no tile
+    }
+    // the block's pair count goes out first; the row bookkeeping below hides the
+    // latency of the predecessors' counts
+    uint32_t total;
+    block_exclusive<uint32_t>(tt, total, shs);
+    if (threadIdx.x == 0) st_relaxed64(dflags + blk, DL_AGG | ((uint64_t)total & DL_VAL));
+    if (j < V) {
         if (tt) {
             const Batch &b = *bp;
             const ViewDesc &vw = b.view[find_entry_view(b, e)];
@@ -573,8 +654,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
             tile_reach_init(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, s_R[threadIdx.x]);
         }
     }
-    uint32_t total, total_rows;
-    block_exclusive<uint32_t>(tt, total, shs);
+    uint32_t total_rows;
     const uint32_t rexcl = block_exclusive<uint32_t>(rows, total_rows, shs);
     s_rinc[threadIdx.x] = rexcl + rows;
     s_e[threadIdx.x] = e;
@@ -582,9 +662,27 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
     s_ry[threadIdx.x] = ry;
     s_base[threadIdx.x] = tbase;
     s_tx[threadIdx.x] = tx;
+    if (threadIdx.x < 32) {
+        const uint64_t excl = dup_lookback(dflags, blk, total, spin_limit, counters + CNT_STATUS);
+        if (threadIdx.x == 0) {
+            s_out0 = excl;
+            if ((V - 1) / 256 == blk) {   // the last block: the totals
+                const uint64_t all = excl + total;
+                counters[CNT_PAIRS] = all;
+                counters[CNT_WRITTEN] = min(all, cap);
+                if (mirror) mirror[0] = all;
+                if (all > cap)
+                    atomicCAS(reinterpret_cast<unsigned long long *>(counters + CNT_STATUS), 0ull,
+                              (unsigned long long)SG_ERR_CAPACITY);
+            }
+        }
+    }
     __syncthreads();
     if (total == 0u) return;
-    const uint64_t out0 = offsets[j0];
+    const uint64_t out0 = s_out0;
+    // pairs the block may write: positions below cap only
+    const uint32_t lim = out0 >= cap ? 0u : (uint32_t)min((uint64_t)total, cap - out0);
+    if (lim == 0u) return;
     uint32_t done = 0u;
     for (uint32_t base = 0; base < total_rows; base += 256) {
         const uint32_t item = base + threadIdx.x;
@@ -606,21 +704,21 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
         const uint32_t key0 = s_base[o] + (uint32_t)row * s_tx[o];
         for (int c = c0; c < c1; ++c) {
             const uint32_t q = at + (uint32_t)(c - c0);
-            if (q < total) {   // rows sum to tiles_touched by construction; never write past the block
+            if (q < lim) {   // rows sum to tiles_touched by construction; never write past the block or cap
                 pkey[out0 + q] = key0 + (uint32_t)c;
                 pval[out0 + q] = s_e[o];
             }
         }
-        if (hist_passes > 0 && at < total)   // the keys written above, no more
+        if (hist_passes > 0 && at < lim)   // the keys written above, no more
             hist_key_run(h, hist_passes, key0 + (uint32_t)c0,
-                         key0 + (uint32_t)c0 + min((uint32_t)(c1 - c0), total - at));
+                         key0 + (uint32_t)c0 + min((uint32_t)(c1 - c0), lim - at));
         done += chunk;
     }
     // Rows add up to tiles_touched by construction. Should they ever fall short,
     // the rest of the block's range still gets valid tile ids and entries.
-    for (uint32_t q = done + threadIdx.x; q < total; q += 256) {
+    for (uint32_t q = done + threadIdx.x; q < lim; q += 256) {
         pkey[out0 + q] = s_base[0];
-        pval[out0 + q] = (uint32_t)j0;
+        pval[out0 + q] = s_e[0];
         if (hist_passes > 0) hist_key_run(h, hist_passes, s_base[0], s_base[0] + 1u);
     }
     if (hist_passes > 0) {
@@ -633,17 +731,15 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
 }
 
 cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,
-                             const uint32_t *tiles_touched, const uint2 *rect, const Rec *rec,
-                             const uint32_t *offsets,
-                             const uint64_t *counters, uint64_t cap, uint32_t *pkey, uint32_t *pval,
-                             int n_views, cudaStream_t s, int hist_passes, uint64_t *sort_aux,
-                             uint32_t *flags, uint64_t flag_words) {
-    (void)n_views;
-    if (M == 0 && flag_words == 0) return cudaSuccess;
+                             const uint32_t *tiles_touched, const uint2 *rect, const Rec *rec, uint64_t *counters,
+                             uint64_t cap, uint32_t *pkey, uint32_t *pval, uint64_t *dup_flags, uint64_t *mirror,
+                             cudaStream_t s, int hist_passes, uint64_t *sort_aux, uint32_t *flags,
+                             uint64_t flag_words) {
+    // one block at least: it reports the zero total of a call without entries
     const uint64_t grid = std::max<uint64_t>(div_up(M, 256), 1);
-    k_duplicate<<<(unsigned)grid, 256, 0, s>>>(db, M, sorted_ent, tiles_touched, rect, rec, offsets, counters, cap,
-                                               pkey, pval, hist_passes, reinterpret_cast<SortAux *>(sort_aux),
-                                               flags, flag_words);
+    k_duplicate<<<(unsigned)grid, 256, 0, s>>>(db, M, sorted_ent, tiles_touched, rect, rec, counters, cap, pkey,
+                                               pval, hist_passes, reinterpret_cast<SortAux *>(sort_aux), flags,
+                                               flag_words, dup_flags, mirror, sort_wait_polls());
     count_launches(1);
     return cudaGetLastError();
 }
@@ -701,16 +797,6 @@ cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *o
     k_tile_bucket_count<<<grid, 256, 0, s>>>(ranges, n_tiles, counts);
     k_tile_bucket_scatter<<<grid, 256, 0, s>>>(ranges, n_tiles, counts, cursor, order);
     count_launches(2);
-    return cudaGetLastError();
-}
-
-__global__ void k_capacity_status(uint64_t *counters, uint64_t cap) {
-    if (counters[CNT_PAIRS] > cap) counters[CNT_STATUS] = (uint64_t)SG_ERR_CAPACITY;
-}
-
-cudaError_t launch_capacity_status(uint64_t *counters, uint64_t cap, cudaStream_t s) {
-    k_capacity_status<<<1, 1, 0, s>>>(counters, cap);
-    count_launches(1);
     return cudaGetLastError();
 }
 
