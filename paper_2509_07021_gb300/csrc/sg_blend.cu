@@ -18,7 +18,6 @@
 
 namespace sgk {
 
-constexpr float ALPHA_MIN = 1.0f / 255.0f;
 constexpr float ALPHA_MAX = 0.99f;
 constexpr float T_STOP = 1e-4f;
 
@@ -47,6 +46,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// log2 of the opacity o' (a normal number wherever a pair is kept; a
+// subnormal flushes to -inf, which skips every pair)
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -63,9 +70,8 @@ template <int NB>
 struct StagedN {
     float4 q[NB];
     float4 r[NB];
-    float s[NB];
+    uint2 cm[NB];        // (bits of the third colour channel, sub-blocks of the tile the Gaussian can reach)
     uint32_t id[NB];
-    uint32_t mask[NB];   // sub-blocks of the tile the Gaussian can reach
 };
 using StagedB = StagedN<BWD_BATCH_MAX>;
 
@@ -109,13 +115,17 @@ __device__ __forceinline__ uint32_t reach_mask(const Rec &rc, float x0, float y0
     return mask;
 }
 
+// Staged per entry: q = (x, y, qa, qb), r = (qc, log2 o', c0, c1) with the
+// conic scaled by -log2(e)/2 (qb by -log2(e)), so that at d = pixel - centre
+//   power' = qa dx^2 + qb dx dy + qc dy^2 + log2 o' = log2(o' G),  alpha = min(0.99, 2^power').
+// o' < 1/255 gives the entry no pair (its record's bound t is negative), so
+// log2 o' is finite wherever a pair is evaluated with culling.
 template <bool CULL, int NB>
 __device__ __forceinline__ void stage(StagedN<NB> &sm, int slot, const Rec &rc, uint32_t e, float x0, float y0) {
     sm.q[slot] = make_float4(rc.a.x, rc.a.y, -0.5f * LOG2E * rc.a.z, -LOG2E * rc.a.w);
-    sm.r[slot] = make_float4(-0.5f * LOG2E * rc.b.x, rc.b.z, rc.b.w, rc.c.x);
-    sm.s[slot] = rc.c.y;
+    sm.r[slot] = make_float4(-0.5f * LOG2E * rc.b.x, lg2_approx(rc.b.z), rc.b.w, rc.c.x);
+    sm.cm[slot] = make_uint2(__float_as_uint(rc.c.y), CULL ? reach_mask(rc, x0, y0) : 0xFFu);
     sm.id[slot] = e;
-    sm.mask[slot] = CULL ? reach_mask(rc, x0, y0) : 0xFFu;
 }
 
 // Pixel (column, row inside the tile) of slot j of this thread. For P >= 2 the
@@ -133,34 +143,42 @@ template <int P>
 constexpr int row_slots() { return P >= 2 ? 2 : 1; }
 
 // The terms of the quadratic form that depend on the pixel row only:
-//   dy = y_pix - y, u = qc dy, b = qb dy, c = u dy
+//   dy = y_pix - y, u = qc dy, b = qb dy, c = u dy + log2 o'
 struct RowEval {
     float dy, u, b, c;
 };
 
+// ag = o' G = 2^power' (before the 0.99 clamp)
 struct PairEval {
-    float dx, t, p2, G, ag, alpha;
+    float dx, p2, ag, alpha;
 };
+
+// log2(1/255): alpha >= 1/255 is decided on the exponent, power' >= this bound.
+// The 3DGS rasterizer's power > 0 skip is left out: the dilated conic is
+// positive definite, so power > 0 can only come from rounding at a pixel
+// within ~1e-3 px of the centre, where the pair is kept.
+constexpr float LOG2_ALPHA_MIN = -7.99435343685885793f;
 
 // Every kernel that decides a skip evaluates a pair with this exact sequence of
 // explicitly rounded operations, so the forward and the backward agree:
-//   t = qa dx + qb dy,  power log2(e) = t dx + qc dy^2.
+//   t = qa dx + qb dy,  power' = t dx + (qc dy^2 + log2 o').
 __device__ __forceinline__ void eval_row(float fpy, const float4 &q, const float4 &r, RowEval &w) {
     w.dy = __fsub_rn(fpy, q.y);
     w.u = __fmul_rn(r.x, w.dy);
     w.b = __fmul_rn(q.w, w.dy);
-    w.c = __fmul_rn(w.u, w.dy);
+    w.c = __fmaf_rn(w.u, w.dy, r.y);
 }
 
-__device__ __forceinline__ void eval_pixel(float fpx, const float4 &q, const float4 &r, const RowEval &w,
-                                           PairEval &p) {
+__device__ __forceinline__ void eval_pixel(float fpx, const float4 &q, const RowEval &w, PairEval &p) {
     p.dx = __fsub_rn(fpx, q.x);
-    p.t = __fmaf_rn(q.z, p.dx, w.b);
-    p.p2 = __fmaf_rn(p.t, p.dx, w.c);
-    p.G = ex2_approx(p.p2);
-    p.ag = __fmul_rn(r.y, p.G);
+    const float t = __fmaf_rn(q.z, p.dx, w.b);
+    p.p2 = __fmaf_rn(t, p.dx, w.c);
+    p.ag = ex2_approx(p.p2);
     p.alpha = fminf(ALPHA_MAX, p.ag);
 }
+
+// The pair's skip rule (alpha < 1/255), on the exponent; NaN is skipped.
+__device__ __forceinline__ bool pair_kept(const PairEval &p) { return p.p2 >= LOG2_ALPHA_MIN; }
 
 __device__ __forceinline__ bool tile_of_block(const Batch &b, uint32_t tile, int &tx, int &ty,
                                               const ViewDesc *&vw) {
@@ -238,10 +256,11 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
         // the importance sums are warp collectives: there, only whole warps leave
         if (IMP ? __all_sync(0xffffffffu, all) : all) continue;
         for (int k = 0; k < cnt; ++k) {
-            const uint32_t msk = sm.mask[k] >> sub0;
+            const uint2 cm = sm.cm[k];
+            const uint32_t msk = cm.y >> sub0;
             if ((msk & ((1u << P) - 1u)) == 0u) continue;   // warp-uniform
             const float4 q = sm.q[k], r = sm.r[k];
-            const float bl = sm.s[k];
+            const float bl = __uint_as_float(cm.x);
             float wsum = 0.f;
             constexpr int RS = row_slots<P>();
 #pragma unroll
@@ -256,19 +275,20 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
 #pragma unroll
                 for (int h = 0; h < RS; ++h) {
                     const int j = j0 + h;
-                    eval_pixel(fpx[j], q, r, row, pe[h]);
+                    eval_pixel(fpx[j], q, row, pe[h]);
                     const bool live = ((bits >> h) & 1u) && !done[j];
                     if (COUNT) ne += live ? 1u : 0u;
-                    ok[h] = live && !(pe[h].p2 > 0.f || pe[h].alpha < ALPHA_MIN);
+                    ok[h] = live && pair_kept(pe[h]);
                 }
 #pragma unroll
                 for (int h = 0; h < RS; ++h) {
                     const int j = j0 + h;
                     if (!ok[h]) continue;
                     const PairEval &p = pe[h];
-                    const float tt = __fmul_rn(T[j], __fsub_rn(1.f, p.alpha));
+                    // T (1 - alpha) as T - alpha T
+                    const float w = __fmul_rn(p.alpha, T[j]);
+                    const float tt = __fsub_rn(T[j], w);
                     if (tt < T_STOP) { done[j] = true; continue; }
-                    const float w = p.alpha * T[j];
                     c0[j] = fmaf(r.z, w, c0[j]);
                     c1[j] = fmaf(r.w, w, c1[j]);
                     c2[j] = fmaf(bl, w, c2[j]);
@@ -443,16 +463,16 @@ __device__ __forceinline__ void bwd_adjoint(const PairEval &p, float dy, const f
     v[6] = fmaf(w, g0, v[6]);
     v[7] = fmaf(w, g1, v[7]);
     v[8] = fmaf(w, g2, v[8]);
-    // dL/do' share of this pixel; none where the 0.99 clamp is active.
-    // dL/dpower = o' dG: the factor o' is applied once per Gaussian.
-    const float dG = p.ag > ALPHA_MAX ? 0.f : dal * p.G;
-    v[5] += dG;
-    const float hx = dG * p.dx, hy = dG * dy;
-    v[0] += hx;                          // sum dG dx
-    v[1] += hy;                          // sum dG dy
-    v[2] = fmaf(hx, p.dx, v[2]);         // sum dG dx^2
-    v[3] = fmaf(hx, dy, v[3]);           // sum dG dx dy
-    v[4] = fmaf(hy, dy, v[4]);           // sum dG dy^2
+    // dP = dL/dpower = dL/dalpha o' G, none where the 0.99 clamp is active
+    // (dL/do' = dP / o': the division is applied once per Gaussian)
+    const float dP = p.ag > ALPHA_MAX ? 0.f : dal * p.ag;
+    v[5] += dP;
+    const float hx = dP * p.dx, hy = dP * dy;
+    v[0] += hx;                          // sum dP dx
+    v[1] += hy;                          // sum dP dy
+    v[2] = fmaf(hx, p.dx, v[2]);         // sum dP dx^2
+    v[3] = fmaf(hx, dy, v[3]);           // sum dP dx dy
+    v[4] = fmaf(hy, dy, v[4]);           // sum dP dy^2
 }
 
 // Per pixel the walk runs back from the pixel's last blended pair, recovering
@@ -460,10 +480,10 @@ __device__ __forceinline__ void bwd_adjoint(const PairEval &p, float dy, const f
 // keeping Sg = sum over later pairs of (c . g) alpha T, so that
 //   dL/dalpha_i = T_i (c_i . g) - (Sg + T_final (bg . g)) / (1 - alpha_i).
 // Per-thread sums over its P pixels are reduced over the warp before the
-// atomics. Accumulated per pair (in dg order), with dG = dL/dalpha G (so that
-// dL/dpower = o' dG) and (dx, dy) = pixel - centre:
-//   0,1: sum dG dx, sum dG dy   2..4: sum dG dx^2, sum dG dx dy, sum dG dy^2
-//   5: dL/do' = sum dG   6..8: dL/drgb
+// atomics. Accumulated per pair (in dg order), with dP = dL/dpower =
+// dL/dalpha o' G (alpha = o' G below the clamp) and (dx, dy) = pixel - centre:
+//   0,1: sum dP dx, sum dP dy   2..4: sum dP dx^2, sum dP dx dy, sum dP dy^2
+//   5: sum dP (= o' dL/do')   6..8: dL/drgb
 // lists_ok false: a sort of the forward gave up a bounded wait (its lists may
 // hold stale words): no pair contributes.
 template <int P, bool COUNT>
@@ -554,10 +574,11 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
                 }
                 next_on = nx;   // the next slot turns live once pos drops below its last
             }
-            const uint32_t msk = (sm.mask[k] >> sub0) & live_slots;
+            const uint2 cm = sm.cm[k];
+            const uint32_t msk = (cm.y >> sub0) & live_slots;
             if ((msk & ((1u << P) - 1u)) == 0u) continue;   // warp-uniform
             const float4 q = sm.q[k], r = sm.r[k];
-            const float bl = sm.s[k];
+            const float bl = __uint_as_float(cm.x);
             float v[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) v[i] = 0.f;
@@ -580,10 +601,10 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
 #pragma unroll
                 for (int hh = 0; hh < RS; ++hh) {
                     slot_pixel<P>(j0 + hh, cx, cy);
-                    eval_pixel((float)(tx * TILE + cx), q, r, row, pe[hh]);
+                    eval_pixel((float)(tx * TILE + cx), q, row, pe[hh]);
                     const bool live = ((bits >> hh) & 1u) && pos < __float_as_int(pg[hh].w);
                     if (COUNT) ne += live ? 1u : 0u;
-                    ok[hh] = live && !(pe[hh].p2 > 0.f || pe[hh].alpha < ALPHA_MIN);
+                    ok[hh] = live && pair_kept(pe[hh]);
                 }
 #pragma unroll
                 for (int hh = 0; hh < RS; ++hh) {
@@ -593,7 +614,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Batch &b, uint32_t tile, St
                     bwd_adjoint(pe[hh], row.dy, r, bl, T[j], Sg[j], pg[hh].x, pg[hh].y, pg[hh].z, v);
                 }
             }
-            // the moments are linear in dG: the conic factors and o' are applied
+            // the moments are linear in dP: the conic factors and 1/o' are applied
             // once per entry by the preprocess adjoint, after the sum over tiles
             if (__any_sync(0xffffffffu, any)) warp_sum9_atomic(v, dg, M, sm.id[k]);
         }

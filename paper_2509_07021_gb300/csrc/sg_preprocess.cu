@@ -578,7 +578,8 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
             // With one view, every load is issued before the visibility test (the
             // latency of the test is hidden).
             const uint32_t tte = multi_view ? 1u : tiles_touched[e];
-            // moments of dG = dL/dalpha G over the entry's pixels (dx, dy = pixel - centre)
+            // moments of dP = dL/dpower = dL/dalpha o' G over the entry's pixels
+            // (dx, dy = pixel - centre); gop = sum dP = o' dL/do'.
             const float mdx = dg[e], mdy = dg[M + e], mdxx = dg[2 * M + e], mdxy = dg[3 * M + e],
                         mdyy = dg[4 * M + e], gop = dg[5 * M + e];
             const float grgb[3] = {dg[6 * M + e], dg[7 * M + e], dg[8 * M + e]};
@@ -586,10 +587,6 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
             if (tte == 0u) continue;
             // the forward's clamp max(c, 0) per channel, read back from its bits
             const float gc[3] = {(cl & 1u) ? 0.f : grgb[0], (cl & 2u) ? 0.f : grgb[1], (cl & 4u) ? 0.f : grgb[2]};
-
-            // o' = m_g * o
-            d_opac += gm * gop;
-            d_gmask += o * gop;
 
             // ---- colour (Eq. 2) ----
             float vx = px - vw.campos[0], vy = py - vw.campos[1], vz = pz - vw.campos[2];
@@ -681,11 +678,17 @@ k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tile
             // its intermediates are not live across the lobe loop) ----
             Geo G;
             project_view(vw, px, py, pz, g3, o, gm, G);
-            // dL/dpower = o' dG with power = -(A dx^2 + C dy^2) / 2 - B dx dy and
-            // d/dx = -d/d(dx): the gradients of the centre and of the conic
-            const float gx = G.op * (G.conA * mdx + G.conB * mdy);
-            const float gy = G.op * (G.conB * mdx + G.conC * mdy);
-            const float gA = -0.5f * G.op * mdxx, gB = -G.op * mdxy, gC = -0.5f * G.op * mdyy;
+            // o' = m_g * o; a Gaussian with o' = 0 blends no pair (gop = 0)
+            {
+                const float dop = G.op > 0.f ? gop / G.op : 0.f;
+                d_opac += gm * dop;
+                d_gmask += o * dop;
+            }
+            // power = -(A dx^2 + C dy^2) / 2 - B dx dy and d/dx = -d/d(dx):
+            // the gradients of the centre and of the conic
+            const float gx = G.conA * mdx + G.conB * mdy;
+            const float gy = G.conB * mdx + G.conC * mdy;
+            const float gA = -0.5f * mdxx, gB = -mdxy, gC = -0.5f * mdyy;
 
             // ---- projected centre: x = fx t_x / t_z + cx - 0.5 ----
             const float itz = 1.0f / G.tz;
