@@ -60,6 +60,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 static_assert(BWD_BATCH_MAX % 32 == 0 && FWD_BATCH_MAX % 32 == 0, "batch sizes");
 // Minimum resident blocks requested for the 8-pixels-per-thread backward.
 #ifndef SG_BWD8_MIN_BLOCKS
@@ -87,15 +93,18 @@ constexpr int SUB_W = 8, SUB_H = 4;
 // changes no result). Per band of 4 pixel rows, the ellipse's x-extent over the
 // band is taken where its edges are extreme (the right edge at dy = -m, the
 // left at dy = +m, m = B xmax / C, both clamped into the band) and compared
-// with the tile's two 8-column halves. Padded by 0.05 px for rounding.
+// with the tile's two 8-column halves. Padded by 0.05 px. The square roots and
+// reciprocals are the approximate ones (relative error ~1e-6): the mask only
+// has to cover the pixels where alpha reaches 1/255, and the 1 % growth of the
+// bound already moves the ellipse's edge out by ~0.5 % of its radius.
 __device__ __forceinline__ uint32_t reach_mask(const Rec &rc, float x0, float y0) {
     const float x = rc.a.x, y = rc.a.y, A = rc.a.z, B = rc.a.w, C = rc.b.x, t = rc.b.y;
     if (!(t >= 0.f)) return 0u;                      // o' < 1/255: alpha < 1/255 everywhere
     const float det = A * C - B * B;
     if (!(A > 0.f) || !(C > 0.f) || !(det > 0.f)) return 0xFFu;
-    const float At = A * t, invdet = 1.f / det, invA = 1.f / A;
-    const float ymax = sqrtf(At * invdet);
-    const float m = B * sqrtf(C * t * invdet) / C;
+    const float At = A * t, invdet = rcp_approx(det), invA = rcp_approx(A);
+    const float ymax = sqrt_approx(At * invdet);
+    const float m = B * sqrt_approx(C * t * invdet) * rcp_approx(C);
     if (!isfinite(ymax) || !isfinite(m) || !isfinite(invA)) return 0xFFu;
     constexpr float pad = 0.05f;
     uint32_t mask = 0u;
@@ -105,7 +114,8 @@ __device__ __forceinline__ uint32_t reach_mask(const Rec &rc, float x0, float y0
         const float hi = fminf(y0 + (float)(SUB_H * sy + SUB_H - 1) - y + pad, ymax);
         if (!(lo <= hi)) continue;
         const float dr = fminf(fmaxf(-m, lo), hi), dl = fminf(fmaxf(m, lo), hi);
-        const float sr = sqrtf(fmaxf(0.f, At - det * dr * dr)), sl = sqrtf(fmaxf(0.f, At - det * dl * dl));
+        const float sr = sqrt_approx(fmaxf(0.f, At - det * dr * dr));
+        const float sl = sqrt_approx(fmaxf(0.f, At - det * dl * dl));
         const float xr = x + (sr - B * dr) * invA + pad - x0, xl = x - (sl + B * dl) * invA - pad - x0;
 #pragma unroll
         for (int sx = 0; sx < TILE / SUB_W; ++sx)
@@ -333,6 +343,7 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             float *__restrict__ img, float *__restrict__ T_final, int32_t *__restrict__ last,
             const uint32_t *__restrict__ tile_order, uint32_t *__restrict__ queue, uint32_t n_tiles,
             unsigned long long *__restrict__ evals, const uint64_t *__restrict__ status) {
+    chain_enter();
     __shared__ StagedN<NB> sm;
     __shared__ uint32_t s_item;
     const Batch &b = *bp;
@@ -359,7 +370,7 @@ static void fwd_launch(const Batch *db, uint32_t n_tiles, const uint2 *ranges, c
                        const Rec *rec, float *img, float *T_final, int32_t *last, const BlendShape &sh,
                        unsigned long long *evals, cudaStream_t s) {
     const unsigned grid = PERSIST ? (unsigned)sh.grid : n_tiles;
-    k_blend_fwd<P, MODE, PERSIST, NB><<<grid, BLEND_THREADS / P, 0, s>>>(
+    (void)launch_chain(k_blend_fwd<P, MODE, PERSIST, NB>, dim3(grid), dim3(BLEND_THREADS / P), s,
         db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, evals, sh.status);
 }
 
@@ -631,6 +642,7 @@ k_blend_bwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             const float *__restrict__ d_img, float *__restrict__ dg, uint64_t M,
             const uint32_t *__restrict__ tile_order, uint32_t *__restrict__ queue, uint32_t n_tiles,
             unsigned long long *__restrict__ evals, const uint64_t *__restrict__ status, int nb) {
+    chain_enter();
     constexpr int NT = BLEND_THREADS / P;
     __shared__ StagedB sm;
     __shared__ float4 spx[BLEND_THREADS];   // per pixel slot: upstream gradient and last position
@@ -663,10 +675,10 @@ static void bwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const 
                   uint64_t M, const BlendShape &sh, unsigned long long *evals, cudaStream_t s) {
     const unsigned grid = PERSIST ? (unsigned)sh.grid : n_tiles;
     if (evals)
-        k_blend_bwd<P, true, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
+        (void)launch_chain(k_blend_bwd<P, true, PERSIST>, dim3(grid), dim3(BLEND_THREADS / P), s,
             db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, evals, sh.status, sh.batch);
     else
-        k_blend_bwd<P, false, PERSIST><<<grid, BLEND_THREADS / P, 0, s>>>(
+        (void)launch_chain(k_blend_bwd<P, false, PERSIST>, dim3(grid), dim3(BLEND_THREADS / P), s,
             db, ranges, pval, rec, T_final, last, d_img, dg, M, sh.tile_order, sh.queue, n_tiles, nullptr, sh.status, sh.batch);
 }
 

@@ -205,6 +205,36 @@ __device__ __forceinline__ void tile_reach_row(const TileReach &R, int ty, int x
     c1 = max(c0, min(x1, (int)b + 1));
 }
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch along the render chain. Each kernel of the
+// chain is launched with programmatic stream serialisation, so the GPU may
+// schedule its blocks while the kernel before it drains; its first statement
+// waits until that kernel has completed and its writes are visible, so the
+// chain keeps plain stream order. Right after the wait it lets the next kernel
+// be scheduled in turn. Both instructions are no-ops for a kernel launched
+// without the attribute.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void chain_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chain(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                                Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 // Process-wide count of kernels this library has launched (sg_kernel_launches).
 void count_launches(int n);
 

@@ -233,6 +233,7 @@ static_assert(offsetof(Batch, view) % 8 == 0, "batch header");
 template <int NV, int NS>
 __global__ void __launch_bounds__(256) k_setup(const BatchParam<NV, NS> p, Batch *dst, uint64_t *counters,
                                                ZeroRegions z) {
+    chain_enter();
     const Batch &hb = *reinterpret_cast<const Batch *>(p.head);   // header fields only
     const int n_views = hb.n_views, n_scenes = hb.n_scenes;
     uint32_t *d = reinterpret_cast<uint32_t *>(dst);
@@ -260,7 +261,7 @@ static cudaError_t setup_t(const Batch &b, Batch *dst, uint64_t *counters, const
     std::memcpy(p.head, &b, sizeof(p.head));
     std::memcpy(p.view, b.view, (size_t)b.n_views * sizeof(ViewDesc));
     std::memcpy(p.scene, b.scene, (size_t)b.n_scenes * sizeof(SceneDesc));
-    k_setup<NV, NS><<<1, 256, 0, s>>>(p, dst, counters, z);
+    (void)launch_chain(k_setup<NV, NS>, dim3(1), dim3(256), s, p, dst, counters, z);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(PRE_THREADS, SG_PRE_MIN_BLOCKS)
 k_preprocess(const Batch *__restrict__ bp, Rec *__restrict__ rec, uint32_t *__restrict__ tiles_touched,
              uint2 *__restrict__ rect, uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
              uint8_t *__restrict__ clamp) {
+    chain_enter();
     const Batch &b = *bp;
     const int si = find_block_scene(b, blockIdx.x);
     const SceneDesc &sc = b.scene[si];
@@ -486,10 +488,10 @@ static cudaError_t launch_pre_t(const Batch &hb, const Batch *db, Rec *rec, uint
                                 uint32_t *dkey, uint32_t *dval, uint8_t *clamp, cudaStream_t s) {
     if (hb.scene_blocks == 0) return cudaSuccess;   // one block per 256 scene Gaussians
     if (hb.max_views_per_scene <= 1)
-        k_preprocess<DG, DL, DS, CM, true><<<hb.scene_blocks, PRE_THREADS, 0, s>>>(db, rec, tt, rect, dkey, dval,
+        (void)launch_chain(k_preprocess<DG, DL, DS, CM, true>, dim3(hb.scene_blocks), dim3(PRE_THREADS), s, db, rec, tt, rect, dkey, dval,
                                                                                    clamp);
     else
-        k_preprocess<DG, DL, DS, CM, false><<<hb.scene_blocks, PRE_THREADS, 0, s>>>(db, rec, tt, rect, dkey, dval,
+        (void)launch_chain(k_preprocess<DG, DL, DS, CM, false>, dim3(hb.scene_blocks), dim3(PRE_THREADS), s, db, rec, tt, rect, dkey, dval,
                                                                                     clamp);
     count_launches(1);
     return cudaGetLastError();
@@ -531,6 +533,7 @@ template <int DG, int DL, int DS, int CM>
 __global__ void __launch_bounds__(PRE_THREADS, SG_PRE_BWD_MIN_BLOCKS)
 k_preprocess_bwd(const Batch *__restrict__ bp, const uint32_t *__restrict__ tiles_touched,
                  const uint8_t *__restrict__ clamp, const float *__restrict__ dg, uint64_t M) {
+    chain_enter();
     const Batch &b = *bp;
     const int si = find_block_scene(b, blockIdx.x);
     const SceneDesc &sc = b.scene[si];
@@ -814,7 +817,7 @@ template <int DG, int DL, int DS, int CM = SG_COLOR_SG>
 static cudaError_t launch_bwd_t(const Batch &hb, const Batch *db, const uint32_t *tt, const uint8_t *clamp,
                                 const float *dg, uint64_t M, cudaStream_t s) {
     if (hb.scene_blocks == 0) return cudaSuccess;
-    k_preprocess_bwd<DG, DL, DS, CM><<<hb.scene_blocks, PRE_THREADS, 0, s>>>(db, tt, clamp, dg, M);
+    (void)launch_chain(k_preprocess_bwd<DG, DL, DS, CM>, dim3(hb.scene_blocks), dim3(PRE_THREADS), s, db, tt, clamp, dg, M);
     count_launches(1);
     return cudaGetLastError();
 }

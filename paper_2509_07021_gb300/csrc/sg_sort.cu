@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint32_t *__restri
                                                         const uint64_t *__restrict__ n_dev, uint64_t max_n,
                                                         int bits, bool drop, SortAux *aux,
                                                         uint32_t *__restrict__ flags, uint64_t flag_words) {
+    chain_enter();
     constexpr int NW = RS_THREADS / 32;
     __shared__ uint32_t h[NW][4][RS_RADIX];
     const int passes = radix_passes_dev(bits);
@@ -279,6 +280,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_os_pass(
     uint32_t *__restrict__ vout, const uint64_t *__restrict__ n_dev, uint64_t max_n, int pass, int shift,
     uint32_t mask, bool drop, uint32_t *__restrict__ flags, SortAux *aux, uint2 *__restrict__ ranges,
     uint64_t n_ranges, uint32_t spin_limit, const uint64_t *__restrict__ skip_status) {
+    chain_enter();
     constexpr int NW = RS_THREADS / 32;
     constexpr int PER_WARP = RS_TILE / NW;   // 512 consecutive keys per warp
     __shared__ uint32_t cnt[NW][RS_RADIX];
@@ -424,6 +426,7 @@ uint64_t sort_flag_words(uint64_t max_n, int bits) {
 __global__ void k_os_finish(const SortAux *aux, uint64_t *status, uint64_t *kept_out, uint2 *ranges,
                             uint64_t n_ranges, bool no_pass, const uint64_t *n_dev, uint64_t max_n,
                             uint64_t *status_mirror) {
+    chain_enter();
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && !no_pass) {
         if (status && aux->status) *status = aux->status;
@@ -450,13 +453,13 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
     if (nblocks == 0 || passes == 0) {
         // nothing to sort; ranges still get their final values
         if (ranges) {
-            k_os_finish<<<(unsigned)fgrid, 256, 0, s>>>(reinterpret_cast<SortAux *>(scan_sums), status, nullptr,
+            (void)launch_chain(k_os_finish, dim3((unsigned)fgrid), dim3(256), s, reinterpret_cast<SortAux *>(scan_sums), status, nullptr,
                                                        ranges, n_ranges, passes == 0, n_dev, max_n, status_mirror);
             count_launches(1);
             return cudaGetLastError();
         }
         if (status_mirror) {
-            k_os_finish<<<1, 1, 0, s>>>(reinterpret_cast<SortAux *>(scan_sums), status, nullptr, nullptr, 0, true,
+            (void)launch_chain(k_os_finish, dim3(1), dim3(1), s, reinterpret_cast<SortAux *>(scan_sums), status, nullptr, nullptr, 0, true,
                                         n_dev, max_n, status_mirror);
             count_launches(1);
             return cudaGetLastError();
@@ -474,7 +477,7 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
             if (e != cudaSuccess) return e;
         }
         const unsigned hgrid = nblocks < 4u * 152u ? nblocks : 4u * 152u;
-        k_os_hist<<<hgrid, RS_THREADS, 0, s>>>(k0, n_dev, max_n, bits, drop, aux, hist, pass_words * passes);
+        (void)launch_chain(k_os_hist, dim3(hgrid), dim3(RS_THREADS), s, k0, n_dev, max_n, bits, drop, aux, hist, pass_words * passes);
         count_launches(1);
     }
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
@@ -485,7 +488,7 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
         // with drop, pass 0 leaves SORT_DROP_KEY out and later passes see only the kept keys
         const uint64_t *np = (drop && p > 0) ? &aux->kept : n_dev;
         uint2 *rg = p == passes - 1 ? ranges : nullptr;
-        k_os_pass<<<nblocks, RS_THREADS, 0, s>>>(ki, vi, ko, vo, np, max_n, p, shift, mask, drop && p == 0,
+        (void)launch_chain(k_os_pass, dim3(nblocks), dim3(RS_THREADS), s, ki, vi, ko, vo, np, max_n, p, shift, mask, drop && p == 0,
                                                  hist + pass_words * p, aux, rg, n_ranges, spin_limit,
                                                  skip_status);
         count_launches(1);
@@ -494,7 +497,7 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
         t = vi; vi = vo; vo = t;
     }
     if (status || kept_out || ranges || status_mirror) {
-        k_os_finish<<<(unsigned)fgrid, ranges ? 256 : 1, 0, s>>>(aux, status, kept_out, ranges, n_ranges, false,
+        (void)launch_chain(k_os_finish, dim3((unsigned)fgrid), dim3(ranges ? 256 : 1), s, aux, status, kept_out, ranges, n_ranges, false,
                                                                  n_dev, max_n, status_mirror);
         count_launches(1);
     }
@@ -606,6 +609,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
                                                    SortAux *__restrict__ aux, uint32_t *__restrict__ flags,
                                                    uint64_t flag_words, uint64_t *__restrict__ dflags,
                                                    uint64_t *mirror, uint32_t spin_limit) {
+    chain_enter();
     __shared__ uint32_t s_rinc[256], s_e[256], s_rx[256], s_ry[256], s_base[256], s_tx[256];
     __shared__ TileReach s_R[256];
     __shared__ uint32_t shs[33];
@@ -737,7 +741,7 @@ cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted
                              uint64_t flag_words) {
     // one block at least: it reports the zero total of a call without entries
     const uint64_t grid = std::max<uint64_t>(div_up(M, 256), 1);
-    k_duplicate<<<(unsigned)grid, 256, 0, s>>>(db, M, sorted_ent, tiles_touched, rect, rec, counters, cap, pkey,
+    (void)launch_chain(k_duplicate, dim3((unsigned)grid), dim3(256), s, db, M, sorted_ent, tiles_touched, rect, rec, counters, cap, pkey,
                                                pval, hist_passes, reinterpret_cast<SortAux *>(sort_aux), flags,
                                                flag_words, dup_flags, mirror, sort_wait_polls());
     count_launches(1);
@@ -760,6 +764,7 @@ __device__ __forceinline__ uint32_t len_bucket(const uint2 r) {
 
 __global__ void __launch_bounds__(256) k_tile_bucket_count(const uint2 *__restrict__ ranges, uint32_t n_tiles,
                                                            uint32_t *__restrict__ counts) {
+    chain_enter();
     __shared__ uint32_t h[TB_BUCKETS];
     h[threadIdx.x] = 0u;
     __syncthreads();
@@ -773,6 +778,7 @@ __global__ void __launch_bounds__(256) k_tile_bucket_scatter(const uint2 *__rest
                                                              const uint32_t *__restrict__ counts,
                                                              uint32_t *__restrict__ cursor,
                                                              uint32_t *__restrict__ order) {
+    chain_enter();
     __shared__ uint32_t base[TB_BUCKETS];
     __shared__ uint32_t shs[33];
     // longest lists first: exclusive scan over the buckets in reverse
@@ -794,8 +800,8 @@ cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *o
     if (e != cudaSuccess) return e;
     const uint64_t want = div_up(n_tiles, 256);
     const unsigned grid = (unsigned)(want < 608u ? want : 608u);
-    k_tile_bucket_count<<<grid, 256, 0, s>>>(ranges, n_tiles, counts);
-    k_tile_bucket_scatter<<<grid, 256, 0, s>>>(ranges, n_tiles, counts, cursor, order);
+    (void)launch_chain(k_tile_bucket_count, dim3(grid), dim3(256), s, ranges, n_tiles, counts);
+    (void)launch_chain(k_tile_bucket_scatter, dim3(grid), dim3(256), s, ranges, n_tiles, counts, cursor, order);
     count_launches(2);
     return cudaGetLastError();
 }
