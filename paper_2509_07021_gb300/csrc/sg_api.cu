@@ -584,12 +584,12 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
     if (st != SG_OK) return st;
     shape.status = reinterpret_cast<const uint64_t *>(w + L.counters) + CNT_STATUS;   // the forward's
     {
-        StageTimer t(ST_SETUP, stream);
-        SG_CUDA(launch_setup(b, db, counters, stream), "setup");
-    }
-    {
+        // the setup kernel also clears the 2D-gradient accumulators
         StageTimer t(ST_BWD_CLEAR, stream);
-        if (M > 0) SG_CUDA(cudaMemsetAsync(dg, 0, 9 * M * sizeof(float), stream), "clear 2D gradients");
+        ZeroRegions z;
+        z.ptr[0] = reinterpret_cast<uint32_t *>(dg);
+        z.words[0] = 9 * M;
+        SG_CUDA(launch_setup(b, db, counters, stream, z), "setup");
     }
     if (shape.persistent) {
         StageTimer t(ST_BWD_CLEAR, stream);
@@ -1090,9 +1090,11 @@ extern "C" int sg_render_backward_noalloc(const sg_scene *scene, const sg_camera
     shape.pixels_per_thread = tuning().bwd_pixels_per_thread;
     shape.batch = tuning().bwd_batch ? tuning().bwd_batch : kDefaultBatch;
     shape.status = reinterpret_cast<const uint64_t *>(w + L.counters) + CNT_STATUS;   // the forward's
-    // the setup kernel rewrites the table and counters; the accumulators are cleared
-    SG_CUDA(launch_setup(b, db, counters, stream), "setup");
-    if (M > 0) SG_CUDA(cudaMemsetAsync(dg, 0, 9 * M * sizeof(float), stream), "clear 2D gradients");
+    // the setup kernel rewrites the table and counters and clears the accumulators
+    ZeroRegions z;
+    z.ptr[0] = reinterpret_cast<uint32_t *>(dg);
+    z.words[0] = 9 * M;
+    SG_CUDA(launch_setup(b, db, counters, stream, z), "setup");
     SG_CUDA(launch_blend_backward(db, b.n_tiles, ranges, pv_final, rec, T_final, last, d_img, dg, M, shape,
                                   nullptr, stream),
             "blend backward");

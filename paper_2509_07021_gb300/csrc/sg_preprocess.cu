@@ -228,12 +228,30 @@ struct BatchParam {
 static_assert(offsetof(Batch, view) % 8 == 0, "batch header");
 
 // Writes the table into the workspace, zeroes the counters and the regions the
-// caller names (e.g. tile ranges, sort scratch), and seeds the entry and tile
-// counts. One block.
+// caller names (e.g. tile ranges, sort scratch, the backward's accumulators),
+// and seeds the entry and tile counts. Block 0 writes the table and counters;
+// every block zeroes its share of the regions (16-byte stores where a region
+// starts on a 16-byte boundary).
 template <int NV, int NS>
 __global__ void __launch_bounds__(256) k_setup(const BatchParam<NV, NS> p, Batch *dst, uint64_t *counters,
                                                ZeroRegions z) {
     chain_enter();
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < ZeroRegions::N; ++r) {
+        uint32_t *ptr = z.ptr[r];
+        const uint64_t words = z.words[r];
+        const uint32_t ev = z.even[r];
+        uint64_t i0 = 0;
+        if ((reinterpret_cast<uintptr_t>(ptr) & 15u) == 0u) {
+            const uint64_t n4 = words / 4;
+            const uint4 v = make_uint4(ev, 0u, ev, 0u);   // words 4i, 4i + 2 are even
+            for (uint64_t i = tid; i < n4; i += nth) reinterpret_cast<uint4 *>(ptr)[i] = v;
+            i0 = 4 * n4;
+        }
+        for (uint64_t i = i0 + tid; i < words; i += nth) ptr[i] = (i & 1) ? 0u : ev;
+    }
+    if (blockIdx.x != 0) return;
     const Batch &hb = *reinterpret_cast<const Batch *>(p.head);   // header fields only
     const int n_views = hb.n_views, n_scenes = hb.n_scenes;
     uint32_t *d = reinterpret_cast<uint32_t *>(dst);
@@ -245,8 +263,6 @@ __global__ void __launch_bounds__(256) k_setup(const BatchParam<NV, NS> p, Batch
     const uint32_t *ps = reinterpret_cast<const uint32_t *>(p.scene);
     uint32_t *ds = reinterpret_cast<uint32_t *>(&dst->scene[0]);
     for (int i = threadIdx.x; i < (int)(n_scenes * sizeof(SceneDesc) / 4); i += blockDim.x) ds[i] = ps[i];
-    for (int r = 0; r < ZeroRegions::N; ++r)
-        for (uint64_t i = threadIdx.x; i < z.words[r]; i += blockDim.x) z.ptr[r][i] = (i & 1) ? 0u : z.even[r];
     if (threadIdx.x < CNT_N) counters[threadIdx.x] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -261,7 +277,11 @@ static cudaError_t setup_t(const Batch &b, Batch *dst, uint64_t *counters, const
     std::memcpy(p.head, &b, sizeof(p.head));
     std::memcpy(p.view, b.view, (size_t)b.n_views * sizeof(ViewDesc));
     std::memcpy(p.scene, b.scene, (size_t)b.n_scenes * sizeof(SceneDesc));
-    (void)launch_chain(k_setup<NV, NS>, dim3(1), dim3(256), s, p, dst, counters, z);
+    // about eight 16-byte stores per thread, up to four blocks per SM
+    uint64_t words = 0;
+    for (int r = 0; r < ZeroRegions::N; ++r) words += z.words[r];
+    const uint64_t blocks = std::min<uint64_t>(std::max<uint64_t>(div_up(words, 256 * 32), 1), 4 * 152);
+    (void)launch_chain(k_setup<NV, NS>, dim3((unsigned)blocks), dim3(256), s, p, dst, counters, z);
     count_launches(1);
     return cudaGetLastError();
 }
