@@ -257,7 +257,8 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     L.dval1 = take(M * 4);
     L.dup_flags = take(div_up(M, 256) * 8 + 8);   // the duplicate blocks' look-back words
     L.ranges = take(T * 8);
-    L.order = take(T * 4);
+    L.order = take(T * 4);   // tile order of the persistent blends (forward and backward)
+    L.order_scratch = take(TILE_ORDER_WORDS * 4);
     L.fixed_end = o;
     // pair-capacity dependent tail; the backward only reads pval_final
     L.pval_final = take(cap * 4);
@@ -289,22 +290,19 @@ uint64_t capacity_for(const Batch &b, size_t ws_bytes) {
     return lo;
 }
 
-// Backward scratch: batch table, counters, [9][M] 2D gradients, then the
-// persistent blend's tile order (4 x T) and its radix histograms.
+// Backward scratch: batch table, counters and the [9][M] 2D gradients (the
+// persistent backward takes its tile order from the forward's workspace).
 struct BwdLayout {
-    size_t batch, counters, dg, order, sums, total;
+    size_t batch, counters, dg, total;
 };
 
 BwdLayout bwd_layout(const Batch &b) {
     BwdLayout L{};
-    const uint64_t T = b.n_tiles;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
     L.batch = take(sizeof(Batch));
     L.counters = take(CNT_N * sizeof(uint64_t));
     L.dg = take(9 * b.n_entries * sizeof(float));
-    L.order = take(T * 4);
-    L.sums = take(2 * 256 * 4);   // tile-order bucket counters
     L.total = o;
     return L;
 }
@@ -441,6 +439,8 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         z.words[2] = SORT_AUX_BYTES / 4;
         z.ptr[3] = reinterpret_cast<uint32_t *>(dup_flags);
         z.words[3] = 2 * div_up(M, 256);
+        z.ptr[4] = reinterpret_cast<uint32_t *>(w + L.order_scratch);
+        z.words[4] = TILE_ORDER_WORDS;
         StageTimer t(ST_SETUP, stream);
         SG_CUDA(launch_setup(b, db, counters, stream, z), "setup");
     }
@@ -486,7 +486,8 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         // plain form: the sorts' merged status also goes to the host word next to the pair count
         SG_CUDA(launch_radix_sort(k0, v0, k1, v1, counters + CNT_WRITTEN, K, L.tile_bits, hist, aux_tile, stream,
                                   counters + CNT_STATUS, nullptr, true, ranges, L.n_tiles, true,
-                                  rb ? rb->dev_ptr + 1 : nullptr, counters + CNT_STATUS),
+                                  rb ? rb->dev_ptr + 1 : nullptr, counters + CNT_STATUS,
+                                  reinterpret_cast<uint32_t *>(w + L.order_scratch)),
                 "tile sort");
     }
     if (sync) SG_CUDA(cudaEventRecord(rb->ev, stream), "read pairs");
@@ -504,10 +505,11 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
             if (scenes[s].n > 0)
                 SG_CUDA(cudaMemsetAsync(importance[s], 0, (size_t)scenes[s].n * sizeof(float), stream),
                         "clear importance");
-    if (shape.persistent) {
+    {
+        // built for every forward: the persistent backward walks tiles in this order too
         StageTimer t(ST_RANGES, stream);
         SG_CUDA(launch_tile_order(ranges, b.n_tiles, reinterpret_cast<uint32_t *>(w + L.order),
-                                  reinterpret_cast<uint32_t *>(sums), stream),
+                                  reinterpret_cast<uint32_t *>(w + L.order_scratch), stream),
                 "tile order");
     }
     {
@@ -579,7 +581,8 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
     unsigned long long *evals =
         counting ? reinterpret_cast<unsigned long long *>(counters + CNT_EVALS) : nullptr;
     BlendShape shape{};
-    st = blend_shape(true, reinterpret_cast<uint32_t *>(bw + BL.order),
+    // the forward's tile order (longest lists first)
+    st = blend_shape(true, reinterpret_cast<const uint32_t *>(w + L.order),
                      reinterpret_cast<uint32_t *>(counters + CNT_QUEUE), shape);
     if (st != SG_OK) return st;
     shape.status = reinterpret_cast<const uint64_t *>(w + L.counters) + CNT_STATUS;   // the forward's
@@ -590,12 +593,6 @@ int backward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, c
         z.ptr[0] = reinterpret_cast<uint32_t *>(dg);
         z.words[0] = 9 * M;
         SG_CUDA(launch_setup(b, db, counters, stream, z), "setup");
-    }
-    if (shape.persistent) {
-        StageTimer t(ST_BWD_CLEAR, stream);
-        SG_CUDA(launch_tile_order(ranges, b.n_tiles, reinterpret_cast<uint32_t *>(bw + BL.order),
-                                  reinterpret_cast<uint32_t *>(bw + BL.sums), stream),
-                "tile order");
     }
     {
         StageTimer t(ST_BLEND_BWD, stream);

@@ -95,7 +95,7 @@ constexpr int SCAN_TILE = 4096;
 // forward and the backward of one call).
 struct WsLayout {
     size_t batch, counters, rec, tiles_touched, rect, clamp, dkey0, dval0, dkey1, dval1,
-        dup_flags, ranges, order, scan_sums, hist, aux_tile, fixed_end;
+        dup_flags, ranges, order, order_scratch, scan_sums, hist, aux_tile, fixed_end;
     size_t pval_final, pkey_final, pval_tmp, pkey_tmp, total;
     uint64_t M, n_tiles, cap;
     uint32_t hist_blocks;     // radix blocks of the larger sort
@@ -243,10 +243,10 @@ void count_launches(int n);
 // Regions the setup kernel fills: word i of region r gets even[r] if i is
 // even, else 0 (even[r] = 0: plain zeroing).
 struct ZeroRegions {
-    static constexpr int N = 4;
-    uint32_t *ptr[N] = {nullptr, nullptr, nullptr, nullptr};
-    uint64_t words[N] = {0, 0, 0, 0};
-    uint32_t even[N] = {0, 0, 0, 0};
+    static constexpr int N = 5;
+    uint32_t *ptr[N] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint64_t words[N] = {0, 0, 0, 0, 0};
+    uint32_t even[N] = {0, 0, 0, 0, 0};
 };
 cudaError_t launch_setup(const Batch &b, Batch *dst, uint64_t *counters, cudaStream_t s,
                          const ZeroRegions &z = ZeroRegions());
@@ -296,7 +296,7 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
                               uint64_t *aux, cudaStream_t s, uint64_t *status = nullptr,
                               uint64_t *kept_out = nullptr, bool aux_zeroed = false, uint2 *ranges = nullptr,
                               uint64_t n_ranges = 0, bool hist_ready = false, uint64_t *status_mirror = nullptr,
-                              const uint64_t *skip_status = nullptr);
+                              const uint64_t *skip_status = nullptr, uint32_t *order_counts = nullptr);
 int radix_passes(int bits);
 // Bound on a sort block's polls of an unpublished predecessor before it gives
 // up and records SG_ERR_TIMEOUT (0: the default, 2^20).
@@ -319,8 +319,10 @@ cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted
                              uint64_t *counters, uint64_t cap, uint32_t *pkey, uint32_t *pval,
                              uint64_t *dup_flags, uint64_t *mirror, cudaStream_t s, int hist_passes = 0,
                              uint64_t *sort_aux = nullptr, uint32_t *flags = nullptr, uint64_t flag_words = 0);
-// Tiles by descending list length (256 length buckets) into order[n_tiles];
-// scratch: 512 words.
+// Tiles by descending list length (256 length buckets) into order[n_tiles].
+// scratch: TILE_ORDER_WORDS zeroed words whose first 256 already hold the
+// bucket counts (launch_radix_sort's order_counts, filled by its finish kernel).
+constexpr int TILE_ORDER_WORDS = 512;
 cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *scratch,
                               cudaStream_t s);
 

@@ -419,48 +419,78 @@ uint64_t sort_flag_words(uint64_t max_n, int bits) {
     return div_up(max_n, RS_TILE) * RS_RADIX * (uint64_t)radix_passes(bits);
 }
 
+// Buckets by list length on a log scale with 8 buckets per octave (exponent and
+// the 3 bits below the leading one), longest bucket first; inside a bucket the
+// order is whatever the atomics give (it only steers scheduling).
+constexpr int TB_BUCKETS = 256;
+__device__ __forceinline__ uint32_t len_bucket(const uint2 r) {
+    const uint32_t len = (r.y - r.x) | 1u;
+    const uint32_t e = 31u - (uint32_t)__clz(len);              // 0..31
+    const uint32_t m = e >= 3u ? (len >> (e - 3u)) & 7u : (len << (3u - e)) & 7u;
+    return e * 8u + m;                                           // 0..255
+}
+
 // Status and kept count (one thread); ids that got no key get the range (0, 0).
 // no_pass: the keys had no bits, so no pass ran and every key is id 0.
 // status_mirror (nullable, host memory mapped into the device): receives the
 // status word after this sort's own status is merged in.
+// bucket_counts (nullable, with ranges; 256-thread blocks): adds every tile to
+// its list-length bucket (len_bucket), the counts of the persistent blends'
+// tile order.
 __global__ void k_os_finish(const SortAux *aux, uint64_t *status, uint64_t *kept_out, uint2 *ranges,
                             uint64_t n_ranges, bool no_pass, const uint64_t *n_dev, uint64_t max_n,
-                            uint64_t *status_mirror) {
+                            uint64_t *status_mirror, uint32_t *bucket_counts) {
     chain_enter();
+    __shared__ uint32_t h[TB_BUCKETS];
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && !no_pass) {
         if (status && aux->status) *status = aux->status;
         if (kept_out) *kept_out = aux->kept;
     }
     if (i == 0 && status_mirror) *status_mirror = status ? *status : 0u;
-    if (!ranges || i >= n_ranges) return;
-    if (no_pass) {
-        const uint64_t nd = *n_dev, n = nd <= max_n ? nd : 0;   // none when over capacity
-        ranges[i] = (i == 0 && n > 0) ? make_uint2(0u, (uint32_t)n) : make_uint2(0u, 0u);
-    } else if (ranges[i].x == RANGE_EMPTY) {
-        ranges[i] = make_uint2(0u, 0u);
+    if (!ranges) return;   // uniform
+    uint2 rg = make_uint2(0u, 0u);
+    if (i < n_ranges) {
+        if (no_pass) {
+            const uint64_t nd = *n_dev, n = nd <= max_n ? nd : 0;   // none when over capacity
+            rg = (i == 0 && n > 0) ? make_uint2(0u, (uint32_t)n) : make_uint2(0u, 0u);
+            ranges[i] = rg;
+        } else {
+            rg = ranges[i];
+            if (rg.x == RANGE_EMPTY) {
+                rg = make_uint2(0u, 0u);
+                ranges[i] = rg;
+            }
+        }
     }
+    if (!bucket_counts) return;   // uniform
+    h[threadIdx.x] = 0u;
+    __syncthreads();
+    if (i < n_ranges) atomicAdd(&h[len_bucket(rg)], 1u);
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&bucket_counts[threadIdx.x], h[threadIdx.x]);
 }
 
 cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint64_t *n_dev, uint64_t max_n, int bits, uint32_t *hist,
                               uint64_t *scan_sums, cudaStream_t s, uint64_t *status, uint64_t *kept_out,
                               bool aux_zeroed, uint2 *ranges, uint64_t n_ranges, bool hist_ready,
-                              uint64_t *status_mirror, const uint64_t *skip_status) {
+                              uint64_t *status_mirror, const uint64_t *skip_status, uint32_t *order_counts) {
     const uint32_t nblocks = (uint32_t)div_up(max_n, RS_TILE);
     const int passes = radix_passes(bits);
     const uint64_t fgrid = ranges ? std::max<uint64_t>(div_up(n_ranges, 256), 1) : 1;
     if (nblocks == 0 || passes == 0) {
         // nothing to sort; ranges still get their final values
         if (ranges) {
-            (void)launch_chain(k_os_finish, dim3((unsigned)fgrid), dim3(256), s, reinterpret_cast<SortAux *>(scan_sums), status, nullptr,
-                                                       ranges, n_ranges, passes == 0, n_dev, max_n, status_mirror);
+            (void)launch_chain(k_os_finish, dim3((unsigned)fgrid), dim3(256), s, reinterpret_cast<SortAux *>(scan_sums),
+                               status, nullptr, ranges, n_ranges, passes == 0, n_dev, max_n, status_mirror,
+                               order_counts);
             count_launches(1);
             return cudaGetLastError();
         }
         if (status_mirror) {
-            (void)launch_chain(k_os_finish, dim3(1), dim3(1), s, reinterpret_cast<SortAux *>(scan_sums), status, nullptr, nullptr, 0, true,
-                                        n_dev, max_n, status_mirror);
+            (void)launch_chain(k_os_finish, dim3(1), dim3(1), s, reinterpret_cast<SortAux *>(scan_sums), status,
+                               nullptr, nullptr, 0, true, n_dev, max_n, status_mirror, nullptr);
             count_launches(1);
             return cudaGetLastError();
         }
@@ -498,7 +528,7 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
     }
     if (status || kept_out || ranges || status_mirror) {
         (void)launch_chain(k_os_finish, dim3((unsigned)fgrid), dim3(ranges ? 256 : 1), s, aux, status, kept_out, ranges, n_ranges, false,
-                                                                 n_dev, max_n, status_mirror);
+                                                                 n_dev, max_n, status_mirror, ranges ? order_counts : nullptr);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -751,29 +781,6 @@ cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted
 // ---------------------------------------------------------------------------
 // work order of the persistent blend: tiles by descending list length
 // ---------------------------------------------------------------------------
-// Buckets by list length on a log scale with 8 buckets per octave (exponent and
-// the 3 bits below the leading one), longest bucket first; inside a bucket the
-// order is whatever the atomics give (it only steers scheduling).
-constexpr int TB_BUCKETS = 256;
-__device__ __forceinline__ uint32_t len_bucket(const uint2 r) {
-    const uint32_t len = (r.y - r.x) | 1u;
-    const uint32_t e = 31u - (uint32_t)__clz(len);              // 0..31
-    const uint32_t m = e >= 3u ? (len >> (e - 3u)) & 7u : (len << (3u - e)) & 7u;
-    return e * 8u + m;                                           // 0..255
-}
-
-__global__ void __launch_bounds__(256) k_tile_bucket_count(const uint2 *__restrict__ ranges, uint32_t n_tiles,
-                                                           uint32_t *__restrict__ counts) {
-    chain_enter();
-    __shared__ uint32_t h[TB_BUCKETS];
-    h[threadIdx.x] = 0u;
-    __syncthreads();
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
-        atomicAdd(&h[len_bucket(ranges[t])], 1u);
-    __syncthreads();
-    if (h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
-}
-
 __global__ void __launch_bounds__(256) k_tile_bucket_scatter(const uint2 *__restrict__ ranges, uint32_t n_tiles,
                                                              const uint32_t *__restrict__ counts,
                                                              uint32_t *__restrict__ cursor,
@@ -794,15 +801,13 @@ __global__ void __launch_bounds__(256) k_tile_bucket_scatter(const uint2 *__rest
 
 cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *scratch,
                               cudaStream_t s) {
+    static_assert(TILE_ORDER_WORDS == 2 * TB_BUCKETS, "tile order scratch");
     if (n_tiles == 0) return cudaSuccess;
     uint32_t *counts = scratch, *cursor = scratch + TB_BUCKETS;
-    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * TB_BUCKETS * sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
     const uint64_t want = div_up(n_tiles, 256);
     const unsigned grid = (unsigned)(want < 608u ? want : 608u);
-    (void)launch_chain(k_tile_bucket_count, dim3(grid), dim3(256), s, ranges, n_tiles, counts);
     (void)launch_chain(k_tile_bucket_scatter, dim3(grid), dim3(256), s, ranges, n_tiles, counts, cursor, order);
-    count_launches(2);
+    count_launches(1);
     return cudaGetLastError();
 }
 
