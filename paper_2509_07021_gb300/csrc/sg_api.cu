@@ -101,8 +101,9 @@ struct StageTimer {
     }
 };
 
-// Process-wide kernel shape choices (sg_set_tuning); defaults from measurement.
-constexpr sg_tuning kDefaultTuning = {2, 8, 0, 1, 0, 0, 0, {0}};
+// Process-wide kernel shape choices (sg_set_tuning); defaults from measurement
+// (1M Gaussians at 1920x1080: both blends persistent, 4 and 8 pixels per thread).
+constexpr sg_tuning kDefaultTuning = {4, 8, 1, 1, 0, 0, 0, {0}};
 constexpr int kDefaultBatch = 64;
 sg_tuning &tuning() {
     static sg_tuning t = kDefaultTuning;

@@ -224,7 +224,7 @@ def test_tuning_rejects_bad_shapes():
     sgsplat.sg_set_tuning()
     t = sgsplat.sg_get_tuning()
     assert (t["fwd_pixels_per_thread"], t["bwd_pixels_per_thread"], t["fwd_persistent"],
-            t["bwd_persistent"]) == (2, 8, 0, 1)
+            t["bwd_persistent"]) == (4, 8, 1, 1)
 
 
 def test_capacity_error_and_retry():
