@@ -708,9 +708,15 @@ def run_forms(args, scene, cams, d_img, flush, steps):
         gen_t = torch.Generator(device="cuda").manual_seed(synth.SEED_BASE + 2)
         targets = torch.rand(br.img.shape, device="cuda", generator=gen_t)
         lg = render.l1_loss_grad(br, targets)
+        # this batch's own shapes and batch sizes (the plain loop below keeps the
+        # single-view workload's)
+        main_tuning = sgsplat.sg_get_tuning()
+        tuned_b = br.autotune(lg) if not args.no_autotune else None
+        batch_tuning = sgsplat.sg_get_tuning()
         br.capture(lg)
         ms_b = _timed(br.replay, max(3, steps // 2), 2, flush)
         n_pairs, status = br.status()
+        sgsplat.sg_set_tuning(**main_tuning)
         P = int(br.offsets[-1])
         # the same work through the plain single-view renderer, view by view
         plain_grads = [render.alloc_grads(d) for d in dss]
@@ -730,7 +736,8 @@ def run_forms(args, scene, cams, d_img, flush, steps):
                        "ms_per_launch": ms_b, "ms_per_view": ms_b / len(all_cams),
                        "mpixel_s": P / ms_b / 1e3, "plain_loop_ms": ms_p,
                        "speedup_vs_plain_loop": ms_p / ms_b,
-                       "tuning": sgsplat.sg_get_tuning()}
+                       "tuning": batch_tuning, "plain_loop_tuning": sgsplat.sg_get_tuning(),
+                       "autotune_ms": tuned_b and tuned_b.get("ms")}
         del br, dss, plain_grads, targets
         torch.cuda.empty_cache()
     return forms

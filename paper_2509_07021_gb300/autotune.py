@@ -54,6 +54,55 @@ def _store(data):
         pass
 
 
+def search(measure, candidates=CANDIDATES, persistent=(0, 1)):
+    """The search both tuners run. measure(**tuning) sets a tuning, runs the
+    workload and returns {"blend_fwd": ms, "blend_bwd": ms}. Every shape
+    (pixels per thread x persistent) first, the forward and the backward picked
+    independently; then the batch sizes at those shapes. Installs the choice
+    and returns it with the timings."""
+    timings = {}
+    for p, q in [(p, q) for q in persistent for p in candidates]:
+        timings[(p, q)] = measure(fwd_pixels_per_thread=p, bwd_pixels_per_thread=p, fwd_persistent=q,
+                                  bwd_persistent=q, fwd_batch=0, bwd_batch=0)
+    best_f = min(timings, key=lambda k: timings[k]["blend_fwd"])
+    best_b = min(timings, key=lambda k: timings[k]["blend_bwd"])
+    batch_ms = {}
+    for i in range(max(len(FWD_BATCHES), len(BWD_BATCHES))):
+        fb = FWD_BATCHES[min(i, len(FWD_BATCHES) - 1)]
+        bb = BWD_BATCHES[min(i, len(BWD_BATCHES) - 1)]
+        batch_ms[(fb, bb)] = measure(fwd_pixels_per_thread=best_f[0], bwd_pixels_per_thread=best_b[0],
+                                     fwd_persistent=best_f[1], bwd_persistent=best_b[1], fwd_batch=fb,
+                                     bwd_batch=bb)
+    fwd_batch = min(batch_ms, key=lambda k: batch_ms[k]["blend_fwd"])[0]
+    bwd_batch = min(batch_ms, key=lambda k: batch_ms[k]["blend_bwd"])[1]
+    sgsplat.sg_set_tuning(best_f[0], best_b[0], best_f[1], best_b[1], fwd_batch=fwd_batch, bwd_batch=bwd_batch)
+    return {"fwd_pixels_per_thread": best_f[0], "bwd_pixels_per_thread": best_b[0],
+            "fwd_persistent": best_f[1], "bwd_persistent": best_b[1],
+            "fwd_batch": fwd_batch, "bwd_batch": bwd_batch,
+            "ms": {f"p{k[0]}{'_persistent' if k[1] else ''}": v for k, v in timings.items()},
+            "batch_ms": {f"fwd{k[0]}_bwd{k[1]}": v for k, v in batch_ms.items()}}
+
+
+def stage_measure(run, reps):
+    """A measure() for search: run() is one forward + backward of the workload;
+    timed with the library's stage events over `reps` runs after a warm-up."""
+    def measure(**tuning):
+        sgsplat.sg_set_tuning(**tuning)
+        run()                                          # warm-up for this choice
+        torch.cuda.synchronize()
+        sgsplat.sg_profile_enable(sgsplat.SG_PROFILE_EVENTS)
+        sgsplat.sg_profile_read(reset=True)
+        for _ in range(reps):
+            run()
+        torch.cuda.synchronize()
+        st = sgsplat.sg_profile_read(reset=True)["stages"]
+        sgsplat.sg_profile_enable(0)
+        # every forward builds the tile order (tile_ranges) whatever the shapes, so
+        # the blend stages alone tell the shapes apart
+        return {"blend_fwd": st["blend_fwd"]["ms"] / reps, "blend_bwd": st["blend_bwd"]["ms"] / reps}
+    return measure
+
+
 def tune(ds, cams, d_img, reps=3, use_cache=True, candidates=CANDIDATES, persistent=(0, 1)):
     """Picks and sets the fastest blend shape (pixels per thread, one block per
     tile or persistent) for the forward and the backward independently on
@@ -69,47 +118,12 @@ def tune(ds, cams, d_img, reps=3, use_cache=True, candidates=CANDIDATES, persist
     grads = render.alloc_grads(ds)
     prev = sgsplat.sg_get_tuning()
 
-    def measure(**tuning):
-        sgsplat.sg_set_tuning(**tuning)
-        out = render.render_forward(ds, cams)          # warm-up for this choice
+    def run():
+        out = render.render_forward(ds, cams)
         render.render_backward(ds, cams, out, d_img, grads)
-        torch.cuda.synchronize()
-        sgsplat.sg_profile_enable(sgsplat.SG_PROFILE_EVENTS)
-        sgsplat.sg_profile_read(reset=True)
-        for _ in range(reps):
-            out = render.render_forward(ds, cams)
-            render.render_backward(ds, cams, out, d_img, grads)
-        torch.cuda.synchronize()
-        st = sgsplat.sg_profile_read(reset=True)["stages"]
-        sgsplat.sg_profile_enable(0)
-        q_f, q_b = tuning["fwd_persistent"], tuning["bwd_persistent"]
-        # the persistent forms also pay for their tile order (in tile_ranges / bwd_clear)
-        return {"blend_fwd": (st["blend_fwd"]["ms"] + (st["tile_ranges"]["ms"] if q_f else 0)) / reps,
-                "blend_bwd": (st["blend_bwd"]["ms"] + (st["bwd_clear"]["ms"] if q_b else 0)) / reps}
 
-    timings = {}
-    for p, q in [(p, q) for q in persistent for p in candidates]:
-        timings[(p, q)] = measure(fwd_pixels_per_thread=p, bwd_pixels_per_thread=p, fwd_persistent=q,
-                                  bwd_persistent=q, fwd_batch=0, bwd_batch=0)
-    best_f = min(timings, key=lambda k: timings[k]["blend_fwd"])
-    best_b = min(timings, key=lambda k: timings[k]["blend_bwd"])
-    # then the batch sizes for the chosen shapes
-    batch_ms = {}
-    for i in range(max(len(FWD_BATCHES), len(BWD_BATCHES))):
-        fb = FWD_BATCHES[min(i, len(FWD_BATCHES) - 1)]
-        bb = BWD_BATCHES[min(i, len(BWD_BATCHES) - 1)]
-        batch_ms[(fb, bb)] = measure(fwd_pixels_per_thread=best_f[0], bwd_pixels_per_thread=best_b[0],
-                                     fwd_persistent=best_f[1], bwd_persistent=best_b[1], fwd_batch=fb,
-                                     bwd_batch=bb)
-    fwd_batch = min(batch_ms, key=lambda k: batch_ms[k]["blend_fwd"])[0]
-    bwd_batch = min(batch_ms, key=lambda k: batch_ms[k]["blend_bwd"])[1]
-    sgsplat.sg_set_tuning(best_f[0], best_b[0], best_f[1], best_b[1], fwd_batch=fwd_batch, bwd_batch=bwd_batch)
-    res = {"fwd_pixels_per_thread": best_f[0], "bwd_pixels_per_thread": best_b[0],
-           "fwd_persistent": best_f[1], "bwd_persistent": best_b[1],
-           "fwd_batch": fwd_batch, "bwd_batch": bwd_batch,
-           "ms": {f"p{k[0]}{'_persistent' if k[1] else ''}": v for k, v in timings.items()},
-           "batch_ms": {f"fwd{k[0]}_bwd{k[1]}": v for k, v in batch_ms.items()},
-           "previous": prev}
+    res = search(stage_measure(run, reps), candidates, persistent)
+    res["previous"] = prev
     if use_cache:
         cache[key] = res
         _store(cache)

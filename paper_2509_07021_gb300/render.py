@@ -358,6 +358,14 @@ class BatchedRenderer:
             loss_grad(self.img, self.d_img)
         self.backward()
 
+    def autotune(self, loss_grad=None, reps=2):
+        """Picks the blend shapes and batch sizes for this batch: every shape,
+        then the batch sizes, each timed over eager steps with the library's
+        stage events (the search of autotune.tune). Installs the choice (process
+        wide) and returns it with the timings; capture afterwards."""
+        from . import autotune
+        return autotune.search(autotune.stage_measure(lambda: self.step(loss_grad), reps))
+
     def capture(self, loss_grad=None, warmup=2):
         """Captures step(loss_grad) in a CUDA graph; replay() runs it."""
         s = torch.cuda.Stream(device=self.device)

@@ -59,3 +59,37 @@ def test_autotune_rejects_bad_reps():
     d = torch.zeros_like(out.img)
     with pytest.raises(sgsplat.SGError):
         sgsplat.sg_autotune(ds, cams, out.ws, out.img, out.T_final, out.last, d, bwd, grads, reps=0)
+
+
+def test_batched_autotune_picks_valid_shapes_and_keeps_results():
+    """BatchedRenderer.autotune runs the same search over the batch (every shape,
+    then the batch sizes), installs the fastest choice, and the captured step
+    reproduces the images of the default shapes."""
+    sgsplat.lib()
+    old = sgsplat.sg_get_tuning()
+    try:
+        rng = np.random.default_rng(78)
+        scenes = [DeviceScene.from_host(synth.make_scene(rng, n, lobes=synth.LOBE_MIX, means="cube",
+                                                         cube_side=1.4, masks="uniform")) for n in (2000, 700)]
+        cams = [synth.make_camera(96, 64, 80.0), synth.make_camera(48, 80, 60.0), synth.make_camera(64, 64, 70.0)]
+        view_scene = [0, 1, 1]
+        sgsplat.sg_set_tuning()
+        br = render.BatchedRenderer(scenes, cams, view_scene)
+        br.forward()
+        ref = br.img.clone()
+        got = br.autotune(reps=1)
+        t = sgsplat.sg_get_tuning()
+        for k in ("fwd_pixels_per_thread", "bwd_pixels_per_thread", "fwd_persistent", "bwd_persistent",
+                  "fwd_batch", "bwd_batch"):
+            assert t[k] == got[k]
+        assert t["fwd_batch"] in (32, 64, 128) and t["bwd_batch"] in (32, 64)
+        assert len(got["ms"]) == 8 and len(got["batch_ms"]) == 3
+        fastest_b = min(v["blend_bwd"] for v in got["ms"].values())
+        name = f"p{t['bwd_pixels_per_thread']}" + ("_persistent" if t["bwd_persistent"] else "")
+        assert got["ms"][name]["blend_bwd"] == fastest_b
+        br.capture()
+        br.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(br.img, ref)
+    finally:
+        sgsplat.sg_set_tuning(**old)
