@@ -564,7 +564,7 @@ def run_ours(args, world, rank, local):
             "kernel_rooflines": {"counts": counts, "hbm_peak_gbs": hbm_peak, "stages": kernel_roofs},
             "pair_evals": evals}
     if world == 1 and not args.no_forms:
-        forms = run_forms(args, scene, cams, d_img, flush, max(3, args.steps // 2))
+        forms = run_forms(args, scene, cams, d_img, flush, max(3, args.steps // 2), hbm_peak)
         forms.pop("_images")
         if not args.no_cpu_baseline:
             errs = gpu_errors_vs_oracle(scene, cam, d_img_np)
@@ -599,6 +599,59 @@ def _timed(fn, steps, warmup, flush):
     return statistics.median(ms)
 
 
+def next_rows(scene, cams, flush, steps, hbm_gbs):
+    """Time and roofline of the rows built after the render path, on the bench
+    scene: the importance score fused into the forward (against the plain
+    forward), the ADMM steps of Alg. 1 over the N opacities and the L lobes
+    (kappa = half of them), and the post-processing (plan + apply). The HBM
+    fraction counts each array read and written once (the top-kappa selections
+    also sort their scores: that traffic is not counted)."""
+    import torch
+    from paper_2509_07021_gb300 import render, sgsplat
+    from paper_2509_07021_gb300.sgsplat import DeviceScene
+    out = {}
+    ds = DeviceScene.from_host(scene)
+    N, L = ds.n, int(ds.sharp.numel())
+    imp = torch.zeros(N, device="cuda")
+    ms_plain = _timed(lambda: render.render_forward(ds, cams), steps, 2, flush)
+    ms_imp = _timed(lambda: render.render_forward(ds, cams, importance=imp), steps, 2, flush)
+    out["importance_forward"] = {"ms": ms_imp, "plain_forward_ms": ms_plain,
+                                 "overhead": ms_imp / ms_plain - 1.0,
+                                 "nonzero": int((imp > 0).sum().item()), "gaussians": N}
+
+    def hbm(name, ms, nbytes, n, extra=None):
+        a = nbytes / (ms / 1e3) / 1e9
+        out[name] = {"ms": ms, "n": n, "bytes": int(nbytes), "achieved_gbs": round(a, 1),
+                     "frac": round(a / hbm_gbs, 3), **(extra or {})}
+
+    g = torch.Generator(device="cuda").manual_seed(7)
+    lam_o = torch.randn(N, device="cuda", generator=g) * 0.2
+    ot = torch.empty(N, device="cuda")
+    ws = sgsplat.sg_admm_opacity_step(ds.opac, lam_o.clone(), ot, N // 2, importance=imp)
+    lam_w = lam_o.clone()
+    ms = _timed(lambda: sgsplat.sg_admm_opacity_step(ds.opac, lam_w, ot, N // 2, importance=imp, ws=ws),
+                steps, 2, flush)
+    hbm("admm_opacity_step", ms, 20 * N, N, {"kappa": N // 2, "score": "importance"})
+    lam_s = torch.randn(L, device="cuda", generator=g) * 0.3
+    st = torch.empty(L, device="cuda")
+    ws_s = sgsplat.sg_admm_sharpness_step(ds.sharp, ds.amp, lam_s.clone(), st, L // 2)
+    ms = _timed(lambda: sgsplat.sg_admm_sharpness_step(ds.sharp, ds.amp, lam_s, st, L // 2, ws=ws_s),
+                steps, 2, flush)
+    hbm("admm_sharpness_step", ms, 28 * L, L, {"kappa": L // 2, "score": "dynamic range"})
+    grad = torch.zeros(N, device="cuda")
+    ms = _timed(lambda: sgsplat.sg_admm_penalty_grad(ds.opac, ot, lam_o, 1e-3, grad), steps, 2, flush)
+    hbm("admm_penalty_grad", ms, 20 * N, N)
+    ms = _timed(lambda: sgsplat.sg_postprocess(ds, 0.05), steps, 2, flush)
+    kept = sgsplat.sg_postprocess(ds, 0.05)
+    nb = 64 * N + 32 * L + 64 * kept.n + 32 * int(kept.sharp.numel())
+    hbm("postprocess", ms, nb, N, {"tau_opacity": 0.05, "kept_gaussians": kept.n,
+                                   "kept_lobes": int(kept.sharp.numel()),
+                                   "note": "plan + apply, including the output allocation"})
+    del ds, kept
+    torch.cuda.empty_cache()
+    return out
+
+
 def render_vram(ds, cams, d_img, grads, static_bytes):
     """Rendering VRAM as the paper measures it (PyTorch allocator peak during a
     render, static parameters included): static parameter bytes + the peak
@@ -622,7 +675,7 @@ def render_vram(ds, cams, d_img, grads, static_bytes):
     return static_bytes + fwd_peak, static_bytes + both + grads_bytes + d_img.numel() * 4
 
 
-def run_forms(args, scene, cams, d_img, flush, steps):
+def run_forms(args, scene, cams, d_img, flush, steps, hbm_gbs=6800.0):
     """Timing (and VRAM / error) of the storage and batched forms."""
     import torch
     from paper_2509_07021_gb300 import render, sgsplat, synth
@@ -690,6 +743,10 @@ def run_forms(args, scene, cams, d_img, flush, steps):
                               "render_vram_mb": fwd_peak / 2**20, "fwd_bwd_vram_mb": both_peak / 2**20,
                               "sg_static_reduction": 1.0 - f32["static_mb"] / (static / 2**20)}
     del ds, grads
+
+    # ---- the rows after the render path: importance, ADMM steps, post-processing ----
+    torch.cuda.empty_cache()
+    forms["next_rows"] = next_rows(scene, cams, flush, steps, hbm_gbs)
 
     # ---- batched: 8 uneven scenes x 4 cameras, one CUDA graph ----
     for name, gen in (("batched_cfg2", synth.config2), ("stress_cfg4", synth.config4)):
