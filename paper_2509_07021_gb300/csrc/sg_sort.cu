@@ -21,39 +21,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return (1u << (threadIdx.x & 31)) - 1u;
 }
 
-// ---------------------------------------------------------------------------
-// block-wide exclusive scan helpers
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T warp_inclusive(T x) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const T y = __shfl_up_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) >= (unsigned)o) x += y;
-    }
-    return x;
-}
-
-// exclusive scan over blockDim.x (multiple of 32, <= 1024) values; returns the
-// exclusive prefix and writes the block total.
-template <typename T>
-__device__ __forceinline__ T block_exclusive(T x, T &total, T *sh /* >= 32 */) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const T inc = warp_inclusive(x);
-    if (lane == 31) sh[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        T w = lane < nw ? sh[lane] : T(0);
-        const T wi = warp_inclusive(w);
-        sh[lane] = wi - w;
-        if (lane == 31) sh[32] = wi;
-    }
-    __syncthreads();
-    const T r = sh[warp] + inc - x;
-    total = sh[32];
-    __syncthreads();
-    return r;
-}
 
 // ---------------------------------------------------------------------------
 // exclusive scan: reduce -> spine -> downsweep
@@ -561,63 +528,6 @@ __device__ __forceinline__ void hist_key_run(uint32_t (*h)[RS_RADIX], int passes
     }
 }
 
-// Decoupled look-back words of the duplicate blocks: 2 status bits (aggregate,
-// inclusive prefix) and a 62-bit pair count.
-constexpr uint64_t DL_AGG = 1ull << 62, DL_INC = 2ull << 62, DL_VAL = (1ull << 62) - 1ull;
-
-__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t *p) {
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed64(uint64_t *p, uint64_t v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" : : "l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Exclusive prefix of the pair counts of logical blocks [0, blk) (warp 0 of the
-// block; all its lanes return it). The block has published its own count
-// (DL_AGG) before it calls this, so successors never wait on a block that waits. Predecessors are read 32 at a time;
-// a run of ready words ending in an inclusive prefix completes the sum. Unready
-// words are polled at most spin_limit times; past that the status word gets
-// SG_ERR_TIMEOUT and the (smaller) partial prefix is returned.
-__device__ __forceinline__ uint64_t dup_lookback(uint64_t *__restrict__ dflags, uint64_t blk, uint64_t count,
-                                                 uint32_t spin_limit, uint64_t *status) {
-    const int lane = threadIdx.x & 31;
-    uint64_t excl = 0;
-    int64_t p = (int64_t)blk - 1;
-    uint32_t spins = 0;
-    while (p >= 0) {
-        const int64_t q = p - lane;
-        const uint64_t f = q >= 0 ? ld_relaxed64(dflags + q) : DL_INC;   // before block 0: prefix 0
-        const uint32_t unready = __ballot_sync(0xffffffffu, (f & ~DL_VAL) == 0ull);
-        const uint32_t inc = __ballot_sync(0xffffffffu, (f & DL_INC) != 0ull);
-        const int first_unready = unready ? __ffs(unready) - 1 : 32;
-        const int first_inc = inc ? __ffs(inc) - 1 : 32;
-        if (first_inc < first_unready) {
-            excl += warp_sum64(lane <= first_inc ? (f & DL_VAL) : 0ull);
-            break;
-        }
-        excl += warp_sum64(lane < first_unready ? (f & DL_VAL) : 0ull);
-        p -= first_unready;
-        if (first_unready < 32) {
-            if (++spins >= spin_limit) {
-                if (lane == 0) atomicExch(reinterpret_cast<unsigned long long *>(status),
-                                          (unsigned long long)SG_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(32);
-        }
-    }
-    if (lane == 0) st_relaxed64(dflags + blk, DL_INC | ((excl + count) & DL_VAL));
-    return excl;
-}
 
 // One block per 256 depth-sorted entries, in the order the blocks start
 // (logical index from counters[CNT_DUP_BLOCK]). The block's pairs go, entry by
@@ -697,7 +607,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
     s_base[threadIdx.x] = tbase;
     s_tx[threadIdx.x] = tx;
     if (threadIdx.x < 32) {
-        const uint64_t excl = dup_lookback(dflags, blk, total, spin_limit, counters + CNT_STATUS);
+        const uint64_t excl = block_lookback64(dflags, blk, total, spin_limit, counters + CNT_STATUS);
         if (threadIdx.x == 0) {
             s_out0 = excl;
             if ((V - 1) / 256 == blk) {   // the last block: the totals
