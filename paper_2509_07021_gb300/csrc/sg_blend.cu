@@ -224,10 +224,11 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
                                                const uint32_t *__restrict__ pval,
                                                const Rec *__restrict__ rec, float *__restrict__ img,
                                                float *__restrict__ T_final, int32_t *__restrict__ last,
-                                               uint32_t &ne, bool lists_ok) {
+                                               uint32_t &ne, bool lists_ok, float *__restrict__ part) {
     constexpr int NT = BLEND_THREADS / P;
     constexpr bool COUNT = MODE == FWD_COUNT;
     constexpr bool IMP = MODE == FWD_IMPORTANCE;
+    constexpr int PS = NB + 1;   // importance partials: part[thread * PS + entry], zero between batches
     int tx, ty;
     const ViewDesc *vw;
     tile_of_block(b, tile, tx, ty, vw);
@@ -252,19 +253,42 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
     }
     const int sub0 = (int)(threadIdx.x >> 5) * P;
     const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
+    // Importance: each thread leaves its share of Sum alpha T (over its pixels) for
+    // entry k of the batch in part[thread][k]; after the block's next barrier,
+    // thread k sums column k, zeroes it and adds the total to the Gaussian's
+    // score with one atomic (no warp collective per list entry).
+    int pending = 0;   // entries of the last batch whose partials are not yet summed
+    auto flush = [&]() {
+        for (int k = threadIdx.x; k < pending; k += NT) {
+            float sum = 0.f;
+            for (int t = 0; t < NT; ++t) {
+                sum += part[t * PS + k];
+                part[t * PS + k] = 0.f;
+            }
+            // only an entry of this view's scene (a stale id from another view is left out)
+            const uint32_t li = sm.id[k] - (uint32_t)vw->ent_off;
+            if (sum != 0.f && li < (uint32_t)vw->n) atomicAdd(imp + li, sum);
+        }
+        pending = 0;
+    };
     for (int base = 0; base < n; base += NB) {
         bool all = true;
 #pragma unroll
         for (int j = 0; j < P; ++j) all = all && done[j];
-        if (__syncthreads_count(all) == NT) break;
+        const bool stop = __syncthreads_count(all) == NT;
+        if (IMP && pending) {   // uniform
+            flush();
+            __syncthreads();   // before the staging below overwrites the batch's ids
+        }
+        if (stop) break;
         const int cnt = min(NB, n - base);
         for (int k = threadIdx.x; k < cnt; k += NT) {
             const uint32_t e = pval[rg.x + base + k];
             stage<!COUNT>(sm, k, rec[e], e, x0, y0);
         }
         __syncthreads();
-        // the importance sums are warp collectives: there, only whole warps leave
-        if (IMP ? __all_sync(0xffffffffu, all) : all) continue;
+        if (IMP) pending = cnt;
+        if (all) continue;
         // unrolled by 8 (measured: 3 % fewer cycles than no unrolling)
 #pragma unroll 8
         for (int k = 0; k < cnt; ++k) {
@@ -309,14 +333,13 @@ __device__ __forceinline__ void blend_fwd_tile(const Batch &b, uint32_t tile, St
                     if (IMP) wsum += w;
                 }
             }
-            if (IMP && __any_sync(0xffffffffu, wsum != 0.f)) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-                // only an entry of this view's scene (a stale id from another view is left out)
-                const uint32_t li = sm.id[k] - (uint32_t)vw->ent_off;
-                if ((threadIdx.x & 31) == 0 && li < (uint32_t)vw->n) atomicAdd(imp + li, wsum);
-            }
+            if (IMP && wsum != 0.f) part[threadIdx.x * PS + k] = wsum;
         }
+    }
+    if (IMP) {
+        __syncthreads();   // every thread's partials of the last batch are in
+        flush();
+        __syncthreads();   // the next tile's staging (persistent form) overwrites the ids
     }
     const uint64_t HW = (uint64_t)vw->W * (uint64_t)vw->H;
     float *im = img + 3 * vw->pix_off;
@@ -345,12 +368,17 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             unsigned long long *__restrict__ evals, const uint64_t *__restrict__ status) {
     chain_enter();
     __shared__ StagedN<NB> sm;
+    __shared__ float part[MODE == FWD_IMPORTANCE ? (BLEND_THREADS / P) * (NB + 1) : 1];
     __shared__ uint32_t s_item;
     const Batch &b = *bp;
     uint32_t ne = 0;
     const bool lists_ok = *status != (uint64_t)SG_ERR_TIMEOUT;
+    if (MODE == FWD_IMPORTANCE) {
+        for (int i = threadIdx.x; i < (BLEND_THREADS / P) * (NB + 1); i += BLEND_THREADS / P) part[i] = 0.f;
+        __syncthreads();
+    }
     if (!PERSIST) {
-        blend_fwd_tile<P, MODE, NB>(b, blockIdx.x, sm, ranges, pval, rec, img, T_final, last, ne, lists_ok);
+        blend_fwd_tile<P, MODE, NB>(b, blockIdx.x, sm, ranges, pval, rec, img, T_final, last, ne, lists_ok, part);
     } else {
         for (;;) {
             if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
@@ -359,7 +387,7 @@ k_blend_fwd(const Batch *__restrict__ bp, const uint2 *__restrict__ ranges,
             __syncthreads();
             if (item >= n_tiles) break;
             blend_fwd_tile<P, MODE, NB>(b, tile_order ? tile_order[item] : item, sm, ranges, pval, rec, img,
-                                        T_final, last, ne, lists_ok);
+                                        T_final, last, ne, lists_ok, part);
         }
     }
     if (MODE == FWD_COUNT) add_evals(ne, evals);
@@ -374,8 +402,9 @@ static void fwd_launch(const Batch *db, uint32_t n_tiles, const uint2 *ranges, c
         db, ranges, pval, rec, img, T_final, last, sh.tile_order, sh.queue, n_tiles, evals, sh.status);
 }
 
-// The plain forward takes the batch size of the tuning; the counting and
-// importance forms (whose results the batch does not change) take 64.
+// The plain forward takes the batch size of the tuning; the counting form
+// takes 64 and the importance form 32 (its per-thread partials of a batch sit in
+// shared memory); the batch changes no result.
 template <int P, bool PERSIST>
 static void fwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval,
                   const Rec *rec, float *img, float *T_final, int32_t *last, const BlendShape &sh,
@@ -383,7 +412,7 @@ static void fwd_p(const Batch *db, uint32_t n_tiles, const uint2 *ranges, const 
     if (evals)
         fwd_launch<P, FWD_COUNT, PERSIST, 64>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, evals, s);
     else if (sh.importance)
-        fwd_launch<P, FWD_IMPORTANCE, PERSIST, 64>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh,
+        fwd_launch<P, FWD_IMPORTANCE, PERSIST, 32>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh,
                                                    nullptr, s);
     else if (sh.batch == 32)
         fwd_launch<P, FWD_PLAIN, PERSIST, 32>(db, n_tiles, ranges, pval, rec, img, T_final, last, sh, nullptr, s);
