@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
     uint32_t e = 0, tt = 0, rows = 0, rx = 0, ry = 0, tbase = 0, tx = 1;
     if (j < V) {
         e = sorted_ent[j];
-        tt = e < M ? tiles_touched[e] : 0u;   // a stale id (see scan_load) reaches no tile
+        tt = e < M ? tiles_touched[e] : 0u;   // an id left by a sort that gave up a wait reaches no tile
     }
     // the block's pair count goes out first; the row bookkeeping below hides the
     // latency of the predecessors' counts

@@ -64,3 +64,20 @@ def test_penalty_grad_bit_exact():
     sgsplat.sg_admm_penalty_grad(_t(x), _t(xt), _t(lam), 5e-4, gd)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(gd.cpu().numpy(), admm.penalty_grad(g, x, xt, lam, 5e-4))
+
+
+@pytest.mark.parametrize("kappa", [1, 4000, 12345, 20000])
+def test_opacity_step_ties_across_blocks(kappa):
+    """The kappa-th score lies in a run of equal scores that spans many blocks
+    of the selection's final pass: the kept ties are the lowest indices."""
+    rng = np.random.default_rng(kappa)
+    n = 30000
+    o = rng.random(n).astype(np.float32)
+    lam = rng.normal(0, 0.2, n).astype(np.float32)
+    imp = np.where(rng.random(n) < 0.7, np.float32(0.5), rng.random(n).astype(np.float32)).astype(np.float32)
+    ot_ref, lam_ref, keep = admm.opacity_step(o, lam, kappa, imp)
+    lam_d, ot_d = _t(lam), torch.full((n,), float("nan"), device="cuda")
+    sgsplat.sg_admm_opacity_step(_t(o), lam_d, ot_d, kappa, importance=_t(imp))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ot_d.cpu().numpy(), ot_ref)
+    np.testing.assert_array_equal(lam_d.cpu().numpy(), lam_ref)
