@@ -231,16 +231,18 @@ int sg_profile_set_stages(uint32_t stage_mask);
  * threads to hide latency. *_persistent selects the persistent blend: one
  * launch of resident blocks that take (view, tile) items from a work counter,
  * tiles ordered by descending list length, instead of one block per tile.
- * sg_set_tuning(NULL) restores the defaults.
+ * sg_set_tuning(NULL) restores the defaults: both blends persistent, the
+ * forward with 4 pixels per thread, the backward with 8, 64-Gaussian batches.
  */
 typedef struct sg_tuning {
     int32_t fwd_pixels_per_thread;
     int32_t bwd_pixels_per_thread;
     int32_t fwd_persistent;   /* 1: resident blocks pull tiles, longest lists first */
     int32_t bwd_persistent;
-    /* Bound on the polls a radix-sort block makes of a predecessor that has not
-     * yet published its digit counts (the decoupled look-back of the depth and
-     * tile sorts) before it gives up: 0 = the default 2^20 (about a second).
+    /* Bound on the polls a block makes of a predecessor that has not yet
+     * published its counts (the decoupled look-backs of the depth and tile
+     * sorts, of the pair offsets in duplicateWithKeys and of the ADMM
+     * selection) before it gives up: 0 = the default 2^20 (about a second).
      * A block that gives up records SG_ERR_TIMEOUT (returned by the plain
      * forward, kept in the batched form's device status) and leaves that
      * call's outputs unspecified but every access inside its buffers.
