@@ -176,7 +176,9 @@ typedef struct sg_sizes {
  *   rect          [M] 2 x uint32: x0 | x1 << 16, y0 | y1 << 16 (tiles, half
  *                 open; the 3-sigma rectangle; empty = culled)
  *   depth_order   [M] uint32: the entries with tiles_touched > 0 sorted by
- *                 (depth bits, entry), first; the rest of the array is scratch
+ *                 (depth bits, entry), first. Scratch of the forward: its
+ *                 memory is reused by the tile sort, so a finished forward no
+ *                 longer holds it.
  *   ranges        [n_tiles] 2 x uint32 [start, end) into the pair arrays
  *                 ((0, 0) for a tile with no pair)
  *   pair_tile     [n_pairs] uint32 global tile id (view tile offset + ty * tiles_x + tx)

@@ -252,32 +252,40 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     L.tiles_touched = take(M * 4);
     L.rect = take(M * 8);
     L.clamp = take(M);
-    L.dkey0 = take(M * 4);
-    L.dval0 = take(M * 4);
-    L.dkey1 = take(M * 4);
-    L.dval1 = take(M * 4);
     L.dup_flags = take(div_up(M, 256) * 8 + 8);   // the duplicate blocks' look-back words
     L.ranges = take(T * 8);
     L.order = take(T * 4);   // tile order of the persistent blends (forward and backward)
     L.order_scratch = take(TILE_ORDER_WORDS * 4);
     L.fixed_end = o;
-    // pair-capacity dependent tail; the backward only reads pval_final
-    L.pval_final = take(cap * 4);
-    L.pkey_final = take(cap * 4);
-    L.pval_tmp = take(cap * 4);
-    L.pkey_tmp = take(cap * 4);
-    const uint64_t items = std::max<uint64_t>(std::max<uint64_t>(M, cap), T);
-    L.hist_blocks = (uint32_t)div_up(items, RS_TILE);
-    L.hist = take((size_t)4 * RS_RADIX * L.hist_blocks * 4);   // look-back flags of up to 4 passes
-    const uint64_t sums = div_up(items, SCAN_TILE) + div_up((uint64_t)RS_RADIX * L.hist_blocks, SCAN_TILE) + 1;
-    L.scan_sums = take(std::max<size_t>(sums * 8, SORT_AUX_BYTES));
+    L.tile_bits = tile_bits_for(T);
+    L.tile_passes = radix_passes(L.tile_bits);
+    // Pairs: region A receives the duplicate's (tile, entry) pairs, region B the
+    // first tile pass's output, and the passes alternate between them. The
+    // depth sort's four buffers live in B: B is first written by the tile sort,
+    // after the duplicate has read the depth order. The backward reads only the
+    // final entries (A after an even number of passes, else B).
+    const size_t pairs4 = al(cap * 4), m4 = al(M * 4);
+    const size_t A = take(2 * pairs4);
+    const size_t B = take(std::max(2 * pairs4, 4 * m4));
+    L.dkey0 = B;
+    L.dval0 = B + m4;
+    L.dkey1 = B + 2 * m4;
+    L.dval1 = B + 3 * m4;
+    const size_t fin = L.tile_passes % 2 == 0 ? A : B, tmp = fin == A ? B : A;
+    L.pkey_final = fin;
+    L.pval_final = fin + pairs4;
+    L.pkey_tmp = tmp;
+    L.pval_tmp = tmp + pairs4;
+    // look-back flags of the depth sort's 4 passes, then of the tile sort's passes
+    const uint64_t flag_words =
+        std::max<uint64_t>(4 * div_up(M, RS_TILE), (uint64_t)L.tile_passes * div_up(cap, RS_TILE)) * RS_RADIX;
+    L.hist = take(flag_words * 4);
+    L.scan_sums = take(SORT_AUX_BYTES);   // the depth sort's aux
     L.aux_tile = take(SORT_AUX_BYTES);
     L.total = o;
     L.M = M;
     L.n_tiles = T;
     L.cap = cap;
-    L.tile_bits = tile_bits_for(T);
-    L.tile_passes = radix_passes(L.tile_bits);
     return L;
 }
 

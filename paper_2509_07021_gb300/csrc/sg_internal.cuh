@@ -98,7 +98,6 @@ struct WsLayout {
         dup_flags, ranges, order, order_scratch, scan_sums, hist, aux_tile, fixed_end;
     size_t pval_final, pkey_final, pval_tmp, pkey_tmp, total;
     uint64_t M, n_tiles, cap;
-    uint32_t hist_blocks;     // radix blocks of the larger sort
     int tile_bits, tile_passes;
 };
 
