@@ -45,8 +45,8 @@ FLOPS_PER_EVAL = {"blend_fwd": 23.0, "blend_bwd": 69.0}
 # while the sources are unchanged (any kernel change makes it null until the
 # next capture).
 RECORDED_TRAFFIC = {
-    "sources": "696d3f25c519d3cc9749fbe37b2956df907802326948e4f4a3bcb0e184315549",
-    "bytes": {"blend_bwd": 121858048, "blend_fwd": 50713600},
+    "sources": "a1bec279fc40508abf75bbded62dc8198c8dcea5d1901ab6029ec859bf14ac93",
+    "bytes": {"blend_bwd": 120956928, "blend_fwd": 50107136},
 }
 
 
