@@ -181,7 +181,10 @@ typedef struct sg_sizes {
  *                 longer holds it.
  *   ranges        [n_tiles] 2 x uint32 [start, end) into the pair arrays
  *                 ((0, 0) for a tile with no pair)
- *   pair_tile     [n_pairs] uint32 global tile id (view tile offset + ty * tiles_x + tx)
+ *   pair_tile     [n_pairs] uint32 global tile id (view tile offset + ty * tiles_x + tx),
+ *                 or UINT64_MAX: a forward whose views have at most 12288 tiles
+ *                 in all sorts the pairs by counting and keeps no sorted tile
+ *                 ids; pair k's tile is then the tile whose range holds k
  *   pair_entry    [n_pairs] uint32 entry of each pair, sorted by (tile, depth bits, entry)
  */
 typedef struct sg_ws_layout {

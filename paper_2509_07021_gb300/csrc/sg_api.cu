@@ -259,26 +259,40 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     L.fixed_end = o;
     L.tile_bits = tile_bits_for(T);
     L.tile_passes = radix_passes(L.tile_bits);
+    // the tile sort counts where one chunk's tile counters fit shared memory
+    L.tile_counting = T >= 1 && T <= TC_MAX_TILES;
+    L.tc_chunks = L.tile_counting ? tc_chunks(cap) : 0u;
     // Pairs: region A receives the duplicate's (tile, entry) pairs, region B the
-    // first tile pass's output, and the passes alternate between them. The
-    // depth sort's four buffers live in B: B is first written by the tile sort,
-    // after the duplicate has read the depth order. The backward reads only the
-    // final entries (A after an even number of passes, else B).
+    // tile sort's first output, and radix passes alternate between them; the
+    // counting sort writes only the sorted entries, into B. The depth sort's
+    // four buffers live in B: B is first written by the tile sort, after the
+    // duplicate has read the depth order. The backward reads only the final
+    // entries (B when counting, else A after an even number of passes, B after
+    // an odd one).
     const size_t pairs4 = al(cap * 4), m4 = al(M * 4);
     const size_t A = take(2 * pairs4);
-    const size_t B = take(std::max(2 * pairs4, 4 * m4));
+    const size_t B = take(std::max((L.tile_counting ? 1 : 2) * pairs4, 4 * m4));
     L.dkey0 = B;
     L.dval0 = B + m4;
     L.dkey1 = B + 2 * m4;
     L.dval1 = B + 3 * m4;
-    const size_t fin = L.tile_passes % 2 == 0 ? A : B, tmp = fin == A ? B : A;
-    L.pkey_final = fin;
-    L.pval_final = fin + pairs4;
-    L.pkey_tmp = tmp;
-    L.pval_tmp = tmp + pairs4;
-    // look-back flags of the depth sort's 4 passes, then of the tile sort's passes
-    const uint64_t flag_words =
-        std::max<uint64_t>(4 * div_up(M, RS_TILE), (uint64_t)L.tile_passes * div_up(cap, RS_TILE)) * RS_RADIX;
+    if (L.tile_counting) {
+        L.pkey_final = NO_OFFSET;
+        L.pval_final = B;
+        L.pkey_tmp = A;
+        L.pval_tmp = A + pairs4;
+    } else {
+        const size_t fin = L.tile_passes % 2 == 1 ? B : A, tmp = fin == A ? B : A;
+        L.pkey_final = fin;
+        L.pval_final = fin + pairs4;
+        L.pkey_tmp = tmp;
+        L.pval_tmp = tmp + pairs4;
+    }
+    // look-back flags of the depth sort's 4 passes, then those of the tile
+    // sort's radix passes or the counting sort's [chunks][row] count matrix
+    const uint64_t tile_words = L.tile_counting ? (uint64_t)L.tc_chunks * tc_row(T)
+                                                : (uint64_t)L.tile_passes * div_up(cap, RS_TILE) * RS_RADIX;
+    const uint64_t flag_words = std::max<uint64_t>(4 * div_up(M, RS_TILE) * RS_RADIX, tile_words);
     L.hist = take(flag_words * 4);
     L.scan_sums = take(SORT_AUX_BYTES);   // the depth sort's aux
     L.aux_tile = take(SORT_AUX_BYTES);
@@ -342,7 +356,10 @@ void fill_sizes(const Batch &b, const WsLayout &L, uint64_t n_pairs, sg_sizes *o
     out->n_pairs = n_pairs;
     out->pair_capacity = L.cap;
     out->ws_fixed_bytes = make_layout(b, 0).total;
-    out->ws_per_pair_bytes = 17;
+    // pair buffers (keys and entries twice; the counting sort keeps no sorted
+    // keys), plus the radix passes' look-back words or, below the counting
+    // sort's chunk limit, its count matrix rows
+    out->ws_per_pair_bytes = L.tile_counting ? 12 + div_up(4 * tc_row(b.n_tiles), TC_CHUNK_TARGET) : 17;
     out->ws_bytes = L.total;
     out->bwd_ws_bytes = bwd_bytes(b);
 }
@@ -472,24 +489,34 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
     // grids sized by the capacity (at most SORT_MAX_KEYS pairs); counts read on the device
     const uint64_t cap_dev = std::min<uint64_t>(cap, SORT_MAX_KEYS);
     uint64_t K = cap_dev;
-    // duplicate into the buffer from which an even/odd number of tile passes ends in *_final
-    uint32_t *pk_final = reinterpret_cast<uint32_t *>(w + L.pkey_final);
+    // duplicate into the buffer from which the tile sort ends in *_final: the
+    // counting sort and an odd number of radix passes write the other buffer
+    uint32_t *pk_final = L.tile_counting ? nullptr : reinterpret_cast<uint32_t *>(w + L.pkey_final);
     uint32_t *pv_final = reinterpret_cast<uint32_t *>(w + L.pval_final);
     uint32_t *pk_tmp = reinterpret_cast<uint32_t *>(w + L.pkey_tmp);
     uint32_t *pv_tmp = reinterpret_cast<uint32_t *>(w + L.pval_tmp);
-    const bool even = (L.tile_passes % 2) == 0;
-    uint32_t *k0 = even ? pk_final : pk_tmp, *v0 = even ? pv_final : pv_tmp;
-    uint32_t *k1 = even ? pk_tmp : pk_final, *v1 = even ? pv_tmp : pv_final;
+    const bool dup_final = !L.tile_counting && (L.tile_passes % 2) == 0;
+    uint32_t *k0 = dup_final ? pk_final : pk_tmp, *v0 = dup_final ? pv_final : pv_tmp;
+    uint32_t *k1 = dup_final ? pk_tmp : pk_final, *v1 = dup_final ? pv_tmp : pv_final;
     {
         StageTimer t(ST_DUPLICATE, stream);
-        // also the tile sort's digit histograms and cleared look-back flags
+        // radix: also the tile sort's digit histograms and cleared look-back flags
         // the pair offsets come from the duplicate blocks' own look-back (no scan kernel)
+        const int hp = L.tile_counting ? 0 : L.tile_passes;
         SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, rec, counters, cap_dev, k0, v0, dup_flags,
-                                 rb ? rb->dev_ptr : nullptr, stream, L.tile_passes, aux_tile, hist,
-                                 sort_flag_words(K, L.tile_bits)),
+                                 rb ? rb->dev_ptr : nullptr, stream, hp, hp ? aux_tile : nullptr,
+                                 hp ? hist : nullptr, hp ? sort_flag_words(K, L.tile_bits) : 0),
                 "duplicateWithKeys");
     }
-    {
+    if (L.tile_counting) {
+        StageTimer t(ST_TILE_SORT, stream);
+        // also the tile ranges and the tile order's bucket counts; the plain
+        // form's status word goes to the host word next to the pair count
+        SG_CUDA(launch_tile_count_sort(k0, v0, v1, counters, cap_dev, (uint32_t)L.n_tiles, L.tc_chunks, hist,
+                                       aux_tile, ranges, reinterpret_cast<uint32_t *>(w + L.order_scratch),
+                                       rb ? rb->dev_ptr + 1 : nullptr, stream),
+                "tile sort");
+    } else {
         StageTimer t(ST_TILE_SORT, stream);
         // the last pass also bounds every tile's range in the sorted pairs
         // plain form: the sorts' merged status also goes to the host word next to the pair count

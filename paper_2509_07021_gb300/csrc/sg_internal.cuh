@@ -99,9 +99,15 @@ struct WsLayout {
     size_t pval_final, pkey_final, pval_tmp, pkey_tmp, total;
     uint64_t M, n_tiles, cap;
     int tile_bits, tile_passes;
+    bool tile_counting;   // the tile sort counts (launch_tile_count_sort) instead of radix passes:
+    uint32_t tc_chunks;   // its chunks; its count matrix takes the look-back flags' region and
+                          // no sorted keys are kept (pkey_final = NO_OFFSET)
 };
 
 __host__ __device__ inline uint64_t div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// A workspace buffer the layout does not hold.
+constexpr size_t NO_OFFSET = ~(size_t)0;
 
 // ---------------------------------------------------------------------------
 // Tight tile binning. A pair (tile, Gaussian) can only blend where
@@ -311,12 +317,12 @@ __device__ __forceinline__ void chain_enter() {
 }
 
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_chain(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
-                                Args &&...args) {
+inline cudaError_t launch_chain_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                     cudaStream_t s, Args &&...args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -324,6 +330,12 @@ inline cudaError_t launch_chain(void (*kernel)(KArgs...), dim3 grid, dim3 block,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chain(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                                Args &&...args) {
+    return launch_chain_smem(kernel, grid, block, 0, s, static_cast<Args &&>(args)...);
 }
 
 // Process-wide count of kernels this library has launched (sg_kernel_launches).
@@ -410,6 +422,29 @@ cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted
                              uint64_t *counters, uint64_t cap, uint32_t *pkey, uint32_t *pval,
                              uint64_t *dup_flags, uint64_t *mirror, cudaStream_t s, int hist_passes = 0,
                              uint64_t *sort_aux = nullptr, uint32_t *flags = nullptr, uint64_t flag_words = 0);
+// Tile sort by counting, for tile counts up to TC_MAX_TILES (one chunk's
+// counters fit 48 KB of shared memory): a stable sort by tile of the
+// duplicate's (tile, entry) pairs, the same order as launch_radix_sort's, in
+// three kernels with no pass over the key bits. Only the entries are written
+// (ovals, cap words): a pair's tile is the tile whose range holds it. The pair
+// count is min(counters[CNT_WRITTEN], cap), none when counters[CNT_STATUS] is
+// not SG_OK on entry. matrix: n_chunks x tc_row(n_tiles) words (no zeroing
+// needed); words: zeroed, 8 + 8 * ceil(n_tiles / 32) bytes; ranges: every
+// tile's [first, last + 1) in the output ((0, 0) when empty); order_counts:
+// the tile order's zeroed bucket counts, incremented here; status_mirror
+// (nullable): receives counters[CNT_STATUS] after the sort. cap below 2^32.
+constexpr uint32_t TC_MAX_TILES = 12288;
+#ifndef SG_TC_MAX_CHUNKS
+#define SG_TC_MAX_CHUNKS 608
+#endif
+constexpr uint32_t TC_MAX_CHUNKS = SG_TC_MAX_CHUNKS;   // four one-warp placing blocks per SM
+constexpr uint64_t TC_CHUNK_TARGET = 8192;            // pairs per chunk when the capacity is small
+uint32_t tc_chunks(uint64_t cap);                      // chunks of a sort sized for cap pairs
+uint64_t tc_row(uint64_t n_tiles);                     // words per row of the count matrix (multiple of 4)
+cudaError_t launch_tile_count_sort(const uint32_t *keys, const uint32_t *vals, uint32_t *ovals,
+                                   uint64_t *counters, uint64_t cap, uint32_t n_tiles, uint32_t n_chunks,
+                                   uint32_t *matrix, uint64_t *words, uint2 *ranges, uint32_t *order_counts,
+                                   uint64_t *status_mirror, cudaStream_t s);
 // Tiles by descending list length (256 length buckets) into order[n_tiles].
 // scratch: TILE_ORDER_WORDS zeroed words whose first 256 already hold the
 // bucket counts (launch_radix_sort's order_counts, filled by its finish kernel).

@@ -502,6 +502,234 @@ cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
 }
 
 // ---------------------------------------------------------------------------
+// tile sort by counting (tile counts up to TC_MAX_TILES)
+// ---------------------------------------------------------------------------
+// The duplicate's pairs, in depth order, are cut into C chunks of equal length.
+// k_tc_count counts each chunk's pairs per tile (row c of the [C][row] count
+// matrix); k_tc_scan scans the matrix in (tile, chunk) order, which turns row c
+// into the first output position of chunk c's pairs of every tile and bounds
+// every tile's range; k_tc_place walks each chunk's pairs in order and puts
+// each at its tile's next position. Inside a tile the pairs follow the chunks
+// in order and, inside a chunk, their input order: the result is the stable
+// sort by tile, identical to the LSD radix sort's.
+uint32_t tc_chunks(uint64_t cap) {
+    const uint64_t c = div_up(cap, TC_CHUNK_TARGET);
+    return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(c, 1), TC_MAX_CHUNKS);
+}
+
+uint64_t tc_row(uint64_t n_tiles) { return div_up(n_tiles, 4) * 4; }
+
+// [lo, hi): chunk c of the pairs the duplicate wrote; none when the status
+// says the pairs are incomplete (capacity overflow, or a bounded wait that
+// gave up: the lists may hold stale words).
+__device__ __forceinline__ void tc_chunk(const uint64_t *counters, uint64_t cap, uint32_t n_chunks, uint32_t c,
+                                         uint64_t &lo, uint64_t &hi) {
+    const uint64_t st = counters[CNT_STATUS];
+    const uint64_t K = st == (uint64_t)SG_OK ? min(counters[CNT_WRITTEN], cap) : 0ull;
+    const uint64_t len = div_up(div_up(K, n_chunks), 32) * 32;
+    lo = min(K, (uint64_t)c * len);
+    hi = min(K, lo + len);
+}
+
+// One block per chunk: shared-memory counters of every tile, then row c.
+__global__ void __launch_bounds__(256) k_tc_count(const uint32_t *__restrict__ keys,
+                                                  const uint64_t *__restrict__ counters, uint64_t cap,
+                                                  uint32_t n_tiles, uint32_t row, uint32_t *__restrict__ counts) {
+    chain_enter();
+    extern __shared__ uint4 tc_smem[];
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(tc_smem);
+    for (uint32_t q = threadIdx.x; q < row / 4; q += blockDim.x) tc_smem[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    uint64_t lo, hi;
+    tc_chunk(counters, cap, gridDim.x, blockIdx.x, lo, hi);
+    // 16-byte loads (a chunk starts at a multiple of 32 keys), then the tail
+    const uint64_t n4 = (hi - lo) / 4;
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + lo);
+#pragma unroll 8
+    for (uint64_t q = threadIdx.x; q < n4; q += blockDim.x) {
+        const uint4 t = k4[q];
+        if (t.x < n_tiles) atomicAdd(&cnt[t.x], 1u);
+        if (t.y < n_tiles) atomicAdd(&cnt[t.y], 1u);
+        if (t.z < n_tiles) atomicAdd(&cnt[t.z], 1u);
+        if (t.w < n_tiles) atomicAdd(&cnt[t.w], 1u);
+    }
+    for (uint64_t i = lo + 4 * n4 + threadIdx.x; i < hi; i += blockDim.x) {
+        const uint32_t t = keys[i];
+        if (t < n_tiles) atomicAdd(&cnt[t], 1u);
+    }
+    __syncthreads();
+    uint4 *dst = reinterpret_cast<uint4 *>(counts + (uint64_t)blockIdx.x * row);
+    for (uint32_t q = threadIdx.x; q < row / 4; q += blockDim.x) dst[q] = tc_smem[q];
+}
+
+// Groups of 32 tiles (lane = tile), taken in order from a ticket by resident
+// blocks; the chunks split into TC_SCAN_WARPS runs (one per warp), whose counts
+// stay in registers. The sum of each tile's counts and the group's total go
+// through a decoupled look-back over the groups before it, which gives every
+// tile's first position; the second walk replaces each count with its chunk's
+// first position of the tile. Also writes every tile's range ((0, 0) when
+// empty) and adds the tile to its list-length bucket.
+// words: zeroed; [0] the ticket, [1 + g] group g's look-back word.
+constexpr int TC_SCAN_WARPS = 32;
+__global__ void __launch_bounds__(TC_SCAN_WARPS * 32) k_tc_scan(uint32_t *__restrict__ counts, uint32_t n_chunks,
+                                                              uint32_t row, uint32_t n_tiles,
+                                                              uint64_t *__restrict__ words,
+                                                              uint2 *__restrict__ ranges,
+                                                              uint32_t *__restrict__ bucket_counts,
+                                                              uint64_t *__restrict__ status, uint32_t spin_limit) {
+    chain_enter();
+    __shared__ uint32_t part[TC_SCAN_WARPS][32];
+    __shared__ uint32_t s_start[32];
+    __shared__ uint32_t s_grp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t n_groups = (n_tiles + 31) / 32;
+    const uint32_t per = (n_chunks + TC_SCAN_WARPS - 1) / TC_SCAN_WARPS;
+    const uint32_t c0 = min(n_chunks, warp * per), c1 = min(n_chunks, c0 + per);
+    constexpr int RUN = (TC_MAX_CHUNKS + TC_SCAN_WARPS - 1) / TC_SCAN_WARPS;
+    for (;;) {
+        // every thread is past the previous group's reads of the shared words
+        __syncthreads();
+        if (threadIdx.x == 0) s_grp = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long *>(words), 1ull);
+        __syncthreads();
+        const uint32_t grp = s_grp;
+        if (grp >= n_groups) break;   // uniform
+        const uint32_t t = grp * 32 + lane;
+        const bool tv = t < n_tiles;
+        uint32_t *col = counts + t;
+        uint32_t cv[RUN];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < RUN; ++j) {
+            const uint32_t c = c0 + (uint32_t)j;
+            cv[j] = (tv && c < c1) ? col[(uint64_t)c * row] : 0u;
+            sum += cv[j];
+        }
+        part[warp][lane] = sum;
+        __syncthreads();
+        // each warp its runs' prefix over the warps before it; warp 0 the totals
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += part[w][lane];
+        uint32_t tot = 0;
+        if (warp == 0) {
+#pragma unroll
+            for (int w = 0; w < TC_SCAN_WARPS; ++w) tot += part[w][lane];
+        }
+        if (warp == 0) {
+            const uint32_t inc = warp_inclusive(tot);
+            const uint32_t grp_total = __shfl_sync(0xffffffffu, inc, 31);
+            if (lane == 0) st_relaxed64(words + 1 + grp, DL_AGG | (uint64_t)grp_total);
+            const uint64_t excl = block_lookback64(words + 1, grp, grp_total, spin_limit, status);
+            const uint32_t start = (uint32_t)(excl + inc - tot);
+            s_start[lane] = start;
+            if (tv) {
+                const uint2 rg = tot ? make_uint2(start, start + tot) : make_uint2(0u, 0u);
+                ranges[t] = rg;
+                if (bucket_counts) atomicAdd(&bucket_counts[len_bucket(rg)], 1u);
+            }
+        }
+        __syncthreads();
+        uint32_t run = s_start[lane] + before;
+#pragma unroll
+        for (int j = 0; j < RUN; ++j) {
+            const uint32_t c = c0 + (uint32_t)j;
+            if (tv && c < c1) col[(uint64_t)c * row] = run;
+            run += cv[j];
+        }
+    }
+}
+
+// One warp per chunk: its row of first positions in shared memory, then the
+// chunk's pairs 32 at a time in order (the entries only: a pair's tile is the
+// tile whose range holds it). Lanes holding the same tile are grouped
+// (match_any); the group's first lane takes as many positions from the tile's
+// cursor as the group has lanes, and each lane takes the one of its rank in the
+// group. The warp barrier between rounds orders the cursor updates of
+// successive rounds. Positions at or past cap are not written.
+__global__ void __launch_bounds__(32) k_tc_place(const uint32_t *__restrict__ keys,
+                                                 const uint32_t *__restrict__ vals,
+                                                 const uint64_t *__restrict__ counters, uint64_t cap,
+                                                 uint32_t n_tiles, uint32_t row,
+                                                 const uint32_t *__restrict__ first,
+                                                 uint32_t *__restrict__ ovals, uint64_t *status_mirror) {
+    chain_enter();
+    extern __shared__ uint4 tc_smem[];
+    uint32_t *next = reinterpret_cast<uint32_t *>(tc_smem);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x;
+    if (blockIdx.x == 0 && lane == 0 && status_mirror) *status_mirror = counters[CNT_STATUS];
+    const uint4 *src = reinterpret_cast<const uint4 *>(first + (uint64_t)blockIdx.x * row);
+#pragma unroll 8
+    for (uint32_t q = lane; q < row / 4; q += 32) tc_smem[q] = src[q];
+    __syncwarp();
+    uint64_t lo, hi;
+    tc_chunk(counters, cap, gridDim.x, blockIdx.x, lo, hi);
+    const uint32_t lt = (1u << lane) - 1u;
+    // rounds of 32 pairs, U rounds per batch; the next batch's keys and values
+    // are loaded while this one is placed
+    constexpr int U = 8;
+    uint32_t tn[U], vn[U];
+    auto load = [&](uint64_t base) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t i = base + (uint64_t)(32 * u + lane);
+            tn[u] = i < hi ? keys[i] : 0xFFFFFFFFu;
+            vn[u] = i < hi ? vals[i] : 0u;
+        }
+    };
+    load(lo);
+    for (uint64_t base = lo; base < hi; base += 32 * U) {
+        uint32_t t[U], v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            t[u] = tn[u];
+            v[u] = vn[u];
+        }
+        if (base + 32 * U < hi) load(base + 32 * U);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = t[u] < n_tiles;
+            const uint32_t grp = __match_any_sync(FULL, ok ? t[u] : 0xFFFFFFFFu);
+            const int leader = __ffs(grp) - 1;
+            uint32_t at = 0;
+            if (ok && lane == leader) at = atomicAdd(&next[t[u]], (uint32_t)__popc(grp));
+            at = __shfl_sync(FULL, at, leader);
+            const uint32_t pos = at + (uint32_t)__popc(grp & lt);
+            if (ok && pos < cap) ovals[pos] = v[u];
+            __syncwarp();
+        }
+    }
+}
+
+cudaError_t launch_tile_count_sort(const uint32_t *keys, const uint32_t *vals, uint32_t *ovals,
+                                   uint64_t *counters, uint64_t cap, uint32_t n_tiles, uint32_t n_chunks,
+                                   uint32_t *matrix, uint64_t *words, uint2 *ranges, uint32_t *order_counts,
+                                   uint64_t *status_mirror, cudaStream_t s) {
+    if (n_tiles == 0 || n_tiles > TC_MAX_TILES || n_chunks == 0 || n_chunks > TC_MAX_CHUNKS || cap > UINT32_MAX)
+        return cudaErrorInvalidValue;
+    const uint32_t row = (uint32_t)tc_row(n_tiles);
+    const size_t smem = (size_t)row * 4;
+    (void)launch_chain_smem(k_tc_count, dim3(n_chunks), dim3(256), smem, s, keys, (const uint64_t *)counters, cap,
+                       n_tiles, row, matrix);
+    // resident blocks only: a group's look-back may wait on any earlier group
+    static int scan_blocks = 0;
+    if (scan_blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_scan, TC_SCAN_WARPS * 32, 0) != cudaSuccess)
+            return cudaErrorUnknown;
+        scan_blocks = std::max(1, sms * per_sm);
+    }
+    const unsigned sgrid = (unsigned)std::min<uint64_t>(div_up(n_tiles, 32), (uint64_t)scan_blocks);
+    (void)launch_chain(k_tc_scan, dim3(sgrid), dim3(TC_SCAN_WARPS * 32), s, matrix, n_chunks,
+                       row, n_tiles, words, ranges, order_counts, counters + CNT_STATUS, sort_wait_polls());
+    (void)launch_chain_smem(k_tc_place, dim3(n_chunks), dim3(32), smem, s, keys, vals, (const uint64_t *)counters, cap,
+                       n_tiles, row, (const uint32_t *)matrix, ovals, status_mirror);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // duplicateWithKeys: entries in depth order -> (tile, entry) pairs
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int find_entry_view(const Batch &b, uint64_t e) {

@@ -14,6 +14,9 @@ IMG_TOL = 2e-4      # max abs per channel (images)
 GRAD_TOL = 1e-3     # relative L2 per gradient tensor
 
 
+NO_OFFSET = 2**64 - 1   # a workspace buffer the layout does not hold
+
+
 def u32(t: torch.Tensor) -> np.ndarray:
     return t.view(torch.int32).cpu().numpy().view(np.uint32)
 
@@ -31,7 +34,14 @@ class GpuView:
         self.rect = np.stack([rect[:, 0] & 0xFFFF, rect[:, 1] & 0xFFFF, rect[:, 0] >> 16,
                               rect[:, 1] >> 16], 1).astype(np.int64)
         self.ranges = u32(ws[lay["ranges"]:lay["ranges"] + 8 * T]).reshape(T, 2).astype(np.int64)
-        self.pair_tile = u32(ws[lay["pair_tile"]:lay["pair_tile"] + 4 * K]).astype(np.int64)
+        if lay["pair_tile"] == NO_OFFSET:
+            # sorted by counting: no tile ids are kept, pair k's tile is the
+            # tile whose range holds k (-1 where no range does)
+            self.pair_tile = np.full(K, -1, np.int64)
+            for t in np.nonzero(self.ranges[:, 1] > self.ranges[:, 0])[0]:
+                self.pair_tile[self.ranges[t, 0]:self.ranges[t, 1]] = t
+        else:
+            self.pair_tile = u32(ws[lay["pair_tile"]:lay["pair_tile"] + 4 * K]).astype(np.int64)
         self.pair_entry = u32(ws[lay["pair_entry"]:lay["pair_entry"] + 4 * K]).astype(np.int64)
         self.view_n = [int(n) for n in view_n]
         self.ent_off = np.concatenate([[0], np.cumsum(self.view_n)]).astype(np.int64)

@@ -61,14 +61,19 @@ def test_workspace_query_sizes(L):
     assert q0["n_tiles"] == 8 * 6 + 4 * 4
     assert q0["n_pixels"] == 128 * 96 + 64 * 64
     assert q0["ws_fixed_bytes"] == q0["ws_bytes"] == q1["ws_fixed_bytes"]
-    # 16 bytes of pair buffers per pair plus the tile sort's look-back flags; the
-    # depth sort's buffers (16 bytes per entry) live in the pair buffers' memory
+    # 64 tiles: the tile sort counts, so 12 bytes of pair buffers per pair (the
+    # duplicate's keys and entries, the sorted entries) plus its count matrix;
+    # the depth sort's buffers (16 bytes per entry) live in the pair buffers'
+    # memory (regions aligned to 256 bytes)
     diff = q1["ws_bytes"] - q1["ws_fixed_bytes"]
-    assert 16 * 100_000 - 16 * 2000 <= diff <= 18 * 100_000 + 4096
+    assert 12 * 100_000 - 16 * 2000 - 1024 <= diff <= 14 * 100_000 + 4096
+    assert q1["ws_per_pair_bytes"] >= 12
     assert q1["bwd_ws_bytes"] >= 9 * 4 * 2000
     lay = sgsplat.sg_workspace_layout(ds, cams, q1["ws_bytes"])
     assert lay["total_bytes"] == q1["ws_bytes"]
-    offs = sorted(v for k, v in lay.items() if k != "total_bytes")
+    # the counting sort keeps no sorted tile ids
+    assert lay["pair_tile"] == 2**64 - 1
+    offs = sorted(v for k, v in lay.items() if k not in ("total_bytes", "pair_tile"))
     assert all(o % 256 == 0 for o in offs)
     assert len(set(offs)) == len(offs)
 
