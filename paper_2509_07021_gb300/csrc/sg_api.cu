@@ -270,7 +270,8 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
     // entries (B when counting, else A after an even number of passes, B after
     // an odd one).
     const size_t pairs4 = al(cap * 4), m4 = al(M * 4);
-    const size_t A = take(2 * pairs4);
+    // (the counting sort's keys are 16-bit)
+    const size_t A = take(L.tile_counting ? al(cap * 2) + pairs4 : 2 * pairs4);
     const size_t B = take(std::max((L.tile_counting ? 1 : 2) * pairs4, 4 * m4));
     L.dkey0 = B;
     L.dval0 = B + m4;
@@ -280,7 +281,7 @@ WsLayout make_layout(const Batch &b, uint64_t cap) {
         L.pkey_final = NO_OFFSET;
         L.pval_final = B;
         L.pkey_tmp = A;
-        L.pval_tmp = A + pairs4;
+        L.pval_tmp = A + al(cap * 2);
     } else {
         const size_t fin = L.tile_passes % 2 == 1 ? B : A, tmp = fin == A ? B : A;
         L.pkey_final = fin;
@@ -356,10 +357,11 @@ void fill_sizes(const Batch &b, const WsLayout &L, uint64_t n_pairs, sg_sizes *o
     out->n_pairs = n_pairs;
     out->pair_capacity = L.cap;
     out->ws_fixed_bytes = make_layout(b, 0).total;
-    // pair buffers (keys and entries twice; the counting sort keeps no sorted
-    // keys), plus the radix passes' look-back words or, below the counting
-    // sort's chunk limit, its count matrix rows
-    out->ws_per_pair_bytes = L.tile_counting ? 12 + div_up(4 * tc_row(b.n_tiles), TC_CHUNK_TARGET) : 17;
+    // pair buffers (32-bit keys and entries twice; the counting sort's 16-bit
+    // keys and entries, then the sorted entries), plus the radix passes'
+    // look-back words or, below the counting sort's chunk limit, its count
+    // matrix rows
+    out->ws_per_pair_bytes = L.tile_counting ? 10 + div_up(4 * tc_row(b.n_tiles), TC_CHUNK_TARGET) : 17;
     out->ws_bytes = L.total;
     out->bwd_ws_bytes = bwd_bytes(b);
 }
@@ -505,14 +507,15 @@ int forward_impl(const sg_scene *scenes, int n_scenes, const sg_camera *cams, co
         const int hp = L.tile_counting ? 0 : L.tile_passes;
         SG_CUDA(launch_duplicate(db, M, dval0, tt, rect, rec, counters, cap_dev, k0, v0, dup_flags,
                                  rb ? rb->dev_ptr : nullptr, stream, hp, hp ? aux_tile : nullptr,
-                                 hp ? hist : nullptr, hp ? sort_flag_words(K, L.tile_bits) : 0),
+                                 hp ? hist : nullptr, hp ? sort_flag_words(K, L.tile_bits) : 0, L.tile_counting),
                 "duplicateWithKeys");
     }
     if (L.tile_counting) {
         StageTimer t(ST_TILE_SORT, stream);
         // also the tile ranges and the tile order's bucket counts; the plain
         // form's status word goes to the host word next to the pair count
-        SG_CUDA(launch_tile_count_sort(k0, v0, v1, counters, cap_dev, (uint32_t)L.n_tiles, L.tc_chunks, hist,
+        SG_CUDA(launch_tile_count_sort(reinterpret_cast<const uint16_t *>(k0), v0, v1, counters, cap_dev,
+                                       (uint32_t)L.n_tiles, L.tc_chunks, hist,
                                        aux_tile, ranges, reinterpret_cast<uint32_t *>(w + L.order_scratch),
                                        rb ? rb->dev_ptr + 1 : nullptr, stream),
                 "tile sort");

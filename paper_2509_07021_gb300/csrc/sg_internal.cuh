@@ -417,15 +417,19 @@ uint64_t sort_flag_words(uint64_t max_n, int bits);
 // and SG_ERR_CAPACITY to counters[CNT_STATUS] when the pairs exceed cap; pairs
 // at positions >= cap are not written. A status of SG_ERR_TIMEOUT on entry
 // (a sort gave up a bounded wait) makes the kernel write nothing.
+// key16: the keys are written as uint16_t (tile ids below 2^16, for the
+// counting tile sort; no digit histograms then), else as uint32_t.
 cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,
                              const uint32_t *tiles_touched, const uint2 *rect, const Rec *rec,
-                             uint64_t *counters, uint64_t cap, uint32_t *pkey, uint32_t *pval,
+                             uint64_t *counters, uint64_t cap, void *pkey, uint32_t *pval,
                              uint64_t *dup_flags, uint64_t *mirror, cudaStream_t s, int hist_passes = 0,
-                             uint64_t *sort_aux = nullptr, uint32_t *flags = nullptr, uint64_t flag_words = 0);
+                             uint64_t *sort_aux = nullptr, uint32_t *flags = nullptr, uint64_t flag_words = 0,
+                             bool key16 = false);
 // Tile sort by counting, for tile counts up to TC_MAX_TILES (one chunk's
 // counters fit 48 KB of shared memory): a stable sort by tile of the
 // duplicate's (tile, entry) pairs, the same order as launch_radix_sort's, in
-// three kernels with no pass over the key bits. Only the entries are written
+// three kernels with no pass over the key bits; the keys (tile ids) are
+// 16-bit, as the duplicate writes them for it. Only the entries are written
 // (ovals, cap words): a pair's tile is the tile whose range holds it. The pair
 // count is min(counters[CNT_WRITTEN], cap), none when counters[CNT_STATUS] is
 // not SG_OK on entry. matrix: n_chunks x tc_row(n_tiles) words (no zeroing
@@ -441,7 +445,7 @@ constexpr uint32_t TC_MAX_CHUNKS = SG_TC_MAX_CHUNKS;   // four one-warp placing 
 constexpr uint64_t TC_CHUNK_TARGET = 8192;            // pairs per chunk when the capacity is small
 uint32_t tc_chunks(uint64_t cap);                      // chunks of a sort sized for cap pairs
 uint64_t tc_row(uint64_t n_tiles);                     // words per row of the count matrix (multiple of 4)
-cudaError_t launch_tile_count_sort(const uint32_t *keys, const uint32_t *vals, uint32_t *ovals,
+cudaError_t launch_tile_count_sort(const uint16_t *keys, const uint32_t *vals, uint32_t *ovals,
                                    uint64_t *counters, uint64_t cap, uint32_t n_tiles, uint32_t n_chunks,
                                    uint32_t *matrix, uint64_t *words, uint2 *ranges, uint32_t *order_counts,
                                    uint64_t *status_mirror, cudaStream_t s);

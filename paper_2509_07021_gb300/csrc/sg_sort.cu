@@ -532,7 +532,7 @@ __device__ __forceinline__ void tc_chunk(const uint64_t *counters, uint64_t cap,
 }
 
 // One block per chunk: shared-memory counters of every tile, then row c.
-__global__ void __launch_bounds__(256) k_tc_count(const uint32_t *__restrict__ keys,
+__global__ void __launch_bounds__(256) k_tc_count(const uint16_t *__restrict__ keys,
                                                   const uint64_t *__restrict__ counters, uint64_t cap,
                                                   uint32_t n_tiles, uint32_t row, uint32_t *__restrict__ counts) {
     chain_enter();
@@ -542,18 +542,21 @@ __global__ void __launch_bounds__(256) k_tc_count(const uint32_t *__restrict__ k
     __syncthreads();
     uint64_t lo, hi;
     tc_chunk(counters, cap, gridDim.x, blockIdx.x, lo, hi);
-    // 16-byte loads (a chunk starts at a multiple of 32 keys), then the tail
-    const uint64_t n4 = (hi - lo) / 4;
-    const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + lo);
-#pragma unroll 8
-    for (uint64_t q = threadIdx.x; q < n4; q += blockDim.x) {
-        const uint4 t = k4[q];
-        if (t.x < n_tiles) atomicAdd(&cnt[t.x], 1u);
-        if (t.y < n_tiles) atomicAdd(&cnt[t.y], 1u);
-        if (t.z < n_tiles) atomicAdd(&cnt[t.z], 1u);
-        if (t.w < n_tiles) atomicAdd(&cnt[t.w], 1u);
+    // 16-byte loads of 8 keys (a chunk starts at a multiple of 32 keys), then the tail
+    const uint64_t n8 = (hi - lo) / 8;
+    const uint4 *k8 = reinterpret_cast<const uint4 *>(keys + lo);
+#pragma unroll 4
+    for (uint64_t q = threadIdx.x; q < n8; q += blockDim.x) {
+        const uint4 w = k8[q];
+        const uint32_t h[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t a = h[k] & 0xFFFFu, b = h[k] >> 16;
+            if (a < n_tiles) atomicAdd(&cnt[a], 1u);
+            if (b < n_tiles) atomicAdd(&cnt[b], 1u);
+        }
     }
-    for (uint64_t i = lo + 4 * n4 + threadIdx.x; i < hi; i += blockDim.x) {
+    for (uint64_t i = lo + 8 * n8 + threadIdx.x; i < hi; i += blockDim.x) {
         const uint32_t t = keys[i];
         if (t < n_tiles) atomicAdd(&cnt[t], 1u);
     }
@@ -645,7 +648,7 @@ __global__ void __launch_bounds__(TC_SCAN_WARPS * 32) k_tc_scan(uint32_t *__rest
 // cursor as the group has lanes, and each lane takes the one of its rank in the
 // group. The warp barrier between rounds orders the cursor updates of
 // successive rounds. Positions at or past cap are not written.
-__global__ void __launch_bounds__(32) k_tc_place(const uint32_t *__restrict__ keys,
+__global__ void __launch_bounds__(32) k_tc_place(const uint16_t *__restrict__ keys,
                                                  const uint32_t *__restrict__ vals,
                                                  const uint64_t *__restrict__ counters, uint64_t cap,
                                                  uint32_t n_tiles, uint32_t row,
@@ -672,7 +675,7 @@ __global__ void __launch_bounds__(32) k_tc_place(const uint32_t *__restrict__ ke
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint64_t i = base + (uint64_t)(32 * u + lane);
-            tn[u] = i < hi ? keys[i] : 0xFFFFFFFFu;
+            tn[u] = i < hi ? (uint32_t)keys[i] : 0xFFFFFFFFu;
             vn[u] = i < hi ? vals[i] : 0u;
         }
     };
@@ -700,7 +703,7 @@ __global__ void __launch_bounds__(32) k_tc_place(const uint32_t *__restrict__ ke
     }
 }
 
-cudaError_t launch_tile_count_sort(const uint32_t *keys, const uint32_t *vals, uint32_t *ovals,
+cudaError_t launch_tile_count_sort(const uint16_t *keys, const uint32_t *vals, uint32_t *ovals,
                                    uint64_t *counters, uint64_t cap, uint32_t n_tiles, uint32_t n_chunks,
                                    uint32_t *matrix, uint64_t *words, uint2 *ranges, uint32_t *order_counts,
                                    uint64_t *status_mirror, cudaStream_t s) {
@@ -766,13 +769,15 @@ __device__ __forceinline__ void hist_key_run(uint32_t (*h)[RS_RADIX], int passes
 // stay coalesced. Positions at or past cap are not written. With hist_passes > 0
 // the kernel also prepares the tile sort: it clears its look-back flags and
 // adds exactly the keys it writes to the digit histograms of its hist_passes
-// passes.
+// passes. KeyT: uint32_t, or uint16_t for the counting tile sort (tile ids
+// below 2^16).
+template <typename KeyT>
 __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp, uint64_t M,
                                                    const uint32_t *__restrict__ sorted_ent,
                                                    const uint32_t *__restrict__ tiles_touched,
                                                    const uint2 *__restrict__ rect, const Rec *__restrict__ rec,
                                                    uint64_t *__restrict__ counters, uint64_t cap,
-                                                   uint32_t *__restrict__ pkey,
+                                                   KeyT *__restrict__ pkey,
                                                    uint32_t *__restrict__ pval, int hist_passes,
                                                    SortAux *__restrict__ aux, uint32_t *__restrict__ flags,
                                                    uint64_t flag_words, uint64_t *__restrict__ dflags,
@@ -877,7 +882,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
         for (int c = c0; c < c1; ++c) {
             const uint32_t q = at + (uint32_t)(c - c0);
             if (q < lim) {   // rows sum to tiles_touched by construction; never write past the block or cap
-                pkey[out0 + q] = key0 + (uint32_t)c;
+                pkey[out0 + q] = (KeyT)(key0 + (uint32_t)c);
                 pval[out0 + q] = s_e[o];
             }
         }
@@ -889,7 +894,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
     // Rows add up to tiles_touched by construction. Should they ever fall short,
     // the rest of the block's range still gets valid tile ids and entries.
     for (uint32_t q = done + threadIdx.x; q < lim; q += 256) {
-        pkey[out0 + q] = s_base[0];
+        pkey[out0 + q] = (KeyT)s_base[0];
         pval[out0 + q] = s_e[0];
         if (hist_passes > 0) hist_key_run(h, hist_passes, s_base[0], s_base[0] + 1u);
     }
@@ -904,14 +909,21 @@ __global__ void __launch_bounds__(256) k_duplicate(const Batch *__restrict__ bp,
 
 cudaError_t launch_duplicate(const Batch *db, uint64_t M, const uint32_t *sorted_ent,
                              const uint32_t *tiles_touched, const uint2 *rect, const Rec *rec, uint64_t *counters,
-                             uint64_t cap, uint32_t *pkey, uint32_t *pval, uint64_t *dup_flags, uint64_t *mirror,
+                             uint64_t cap, void *pkey, uint32_t *pval, uint64_t *dup_flags, uint64_t *mirror,
                              cudaStream_t s, int hist_passes, uint64_t *sort_aux, uint32_t *flags,
-                             uint64_t flag_words) {
+                             uint64_t flag_words, bool key16) {
+    if (key16 && hist_passes > 0) return cudaErrorInvalidValue;   // 16-bit keys feed the counting sort only
     // one block at least: it reports the zero total of a call without entries
     const uint64_t grid = std::max<uint64_t>(div_up(M, 256), 1);
-    (void)launch_chain(k_duplicate, dim3((unsigned)grid), dim3(256), s, db, M, sorted_ent, tiles_touched, rect, rec, counters, cap, pkey,
-                                               pval, hist_passes, reinterpret_cast<SortAux *>(sort_aux), flags,
-                                               flag_words, dup_flags, mirror, sort_wait_polls());
+    SortAux *aux = reinterpret_cast<SortAux *>(sort_aux);
+    if (key16)
+        (void)launch_chain(k_duplicate<uint16_t>, dim3((unsigned)grid), dim3(256), s, db, M, sorted_ent,
+                           tiles_touched, rect, rec, counters, cap, static_cast<uint16_t *>(pkey), pval, hist_passes,
+                           aux, flags, flag_words, dup_flags, mirror, sort_wait_polls());
+    else
+        (void)launch_chain(k_duplicate<uint32_t>, dim3((unsigned)grid), dim3(256), s, db, M, sorted_ent,
+                           tiles_touched, rect, rec, counters, cap, static_cast<uint32_t *>(pkey), pval, hist_passes,
+                           aux, flags, flag_words, dup_flags, mirror, sort_wait_polls());
     count_launches(1);
     return cudaGetLastError();
 }

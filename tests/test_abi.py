@@ -61,13 +61,13 @@ def test_workspace_query_sizes(L):
     assert q0["n_tiles"] == 8 * 6 + 4 * 4
     assert q0["n_pixels"] == 128 * 96 + 64 * 64
     assert q0["ws_fixed_bytes"] == q0["ws_bytes"] == q1["ws_fixed_bytes"]
-    # 64 tiles: the tile sort counts, so 12 bytes of pair buffers per pair (the
-    # duplicate's keys and entries, the sorted entries) plus its count matrix;
-    # the depth sort's buffers (16 bytes per entry) live in the pair buffers'
-    # memory (regions aligned to 256 bytes)
+    # 64 tiles: the tile sort counts, so 10 bytes of pair buffers per pair (the
+    # duplicate's 16-bit keys and entries, the sorted entries) plus its count
+    # matrix; the depth sort's buffers (16 bytes per entry) live in the pair
+    # buffers' memory (regions aligned to 256 bytes)
     diff = q1["ws_bytes"] - q1["ws_fixed_bytes"]
-    assert 12 * 100_000 - 16 * 2000 - 1024 <= diff <= 14 * 100_000 + 4096
-    assert q1["ws_per_pair_bytes"] >= 12
+    assert 10 * 100_000 - 16 * 2000 - 1024 <= diff <= 12 * 100_000 + 4096
+    assert q1["ws_per_pair_bytes"] >= 10
     assert q1["bwd_ws_bytes"] >= 9 * 4 * 2000
     lay = sgsplat.sg_workspace_layout(ds, cams, q1["ws_bytes"])
     assert lay["total_bytes"] == q1["ws_bytes"]
