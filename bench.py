@@ -45,8 +45,8 @@ FLOPS_PER_EVAL = {"blend_fwd": 23.0, "blend_bwd": 69.0}
 # while the sources are unchanged (any kernel change makes it null until the
 # next capture).
 RECORDED_TRAFFIC = {
-    "sources": "a1bec279fc40508abf75bbded62dc8198c8dcea5d1901ab6029ec859bf14ac93",
-    "bytes": {"blend_bwd": 120956928, "blend_fwd": 50107136},
+    "sources": "152dfa29603bb7f2880aeebebcdfac575fb630bda3dedf85e73ddea12cab12d5",
+    "bytes": {"blend_bwd": 121079808, "blend_fwd": 50215680},
 }
 
 
@@ -339,7 +339,8 @@ def gpu_errors_vs_oracle(scene, cam, d_img, storages=("f32", "f16_bf16s"), n_til
 def stage_rooflines(stages_ms, counts, evals, hbm_gbs):
     """Achieved fraction of roofline for every stage: algorithmic bytes (HBM
     stages) or flops (blend) per step over the stage's event time per step.
-    counts: N Gaussians, L lobes, M entries, V entries with pairs, K pairs, T tiles."""
+    counts: N Gaussians, L lobes, M entries, V entries with pairs, K pairs, T tiles;
+    counting: the tile sort counted (cap: the pair capacity, which sets its chunks)."""
     N, L, M, V, K, T = (counts[k] for k in ("N", "L", "M", "V", "K", "T"))
     by = {
         "preprocess": 64 * N + 32 * L + 69 * M,                 # params in; record, tt, rect, clamp, key, value out
@@ -351,6 +352,13 @@ def stage_rooflines(stages_ms, counts, evals, hbm_gbs):
         "bwd_clear": 36 * M,
         "preprocess_bwd": 64 * N + 32 * L + 41 * M + 60 * N + 32 * L,
     }
+    if counts.get("counting"):
+        # chunks of the counting tile sort (at most 608, 8192 pairs of capacity each)
+        C = min(608, max(1, -(-int(counts["cap"]) // 8192)))
+        by["duplicate"] = 64 * V + 6 * K                        # 16-bit tile keys
+        # keys read twice, entries read and written; the [C][T] count matrix written,
+        # read and rewritten by the scan, read by the placing; tile ranges
+        by["tile_sort"] = 4 * K + 8 * K + 16 * C * T + 8 * T
     out = {}
     for k, ms in stages_ms.items():
         if ms <= 0:
@@ -536,7 +544,8 @@ def run_ours(args, world, rank, local):
     M = out.sizes["n_entries"]
     tt = out.ws[lay["tiles_touched"]:lay["tiles_touched"] + 4 * M].view(torch.int32)
     counts = {"N": scene.n, "L": scene.n_lobes, "M": M, "V": int((tt != 0).sum().item()),
-              "K": n_pairs, "T": cam.n_tiles}
+              "K": n_pairs, "T": cam.n_tiles, "cap": out.sizes["pair_capacity"],
+              "counting": lay["pair_tile"] == 2**64 - 1}
     hbm_peak = 6800.0
     try:
         hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
