@@ -78,6 +78,43 @@ def test_workspace_query_sizes(L):
     assert len(set(offs)) == len(offs)
 
 
+def test_tile_sort_path_follows_the_tile_count(L):
+    """Up to 12288 tiles in all the tile sort counts: 16-bit duplicate keys, the
+    sorted entries only (pair_tile absent), a count matrix of at most 608 rows
+    of the padded tile count in the look-back flags' region. Above it the radix
+    passes keep sorted tile ids in two 16-byte-per-pair regions."""
+    ds = _cpu_scene(1000, 2)
+    cap = 2_000_000
+    # 1920x1080: 120 x 68 = 8160 tiles (counting); two such views: 16320 (radix)
+    one = [synth.make_camera(1920, 1080, 1500.0)]
+    two = one * 2
+    q1 = sgsplat.sg_workspace_query(ds, one, cap)
+    q2 = sgsplat.sg_workspace_query(ds, two, cap)
+    assert q1["n_tiles"] == 8160 and q2["n_tiles"] == 16320
+    l1 = sgsplat.sg_workspace_layout(ds, one, q1["ws_bytes"])
+    l2 = sgsplat.sg_workspace_layout(ds, two, q2["ws_bytes"])
+    assert l1["pair_tile"] == 2**64 - 1
+    assert l2["pair_tile"] != 2**64 - 1 and l2["pair_tile"] % 256 == 0
+    assert q1["pair_capacity"] == cap and q2["pair_capacity"] == cap
+    # per pair of capacity: 10 bytes of pairs + the matrix share (4 B x 8160
+    # tiles per 8192 pairs) against 16 bytes of pairs + the radix flags
+    assert q1["ws_per_pair_bytes"] == 10 + 4 and q2["ws_per_pair_bytes"] == 17
+    f1 = q1["ws_bytes"] - q1["ws_fixed_bytes"]
+    f2 = q2["ws_bytes"] - q2["ws_fixed_bytes"]
+    chunks = min(608, -(-cap // 8192))
+    assert f1 <= 10 * cap + 4 * 8160 * chunks + 4096
+    assert f2 >= 16 * cap - 16 * 2000
+    # at the counting limit (12288 tiles: 2048 x 1536) and one tile row past it
+    at = [synth.make_camera(2048, 1536, 1500.0)]
+    past = [synth.make_camera(2048, 1552, 1500.0)]
+    assert sgsplat.sg_workspace_query(ds, at, 0)["n_tiles"] == 12288
+    assert sgsplat.sg_workspace_query(ds, past, 0)["n_tiles"] == 12416
+    la = sgsplat.sg_workspace_layout(ds, at, sgsplat.sg_workspace_query(ds, at, cap)["ws_bytes"])
+    lp = sgsplat.sg_workspace_layout(ds, past, sgsplat.sg_workspace_query(ds, past, cap)["ws_bytes"])
+    assert la["pair_tile"] == 2**64 - 1
+    assert lp["pair_tile"] != 2**64 - 1
+
+
 def _status(L, fn, *args):
     return fn(*args)
 
