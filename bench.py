@@ -45,8 +45,8 @@ FLOPS_PER_EVAL = {"blend_fwd": 23.0, "blend_bwd": 69.0}
 # while the sources are unchanged (any kernel change makes it null until the
 # next capture).
 RECORDED_TRAFFIC = {
-    "sources": "152dfa29603bb7f2880aeebebcdfac575fb630bda3dedf85e73ddea12cab12d5",
-    "bytes": {"blend_bwd": 121079808, "blend_fwd": 50215680},
+    "sources": "080aff9b363c692f75aa9f2580e8ba2acb293f3bbe3a982abbdad2eae7efd4a0",
+    "bytes": {"blend_bwd": 120819456, "blend_fwd": 50263552},
 }
 
 

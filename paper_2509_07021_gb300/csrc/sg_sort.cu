@@ -566,15 +566,16 @@ __global__ void __launch_bounds__(256) k_tc_count(const uint16_t *__restrict__ k
 }
 
 // Groups of 32 tiles (lane = tile), taken in order from a ticket by resident
-// blocks; the chunks split into TC_SCAN_WARPS runs (one per warp), whose counts
-// stay in registers. The sum of each tile's counts and the group's total go
+// blocks (two per SM); the chunks split into TC_SCAN_WARPS runs (one per warp),
+// whose counts wait in shared memory for the second walk. The sum of each tile's counts and the group's total go
 // through a decoupled look-back over the groups before it, which gives every
 // tile's first position; the second walk replaces each count with its chunk's
 // first position of the tile. Also writes every tile's range ((0, 0) when
 // empty) and adds the tile to its list-length bucket.
 // words: zeroed; [0] the ticket, [1 + g] group g's look-back word.
 constexpr int TC_SCAN_WARPS = 32;
-__global__ void __launch_bounds__(TC_SCAN_WARPS * 32) k_tc_scan(uint32_t *__restrict__ counts, uint32_t n_chunks,
+constexpr int TC_SCAN_RUN = (TC_MAX_CHUNKS + TC_SCAN_WARPS - 1) / TC_SCAN_WARPS;
+__global__ void __launch_bounds__(TC_SCAN_WARPS * 32, 2) k_tc_scan(uint32_t *__restrict__ counts, uint32_t n_chunks,
                                                               uint32_t row, uint32_t n_tiles,
                                                               uint64_t *__restrict__ words,
                                                               uint2 *__restrict__ ranges,
@@ -588,7 +589,8 @@ __global__ void __launch_bounds__(TC_SCAN_WARPS * 32) k_tc_scan(uint32_t *__rest
     const uint32_t n_groups = (n_tiles + 31) / 32;
     const uint32_t per = (n_chunks + TC_SCAN_WARPS - 1) / TC_SCAN_WARPS;
     const uint32_t c0 = min(n_chunks, warp * per), c1 = min(n_chunks, c0 + per);
-    constexpr int RUN = (TC_MAX_CHUNKS + TC_SCAN_WARPS - 1) / TC_SCAN_WARPS;
+    constexpr int RUN = TC_SCAN_RUN;
+    extern __shared__ uint32_t cvs[];   // [RUN][block threads]: the run's counts
     for (;;) {
         // every thread is past the previous group's reads of the shared words
         __syncthreads();
@@ -599,13 +601,13 @@ __global__ void __launch_bounds__(TC_SCAN_WARPS * 32) k_tc_scan(uint32_t *__rest
         const uint32_t t = grp * 32 + lane;
         const bool tv = t < n_tiles;
         uint32_t *col = counts + t;
-        uint32_t cv[RUN];
         uint32_t sum = 0;
 #pragma unroll
         for (int j = 0; j < RUN; ++j) {
             const uint32_t c = c0 + (uint32_t)j;
-            cv[j] = (tv && c < c1) ? col[(uint64_t)c * row] : 0u;
-            sum += cv[j];
+            const uint32_t x = (tv && c < c1) ? col[(uint64_t)c * row] : 0u;
+            cvs[j * TC_SCAN_WARPS * 32 + threadIdx.x] = x;
+            sum += x;
         }
         part[warp][lane] = sum;
         __syncthreads();
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(TC_SCAN_WARPS * 32) k_tc_scan(uint32_t *__rest
         for (int j = 0; j < RUN; ++j) {
             const uint32_t c = c0 + (uint32_t)j;
             if (tv && c < c1) col[(uint64_t)c * row] = run;
-            run += cv[j];
+            run += cvs[j * TC_SCAN_WARPS * 32 + threadIdx.x];
         }
     }
 }
@@ -660,10 +662,13 @@ __global__ void __launch_bounds__(32) k_tc_place(const uint16_t *__restrict__ ke
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x;
     if (blockIdx.x == 0 && lane == 0 && status_mirror) *status_mirror = counters[CNT_STATUS];
+    // the row arrives by asynchronous 16-byte copies while the first batch loads
     const uint4 *src = reinterpret_cast<const uint4 *>(first + (uint64_t)blockIdx.x * row);
-#pragma unroll 8
-    for (uint32_t q = lane; q < row / 4; q += 32) tc_smem[q] = src[q];
-    __syncwarp();
+    for (uint32_t q = lane; q < row / 4; q += 32) {
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(tc_smem + q);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + q) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
     uint64_t lo, hi;
     tc_chunk(counters, cap, gridDim.x, blockIdx.x, lo, hi);
     const uint32_t lt = (1u << lane) - 1u;
@@ -680,6 +685,8 @@ __global__ void __launch_bounds__(32) k_tc_place(const uint16_t *__restrict__ ke
         }
     };
     load(lo);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
     for (uint64_t base = lo; base < hi; base += 32 * U) {
         uint32_t t[U], v[U];
 #pragma unroll
@@ -714,17 +721,21 @@ cudaError_t launch_tile_count_sort(const uint16_t *keys, const uint32_t *vals, u
     (void)launch_chain_smem(k_tc_count, dim3(n_chunks), dim3(256), smem, s, keys, (const uint64_t *)counters, cap,
                        n_tiles, row, matrix);
     // resident blocks only: a group's look-back may wait on any earlier group
+    const size_t scan_smem = (size_t)TC_SCAN_RUN * TC_SCAN_WARPS * 32 * 4;
     static int scan_blocks = 0;
     if (scan_blocks == 0) {
         int dev = 0, sms = 0, per_sm = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
+        if (cudaFuncSetAttribute(k_tc_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem) !=
+                cudaSuccess ||
+            cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_scan, TC_SCAN_WARPS * 32, 0) != cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_scan, TC_SCAN_WARPS * 32, scan_smem) !=
+                cudaSuccess)
             return cudaErrorUnknown;
         scan_blocks = std::max(1, sms * per_sm);
     }
     const unsigned sgrid = (unsigned)std::min<uint64_t>(div_up(n_tiles, 32), (uint64_t)scan_blocks);
-    (void)launch_chain(k_tc_scan, dim3(sgrid), dim3(TC_SCAN_WARPS * 32), s, matrix, n_chunks,
+    (void)launch_chain_smem(k_tc_scan, dim3(sgrid), dim3(TC_SCAN_WARPS * 32), scan_smem, s, matrix, n_chunks,
                        row, n_tiles, words, ranges, order_counts, counters + CNT_STATUS, sort_wait_polls());
     (void)launch_chain_smem(k_tc_place, dim3(n_chunks), dim3(32), smem, s, keys, vals, (const uint64_t *)counters, cap,
                        n_tiles, row, (const uint32_t *)matrix, ovals, status_mirror);
