@@ -332,7 +332,14 @@ def sg_workspace_query(scene: DeviceScene, cams, pair_capacity: int) -> dict:
     return out.as_dict()
 
 
+NO_OFFSET = 2**64 - 1   # a layout entry for a buffer the workspace does not hold
+
+
 def sg_workspace_layout(scene: DeviceScene, cams, ws_bytes: int) -> dict:
+    """Byte offsets of a forward's buffers in a workspace of ws_bytes. pair_tile
+    is NO_OFFSET when the views have at most 12288 tiles in all: the tile sort
+    then counts and keeps no sorted tile ids (pair k's tile is the tile whose
+    range holds k)."""
     s = scene.struct()
     c = camera_array(cams)
     out = sg_ws_layout()
@@ -476,6 +483,7 @@ def sg_batched_workspace_query(scenes, cams, view_scene, pair_capacity: int) -> 
 
 
 def sg_batched_workspace_layout(scenes, cams, view_scene, ws_bytes: int) -> dict:
+    """As sg_workspace_layout, for a batched forward."""
     out = sg_ws_layout()
     _check(lib().sg_batched_workspace_layout(scene_array(scenes), len(scenes), camera_array(cams),
                                              _view_scene_array(view_scene), len(cams), int(ws_bytes),

@@ -8,13 +8,10 @@ import torch
 import oracle
 import tight_binning
 from paper_2509_07021_gb300 import render, sgsplat
-from paper_2509_07021_gb300.sgsplat import DeviceScene
+from paper_2509_07021_gb300.sgsplat import NO_OFFSET, DeviceScene
 
 IMG_TOL = 2e-4      # max abs per channel (images)
 GRAD_TOL = 1e-3     # relative L2 per gradient tensor
-
-
-NO_OFFSET = 2**64 - 1   # a workspace buffer the layout does not hold
 
 
 def u32(t: torch.Tensor) -> np.ndarray:
